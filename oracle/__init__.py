@@ -1,0 +1,298 @@
+"""FP64 CPU oracle for the Gaussian source-finder hot path (ctypes wrapper).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` are the only users.
+The CUDA library never imports or links this package, and this package never
+imports the CUDA library.
+
+The arithmetic lives in ``sf_oracle.c`` (plain FP64 loops, one function per
+definition of the paper):
+
+* taps: sampled Gaussian, truncated at ``R = ceil(truncation * sigma)``,
+  normalised to sum 1 (Sec. 2.1 and Sec. 3.4; the paper gives no sigma or
+  truncation, the filter bank is a parameter);
+* filter: Eq. 2, zero outside the cube, 3D filter = outer product of the 1D
+  taps (separable evaluation, plus the literal triple sum for spot checks);
+* window statistics: population mean and standard deviation over
+  non-overlapping windows from the origin (Sec. 3.3, statistics over a range of
+  voxels around each voxel, read as the window holding it);
+* threshold: ``c > mean + k * std`` (Sec. 3.3 z-score selection), OR over the
+  bank, packed 32 consecutive z per uint32 word.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sf_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "libsforacle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_i64 = ctypes.c_int64
+
+
+def build(force: bool = False) -> str:
+    """Compile sf_oracle.c into oracle/_build/libsforacle.so (gcc, OpenMP)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", _SRC,
+           "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        lib.or_radius.argtypes = [ctypes.c_double, ctypes.c_double]
+        lib.or_radius.restype = ctypes.c_int
+        lib.or_taps.argtypes = [ctypes.c_double, ctypes.c_int, _dp]
+        lib.or_taps.restype = None
+        lib.or_filter_box.argtypes = [_fp, _i64, _i64, _i64, _dp, ctypes.c_int, _dp,
+                                      ctypes.c_int, _dp, ctypes.c_int, _i64, _i64, _i64,
+                                      _i64, _i64, _i64, ctypes.c_int, _dp]
+        lib.or_filter_box.restype = ctypes.c_int
+        lib.or_filter_direct_voxel.argtypes = [_fp, _i64, _i64, _i64, _dp, ctypes.c_int,
+                                               _dp, ctypes.c_int, _dp, ctypes.c_int,
+                                               _i64, _i64, _i64]
+        lib.or_filter_direct_voxel.restype = ctypes.c_double
+        lib.or_moments.argtypes = [_dp, _i64, _dp, _dp]
+        lib.or_moments.restype = None
+        lib.or_window_stats.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, _dp, _dp]
+        lib.or_window_stats.restype = ctypes.c_int
+        lib.or_threshold.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, _dp, _dp, ctypes.c_double,
+                                     ctypes.c_double, _u32p, _u32p]
+        lib.or_threshold.restype = None
+        lib.or_detect_window.argtypes = [_fp, _i64, _i64, _i64, ctypes.c_int, _ip, _dp, _ip,
+                                         _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_double, _i64, _i64, _i64,
+                                         _dp, _dp, _u8p, _u8p, _dp, _dp]
+        lib.or_detect_window.restype = ctypes.c_int
+        lib.or_detect.argtypes = [_fp, _i64, _i64, _i64, ctypes.c_int, _ip, _dp, _ip, _dp,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_double, _u32p, _u32p, _dp, _dp, ctypes.c_int]
+        lib.or_detect.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray, typ):
+    return a.ctypes.data_as(typ)
+
+
+def _cube(d) -> np.ndarray:
+    d = np.ascontiguousarray(np.asarray(d), dtype=np.float32)
+    if d.ndim != 3:
+        raise ValueError("cube must be 3D [x][y][z]")
+    return d
+
+
+# ---------------------------------------------------------------- taps -------
+def radius(sigma: float, truncation: float) -> int:
+    """R = ceil(truncation * sigma); 0 when sigma <= 0."""
+    return int(_load().or_radius(float(sigma), float(truncation)))
+
+
+def taps(sigma: float, truncation: float) -> np.ndarray:
+    """Normalised truncated Gaussian taps, length 2R+1, offset o at index o+R."""
+    r = radius(sigma, truncation)
+    g = np.empty(2 * r + 1, dtype=np.float64)
+    _load().or_taps(float(sigma), r, _ptr(g, _dp))
+    return g
+
+
+# -------------------------------------------------------------- filter -------
+def filter_box(d, sigma_xy: float, sigma_z: float, truncation: float,
+               box=None, take_abs: bool = False) -> np.ndarray:
+    """Eq. 2 filtered values (float64) on box ((x0,x1),(y0,y1),(z0,z1))."""
+    d = _cube(d)
+    nx, ny, nz = d.shape
+    if box is None:
+        box = ((0, nx), (0, ny), (0, nz))
+    (x0, x1), (y0, y1), (z0, z1) = box
+    gxy = taps(sigma_xy, truncation)
+    gz = taps(sigma_z, truncation)
+    rxy, rz = (len(gxy) - 1) // 2, (len(gz) - 1) // 2
+    out = np.empty((x1 - x0, y1 - y0, z1 - z0), dtype=np.float64)
+    rc = _load().or_filter_box(_ptr(d, _fp), nx, ny, nz, _ptr(gxy, _dp), rxy,
+                               _ptr(gxy, _dp), rxy, _ptr(gz, _dp), rz,
+                               x0, x1, y0, y1, z0, z1, int(take_abs), _ptr(out, _dp))
+    if rc != 0:
+        raise MemoryError("oracle filter_box: out of memory")
+    return out
+
+
+def filter_direct_voxel(d, sigma_xy: float, sigma_z: float, truncation: float,
+                        x: int, y: int, z: int) -> float:
+    """Eq. 2 as the literal triple sum at one voxel."""
+    d = _cube(d)
+    nx, ny, nz = d.shape
+    gxy = taps(sigma_xy, truncation)
+    gz = taps(sigma_z, truncation)
+    rxy, rz = (len(gxy) - 1) // 2, (len(gz) - 1) // 2
+    return float(_load().or_filter_direct_voxel(_ptr(d, _fp), nx, ny, nz, _ptr(gxy, _dp),
+                                                rxy, _ptr(gxy, _dp), rxy, _ptr(gz, _dp),
+                                                rz, x, y, z))
+
+
+# --------------------------------------------------------------- stats -------
+def moments(values) -> tuple[float, float]:
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).ravel())
+    m = ctypes.c_double()
+    s = ctypes.c_double()
+    _load().or_moments(_ptr(v, _dp), v.size, ctypes.byref(m), ctypes.byref(s))
+    return m.value, s.value
+
+
+def window_grid(shape, window) -> tuple[int, int, int]:
+    return tuple(-(-int(n) // int(w)) for n, w in zip(shape, window))
+
+
+def window_stats(c, window) -> tuple[np.ndarray, np.ndarray]:
+    """Mean and population std per window of a filtered cube, [nwx][nwy][nwz]."""
+    c = np.ascontiguousarray(np.asarray(c), dtype=np.float64)
+    nx, ny, nz = c.shape
+    wx, wy, wz = window
+    grid = window_grid(c.shape, window)
+    mean = np.empty(grid, dtype=np.float64)
+    std = np.empty(grid, dtype=np.float64)
+    if _load().or_window_stats(_ptr(c, _dp), nx, ny, nz, wx, wy, wz,
+                               _ptr(mean, _dp), _ptr(std, _dp)) != 0:
+        raise MemoryError("oracle window_stats: out of memory")
+    return mean, std
+
+
+def mask_words_shape(shape) -> tuple[int, int, int]:
+    nx, ny, nz = shape
+    return (nx, ny, -(-nz // 32))
+
+
+def threshold(c, window, mean, std, k: float, band_rel: float = 1e-4):
+    """Packed masks (fire, ambiguous) of c > mean + k*std per window."""
+    c = np.ascontiguousarray(np.asarray(c), dtype=np.float64)
+    nx, ny, nz = c.shape
+    wx, wy, wz = window
+    mean = np.ascontiguousarray(mean, dtype=np.float64)
+    std = np.ascontiguousarray(std, dtype=np.float64)
+    mask = np.zeros(mask_words_shape(c.shape), dtype=np.uint32)
+    amb = np.zeros_like(mask)
+    _load().or_threshold(_ptr(c, _dp), nx, ny, nz, wx, wy, wz, _ptr(mean, _dp),
+                         _ptr(std, _dp), float(k), float(band_rel), _ptr(mask, _u32p),
+                         _ptr(amb, _u32p))
+    return mask, amb
+
+
+# -------------------------------------------------------------- detect -------
+def _bank_arrays(bank, truncation):
+    rxy, rz, gxy, gz = [], [], [], []
+    for sxy, sz in bank:
+        a = taps(sxy, truncation)
+        b = taps(sz, truncation)
+        rxy.append((len(a) - 1) // 2)
+        rz.append((len(b) - 1) // 2)
+        gxy.append(a)
+        gz.append(b)
+    return (np.array(rxy, dtype=np.int32), np.concatenate(gxy),
+            np.array(rz, dtype=np.int32), np.concatenate(gz))
+
+
+def detect_window(d, bank, truncation, window, k, widx, band_rel: float = 1e-4):
+    """Whole method on one window (a, b, e); returns a dict of float64/uint8 arrays.
+
+    Keys: mean[f], std[f], thr[f], fire/sure [window voxels as x,y,z box], c[f][box].
+    """
+    d = _cube(d)
+    nx, ny, nz = d.shape
+    wx, wy, wz = window
+    a, b, e = widx
+    ex = min(wx, nx - a * wx)
+    ey = min(wy, ny - b * wy)
+    ez = min(wz, nz - e * wz)
+    if ex <= 0 or ey <= 0 or ez <= 0:
+        raise ValueError("window index outside the cube")
+    nf = len(bank)
+    rxy, gxy, rz, gz = _bank_arrays(bank, truncation)
+    n = ex * ey * ez
+    mean = np.empty(nf)
+    std = np.empty(nf)
+    thr = np.empty(nf)
+    fire = np.empty(n, dtype=np.uint8)
+    sure = np.empty(n, dtype=np.uint8)
+    cv = np.empty((nf, n))
+    rc = _load().or_detect_window(_ptr(d, _fp), nx, ny, nz, nf, _ptr(rxy, _ip), _ptr(gxy, _dp),
+                                  _ptr(rz, _ip), _ptr(gz, _dp), wx, wy, wz, float(k),
+                                  float(band_rel), a, b, e, _ptr(mean, _dp), _ptr(std, _dp),
+                                  _ptr(fire, _u8p), _ptr(sure, _u8p), _ptr(cv, _dp),
+                                  _ptr(thr, _dp))
+    if rc != 0:
+        raise MemoryError("oracle detect_window: out of memory")
+    box = (ex, ey, ez)
+    return {"mean": mean, "std": std, "thr": thr, "fire": fire.reshape(box),
+            "sure": sure.reshape(box), "c": cv.reshape((nf,) + box),
+            "origin": (a * wx, b * wy, e * wz)}
+
+
+def detect(d, bank, truncation, window, k, band_rel: float = 1e-4, nthreads: int = 0):
+    """Whole method on the whole cube.
+
+    Returns dict: mask, sure (packed uint32 [nx][ny][ceil(nz/32)]), mean, std
+    ([nf][nwx][nwy][nwz]) and threads (OpenMP threads used).
+    """
+    d = _cube(d)
+    nx, ny, nz = d.shape
+    wx, wy, wz = window
+    nf = len(bank)
+    rxy, gxy, rz, gz = _bank_arrays(bank, truncation)
+    grid = window_grid(d.shape, window)
+    mask = np.zeros(mask_words_shape(d.shape), dtype=np.uint32)
+    sure = np.zeros_like(mask)
+    mean = np.empty((nf,) + grid)
+    std = np.empty((nf,) + grid)
+    used = _load().or_detect(_ptr(d, _fp), nx, ny, nz, nf, _ptr(rxy, _ip), _ptr(gxy, _dp),
+                             _ptr(rz, _ip), _ptr(gz, _dp), wx, wy, wz, float(k),
+                             float(band_rel), _ptr(mask, _u32p), _ptr(sure, _u32p),
+                             _ptr(mean, _dp), _ptr(std, _dp), int(nthreads))
+    if used < 0:
+        raise MemoryError("oracle detect: out of memory")
+    return {"mask": mask, "sure": sure, "mean": mean, "std": std, "threads": used}
+
+
+def pack_bits(bits) -> np.ndarray:
+    """Pack a boolean [nx][ny][nz] array into the mask word layout (bit z%32)."""
+    bits = np.asarray(bits, dtype=bool)
+    nx, ny, nz = bits.shape
+    nw = -(-nz // 32)
+    padded = np.zeros((nx, ny, nw * 32), dtype=np.uint64)
+    padded[:, :, :nz] = bits
+    weights = (np.uint64(1) << np.arange(32, dtype=np.uint64))
+    words = (padded.reshape(nx, ny, nw, 32) * weights).sum(axis=-1)
+    return words.astype(np.uint32)
+
+
+def unpack_bits(words, nz: int) -> np.ndarray:
+    """Inverse of pack_bits: packed words -> boolean [nx][ny][nz]."""
+    words = np.asarray(words, dtype=np.uint32)
+    bits = (words[..., None] >> np.arange(32, dtype=np.uint32)) & 1
+    nx, ny, nw = words.shape
+    return bits.reshape(nx, ny, nw * 32)[:, :, :nz].astype(bool)

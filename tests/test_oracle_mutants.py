@@ -1,0 +1,58 @@
+"""The pins catch planted slips in the oracle.
+
+Each case copies the oracle, plants one plausible mistake in its C source and
+runs tests/test_oracle_pins.py against the copy (on the CPU); the pins must
+fail.  Sign flips of the symmetric taps are not mistakes in effect and are not
+planted.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    "taps_not_normalised": ("for (int o = -R; o <= R; ++o) g[o + R] /= sum;", ""),
+    "radius_floor": ("return (int)ceil(truncation * sigma);",
+                     "return (int)floor(truncation * sigma);"),
+    "z_pass_shifted": ("t2[(i * ey + j) * ezh + (k + rz + o)]",
+                       "t2[(i * ey + j) * ezh + (k + rz + o + 1 < ezh ? k + rz + o + 1 : k + rz + o)]"),
+    "x_pass_on_y_axis": ("at(d, nx, ny, nz, x + o, y, z, take_abs)",
+                         "at(d, nx, ny, nz, x, y + o, z, take_abs)"),
+    "edge_clamped_not_zero": (
+        "if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz) return 0.0;",
+        "if (x < 0) x = 0; if (y < 0) y = 0; if (z < 0) z = 0;"
+        " if (x >= nx) x = nx - 1; if (y >= ny) y = ny - 1; if (z >= nz) z = nz - 1;"),
+    "sample_std": ("*stdv = sqrt(q / (double)n);", "*stdv = sqrt(q / (double)(n > 1 ? n - 1 : 1));"),
+    "threshold_not_strict": ("if (v > T) mask[word] |= bit;", "if (v >= T) mask[word] |= bit;"),
+    "bit_order_reversed": ("const uint32_t bit = 1u << (z % 32);\n                if (v > T)",
+                           "const uint32_t bit = 1u << (31 - z % 32);\n                if (v > T)"),
+    "window_tail_off_by_one": ("for (int64_t z = e * wz; z < nz && z < (e + 1) * wz; ++z)",
+                               "for (int64_t z = e * wz; z < nz && z <= (e + 1) * wz; ++z)"),
+    "detect_drops_last_filter": ("for (int f = 0; f < nf; ++f) {\n        const double *gxy",
+                                 "for (int f = 0; f < nf - (nf > 1); ++f) {\n        const double *gxy"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_slip(tmp_path, name):
+    old, new = MUTANTS[name]
+    dst = tmp_path / "oracle_mutant"
+    shutil.copytree(os.path.join(ROOT, "oracle"), dst,
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    src = dst / "sf_oracle.c"
+    text = src.read_text()
+    assert old in text, f"mutation site for {name} not found"
+    src.write_text(text.replace(old, new, 1))
+    # the mutant must compile: a build error would count as "caught" otherwise
+    cc = subprocess.run(["gcc", "-std=c99", "-fopenmp", "-fsyntax-only", str(src)],
+                        capture_output=True, text=True)
+    assert cc.returncode == 0, cc.stderr
+    env = dict(os.environ, SF_ORACLE_DIR=str(dst))
+    res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert res.returncode != 0, f"pins did not catch {name}:\n{res.stdout[-2000:]}"
