@@ -1,0 +1,150 @@
+/*
+ * sf.h — C ABI of the GB300 Gaussian source-finder hot path.
+ *
+ * The library applies a bank of separable 3D Gaussian filters to an HI
+ * spectral cube, computes the mean and standard deviation of every filtered
+ * cube over windows, marks the voxels whose filtered value exceeds
+ * mean + k * std of their window, and ORs the marks of all filters into one
+ * bit-packed mask (Westerlund & Harris, Sec. 2.1 Eq. 2 for the filter,
+ * Sec. 3.3 for the local statistics and the z-score voxel selection).
+ *
+ * Conventions shared by every entry point:
+ *   - Cube layout is cube[x][y][z], z (frequency) contiguous, x the major
+ *     axis (Sec. 3.1).  nx, ny, nz >= 1.
+ *   - Pointers prefixed d_ are device pointers, h_ host pointers.  The caller
+ *     owns every buffer it passes and must keep it alive until the work
+ *     enqueued on `stream` has finished.  Device pointers must be 16-byte
+ *     aligned.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     entry points only enqueue work and return; they do not synchronise.
+ *   - The context owns the filter taps, the execution plan, the compiled
+ *     kernels and its scratch buffers (the x-filtered cubes, one per distinct
+ *     non-zero sigma_xy).  Calls on one context are not thread-safe and must
+ *     not overlap on the GPU (use one context per concurrent stream).
+ *   - Errors are return codes; sf_last_error() gives a message.  Arguments
+ *     are validated on the host before anything is enqueued.  After a CUDA
+ *     error the context returns SF_ESTATE until it is destroyed.
+ *   - Mask layout: uint32 words, word (x*ny + y)*ceil(nz/32) + z/32 holds
+ *     voxel (x, y, z) in bit z%32; bits beyond nz in the last word of a row
+ *     are zero.
+ *   - Windows tile the cube from the origin: window (a, b, e) covers
+ *     [a*wx, min((a+1)*wx, nx)) x [b*wy, ...) x [e*wz, ...); tail windows
+ *     hold the voxels present.  Statistics arrays are float32
+ *     [n_filters][nwx][nwy][nwz] (sf_stats: [nwx][nwy][nwz]).
+ */
+#ifndef SF_H
+#define SF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sf_ctx sf_ctx;
+
+typedef enum sf_status {
+    SF_OK = 0,
+    SF_EINVAL = 1,    /* invalid argument or configuration */
+    SF_ENOMEM = 2,    /* device or host allocation failed */
+    SF_EBUDGET = 3,   /* request does not fit the memory budget (serving) */
+    SF_ECUDA = 4,     /* CUDA runtime error */
+    SF_ETIMEOUT = 5,  /* a bounded wait expired */
+    SF_ESTATE = 6,    /* context unusable after an earlier CUDA error */
+    SF_EJIT = 7       /* run-time compilation of a kernel failed */
+} sf_status;
+
+typedef enum sf_dtype {
+    SF_F32 = 0,       /* float32 storage of the cube and intermediates */
+    SF_F16 = 1,       /* IEEE half storage, float32 arithmetic */
+    SF_BF16 = 2       /* bfloat16 storage, float32 arithmetic */
+} sf_dtype;
+
+/* One filter of the bank: Gaussian sigma along x and y (in pixels; 0 means
+ * no spatial smoothing) and along z (in channels). */
+typedef struct sf_filter_spec {
+    float sigma_xy;
+    float sigma_z;
+} sf_filter_spec;
+
+typedef struct sf_config {
+    int64_t nx, ny, nz;            /* cube dimensions */
+    int32_t n_filters;             /* 1 .. 64 */
+    const sf_filter_spec *filters; /* copied by sf_create */
+    float truncation;              /* radius R = ceil(truncation*sigma) per axis */
+    int32_t wx, wy, wz;            /* statistics window (>= 1 each) */
+    float k;                       /* threshold multiplier */
+    int32_t storage;               /* sf_dtype of the cube and the x-filtered scratch */
+    int32_t stats_fp64;            /* reserved, must be 0 */
+    int32_t device;                /* CUDA device ordinal, -1 = current device */
+} sf_config;
+
+/* Create a context: copies cfg, computes the taps (Sec. 2.1: sampled Gaussian
+ * exp(-o^2/2sigma^2), o in [-R, R], normalised to sum 1; radius limit 64 per
+ * axis), plans the kernels, compiles them for the device at run time and
+ * allocates the scratch cubes.  *out is NULL on failure. */
+sf_status sf_create(const sf_config *cfg, sf_ctx **out);
+
+/* Free the context after synchronising the device work it owns. NULL-safe. */
+sf_status sf_destroy(sf_ctx *ctx);
+
+const char *sf_status_str(sf_status s);
+/* Message of the last failure on ctx (or of the last failed sf_create when
+ * ctx is NULL); never NULL. */
+const char *sf_last_error(const sf_ctx *ctx);
+
+/* Host query of the float32 taps the device uses for filter `filter` along
+ * axis 0 (x and y) or 2 (z): writes 2R+1 values (offset o at index o+R) into
+ * out (capacity cap) and R into *radius.  Sec. 2.1 / Sec. 3.4. */
+sf_status sf_taps(const sf_ctx *ctx, int32_t filter, int32_t axis, float *out, int32_t cap,
+                  int32_t *radius);
+
+/* Window grid size and mask size in uint32 words. */
+sf_status sf_window_grid(const sf_ctx *ctx, int32_t *nwx, int32_t *nwy, int32_t *nwz);
+sf_status sf_mask_words(const sf_ctx *ctx, int64_t *words);
+
+/* Filtered cube of one filter (Eq. 2 with the 3D filter the product of the
+ * three 1D tap vectors, image zero outside the cube, no renormalisation at
+ * the edges).  d_cube: storage dtype, nx*ny*nz elements.  d_filtered: float32,
+ * nx*ny*nz elements. */
+sf_status sf_filter(sf_ctx *ctx, const void *d_cube, int32_t filter, float *d_filtered,
+                    void *stream);
+
+/* Window mean and population standard deviation of a float32 filtered cube
+ * (Sec. 3.3).  d_mean, d_std: float32 [nwx][nwy][nwz]. */
+sf_status sf_stats(sf_ctx *ctx, const float *d_filtered, float *d_mean, float *d_std,
+                   void *stream);
+
+/* Threshold of a float32 filtered cube against its window statistics
+ * (Sec. 3.3 voxel selection): bit set where value > mean + k*std (strict).
+ * accumulate = 0 overwrites d_mask, 1 ORs into it. */
+sf_status sf_threshold(sf_ctx *ctx, const float *d_filtered, const float *d_mean,
+                       const float *d_std, uint32_t *d_mask, int32_t accumulate, void *stream);
+
+/* The whole hot path for every filter of the bank: filter, window statistics,
+ * threshold, OR of the per-filter marks into d_mask (overwritten).  d_mean and
+ * d_std, when not NULL, receive the statistics of every filter
+ * ([n_filters][nwx][nwy][nwz]). */
+sf_status sf_detect(sf_ctx *ctx, const void *d_cube, uint32_t *d_mask, float *d_mean,
+                    float *d_std, void *stream);
+
+/* sf_detect from host memory: copies h_cube (storage dtype) to a device
+ * buffer the context owns, runs the hot path and copies the mask back into
+ * h_mask; returns after the mask is on the host.  Pinned host buffers make
+ * the copies asynchronous DMA; pageable ones work too. */
+sf_status sf_detect_host(sf_ctx *ctx, const void *h_cube, uint32_t *h_mask, void *stream);
+
+/* Stage timing (tracing).  While enabled, every sf_detect records CUDA
+ * events on its stream around each of its stages: stage 0 = the x pass
+ * launches, stage 1 = the fused window kernel (or the composed per-filter
+ * path).  sf_profile_read waits for the recorded events, returns per stage
+ * the summed milliseconds and the number of kernel launches since the last
+ * read, and clears the record.  ms and launches have n_stages entries. */
+sf_status sf_profile_enable(sf_ctx *ctx, int32_t enable);
+sf_status sf_profile_read(sf_ctx *ctx, double *ms, int64_t *launches, int32_t n_stages);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SF_H */

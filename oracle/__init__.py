@@ -93,6 +93,12 @@ def _load():
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                   ctypes.c_double, _u32p, _u32p, _dp, _dp, ctypes.c_int]
         lib.or_detect.restype = ctypes.c_int
+        lib.or_detect_windows.argtypes = [_fp, _i64, _i64, _i64, ctypes.c_int, _ip, _dp, _ip, _dp,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, _i64,
+                                          ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+        lib.or_detect_windows.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -276,6 +282,28 @@ def detect(d, bank, truncation, window, k, band_rel: float = 1e-4, nthreads: int
     if used < 0:
         raise MemoryError("oracle detect: out of memory")
     return {"mask": mask, "sure": sure, "mean": mean, "std": std, "threads": used}
+
+
+def detect_windows(d, bank, truncation, window, k, widx, band_rel: float = 1e-4,
+                   nthreads: int = 0):
+    """Whole method on a list of windows (n x 3 indices), in parallel.
+
+    Returns (fired voxels per window, OpenMP threads used).
+    """
+    d = _cube(d)
+    nx, ny, nz = d.shape
+    wx, wy, wz = window
+    rxy, gxy, rz, gz = _bank_arrays(bank, truncation)
+    idx = np.ascontiguousarray(np.asarray(widx, dtype=np.int64).reshape(-1, 3))
+    fired = np.zeros(idx.shape[0], dtype=np.int64)
+    used = _load().or_detect_windows(_ptr(d, _fp), nx, ny, nz, len(bank), _ptr(rxy, _ip),
+                                     _ptr(gxy, _dp), _ptr(rz, _ip), _ptr(gz, _dp), wx, wy, wz,
+                                     float(k), float(band_rel), idx.shape[0],
+                                     _ptr(idx, ctypes.POINTER(ctypes.c_int64)),
+                                     _ptr(fired, ctypes.POINTER(ctypes.c_int64)), int(nthreads))
+    if used < 0:
+        raise MemoryError("oracle detect_windows: out of memory")
+    return fired, used
 
 
 def pack_bits(bits) -> np.ndarray:

@@ -342,3 +342,57 @@ int or_detect(const float *d, int64_t nx, int64_t ny, int64_t nz,
     }
     return failed ? -1 : used;
 }
+
+/*
+ * A listed subset of windows through or_detect_window, in parallel over the
+ * list with nthreads OpenMP threads (<= 0: the runtime's default).  widx holds
+ * n (a, b, e) triples; fired[i] receives the number of voxels of window i that
+ * fire.  Used to time the oracle on a bounded sample of a large cube.
+ * Returns the number of threads used, or -1.
+ */
+int or_detect_windows(const float *d, int64_t nx, int64_t ny, int64_t nz,
+                      int nf, const int *rxy, const double *gxy_all,
+                      const int *rz, const double *gz_all,
+                      int wx, int wy, int wz, double k, double band_rel,
+                      int64_t n, const int64_t *widx, int64_t *fired, int nthreads)
+{
+    int used = 1, failed = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+    }
+#else
+    (void)nthreads;
+#endif
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < n; ++i) {
+        const size_t nvox = (size_t)wx * wy * wz;
+        uint8_t *fire = (uint8_t *)malloc(nvox), *sure = (uint8_t *)malloc(nvox);
+        double *m = (double *)malloc(sizeof(double) * (size_t)nf);
+        double *s = (double *)malloc(sizeof(double) * (size_t)nf);
+        int64_t cnt = -1;
+        if (fire && sure && m && s &&
+            or_detect_window(d, nx, ny, nz, nf, rxy, gxy_all, rz, gz_all, wx, wy, wz, k, band_rel,
+                             widx[3 * i], widx[3 * i + 1], widx[3 * i + 2], m, s, fire, sure,
+                             NULL, NULL) == 0) {
+            const int64_t x0 = widx[3 * i] * wx, y0 = widx[3 * i + 1] * wy, z0 = widx[3 * i + 2] * wz;
+            const int64_t ex = (x0 + wx < nx ? wx : nx - x0), ey = (y0 + wy < ny ? wy : ny - y0),
+                          ez = (z0 + wz < nz ? wz : nz - z0);
+            cnt = 0;
+            for (int64_t v = 0; v < ex * ey * ez; ++v) cnt += fire[v];
+        } else {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            failed = 1;
+        }
+        fired[i] = cnt;
+        free(fire); free(sure); free(m); free(s);
+    }
+    return failed ? -1 : used;
+}

@@ -1,0 +1,657 @@
+/*
+ * Device code of the Gaussian source-finder hot path, compiled at plan time
+ * for sm_103a by the host runtime.  The runtime prepends sf_kernel_abi.h and
+ * a prelude of #defines that fix the filter radii, window shape, storage type
+ * and launch shape of one plan, so every loop over filter taps is fully
+ * unrolled with the taps read from the kernel's parameter bank.
+ *
+ * Method (Westerlund & Harris): Eq. 2 convolution with a separable 3D
+ * Gaussian (x pass, then y and z passes), zero outside the cube; the local
+ * mean / standard deviation of each filtered cube over windows (Sec. 3.3);
+ * voxel selection c > mean + k*std; OR of the selections of all filters.
+ *
+ * Kernels (one per compiled program, chosen by the prelude):
+ *   SF_KERNEL_XPASS   sf_xpass      x pass for up to four sigma_xy at once.
+ *                                   Each thread owns V consecutive z of one
+ *                                   (y, z) lane and marches along x with a
+ *                                   register ring of the last 2R+1+PF planes,
+ *                                   so every input element is read once.
+ *   SF_KERNEL_DETECT  sf_yz_detect  one thread-block cluster per statistics
+ *                                   window; each CTA owns wx/C x-planes.  Per
+ *                                   input cube: cp.async-staged slab with y and
+ *                                   z halo -> y filter in shared memory -> z
+ *                                   filters in registers -> values kept in
+ *                                   shared memory + per-thread moments ->
+ *                                   Chan combine across warps and (through
+ *                                   distributed shared memory) across the
+ *                                   cluster -> threshold -> mask bits OR-ed in
+ *                                   registers; one packed store per word.
+ *   SF_KERNEL_FILTER  sf_yz_filter  y and z passes of one filter writing the
+ *                                   float32 filtered cube.
+ */
+
+typedef unsigned int u32;
+typedef unsigned short u16;
+typedef long long i64;
+typedef unsigned long long u64;
+
+template <class T> struct sf_is_f32 { static constexpr bool v = false; };
+template <> struct sf_is_f32<float> { static constexpr bool v = true; };
+
+template <class T> __device__ __forceinline__ float sf_dec16(u32 b);
+template <> __device__ __forceinline__ float sf_dec16<sf_f16>(u32 b)
+{
+    const u16 h = (u16)b;
+    float f;
+    asm("cvt.f32.f16 %0, %1;" : "=f"(f) : "h"(h));
+    return f;
+}
+template <> __device__ __forceinline__ float sf_dec16<sf_bf16>(u32 b)
+{
+    return __uint_as_float(b << 16);
+}
+template <class T> __device__ __forceinline__ u32 sf_enc16(float f);
+template <> __device__ __forceinline__ u32 sf_enc16<sf_f16>(float f)
+{
+    u16 h;
+    asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(f));
+    return (u32)h;
+}
+template <> __device__ __forceinline__ u32 sf_enc16<sf_bf16>(float f)
+{
+    u16 h;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(f));
+    return (u32)h;
+}
+
+/* N consecutive elements of storage type T -> float (GLOBAL: read-only path). */
+template <class T, int N, bool GLOBAL>
+__device__ __forceinline__ void sf_ld(const T *p, float *o)
+{
+    if constexpr (sf_is_f32<T>::v) {
+        if constexpr (N == 4) {
+            float4 v;
+            if constexpr (GLOBAL) v = __ldg(reinterpret_cast<const float4 *>(p));
+            else v = *reinterpret_cast<const float4 *>(p);
+            o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+        } else if constexpr (N == 2) {
+            float2 v;
+            if constexpr (GLOBAL) v = __ldg(reinterpret_cast<const float2 *>(p));
+            else v = *reinterpret_cast<const float2 *>(p);
+            o[0] = v.x; o[1] = v.y;
+        } else {
+            static_assert(N == 1, "vector width");
+            if constexpr (GLOBAL) o[0] = __ldg(reinterpret_cast<const float *>(p));
+            else o[0] = *reinterpret_cast<const float *>(p);
+        }
+    } else {
+        if constexpr (N == 8) {
+            uint4 v;
+            if constexpr (GLOBAL) v = __ldg(reinterpret_cast<const uint4 *>(p));
+            else v = *reinterpret_cast<const uint4 *>(p);
+            o[0] = sf_dec16<T>(v.x & 0xffffu); o[1] = sf_dec16<T>(v.x >> 16);
+            o[2] = sf_dec16<T>(v.y & 0xffffu); o[3] = sf_dec16<T>(v.y >> 16);
+            o[4] = sf_dec16<T>(v.z & 0xffffu); o[5] = sf_dec16<T>(v.z >> 16);
+            o[6] = sf_dec16<T>(v.w & 0xffffu); o[7] = sf_dec16<T>(v.w >> 16);
+        } else if constexpr (N == 4) {
+            uint2 v;
+            if constexpr (GLOBAL) v = __ldg(reinterpret_cast<const uint2 *>(p));
+            else v = *reinterpret_cast<const uint2 *>(p);
+            o[0] = sf_dec16<T>(v.x & 0xffffu); o[1] = sf_dec16<T>(v.x >> 16);
+            o[2] = sf_dec16<T>(v.y & 0xffffu); o[3] = sf_dec16<T>(v.y >> 16);
+        } else if constexpr (N == 2) {
+            u32 v;
+            if constexpr (GLOBAL) v = __ldg(reinterpret_cast<const unsigned int *>(p));
+            else v = *reinterpret_cast<const unsigned int *>(p);
+            o[0] = sf_dec16<T>(v & 0xffffu); o[1] = sf_dec16<T>(v >> 16);
+        } else {
+            static_assert(N == 1, "vector width");
+            u16 v;
+            if constexpr (GLOBAL) v = __ldg(reinterpret_cast<const unsigned short *>(p));
+            else v = *reinterpret_cast<const unsigned short *>(p);
+            o[0] = sf_dec16<T>((u32)v);
+        }
+    }
+}
+
+/* N floats -> N consecutive elements of storage type T (round to nearest). */
+template <class T, int N>
+__device__ __forceinline__ void sf_st(T *p, const float *v)
+{
+    if constexpr (sf_is_f32<T>::v) {
+        if constexpr (N == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        else if constexpr (N == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+        else *reinterpret_cast<float *>(p) = v[0];
+    } else {
+        if constexpr (N == 8) {
+            uint4 w;
+            w.x = sf_enc16<T>(v[0]) | (sf_enc16<T>(v[1]) << 16);
+            w.y = sf_enc16<T>(v[2]) | (sf_enc16<T>(v[3]) << 16);
+            w.z = sf_enc16<T>(v[4]) | (sf_enc16<T>(v[5]) << 16);
+            w.w = sf_enc16<T>(v[6]) | (sf_enc16<T>(v[7]) << 16);
+            *reinterpret_cast<uint4 *>(p) = w;
+        } else if constexpr (N == 4) {
+            uint2 w;
+            w.x = sf_enc16<T>(v[0]) | (sf_enc16<T>(v[1]) << 16);
+            w.y = sf_enc16<T>(v[2]) | (sf_enc16<T>(v[3]) << 16);
+            *reinterpret_cast<uint2 *>(p) = w;
+        } else if constexpr (N == 2) {
+            *reinterpret_cast<unsigned int *>(p) = sf_enc16<T>(v[0]) | (sf_enc16<T>(v[1]) << 16);
+        } else {
+            *reinterpret_cast<unsigned short *>(p) = (unsigned short)sf_enc16<T>(v[0]);
+        }
+    }
+}
+
+/* ======================================================================= */
+#ifdef SF_KERNEL_XPASS
+/* Prelude: SFX_NOUT, SFX_R0..SFX_R3 (radii, 0 = unused), SFX_RM (max radius), SFX_PF (prefetch
+ * depth), SFX_V (elements per lane), SFX_THREADS, typedef sfx_t. */
+struct sfx_taps { float g[SFX_NOUT][SFX_RM + 1]; };   /* g[k][|o|] */
+__host__ __device__ constexpr int sfx_r(int k)
+{
+    return k == 0 ? SFX_R0 : k == 1 ? SFX_R1 : k == 2 ? SFX_R2 : SFX_R3;
+}
+
+extern "C" __global__ void __launch_bounds__(SFX_THREADS)
+sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
+{
+    constexpr int RM = SFX_RM, V = SFX_V, K = 2 * RM + 1 + SFX_PF;
+    const i64 lane = (i64)blockIdx.x * SFX_THREADS + threadIdx.x;
+    if (lane >= a.lanes) return;
+    const i64 xb = (i64)blockIdx.y * a.xseg;
+    const i64 xe = min(a.nx, xb + a.xseg);
+    const i64 xlim = min(a.nx, xe + RM);            /* inputs used: [xb-RM, xe+RM) */
+    const sfx_t *__restrict__ p = reinterpret_cast<const sfx_t *>(a.src) + lane * V;
+
+    /* slot i of the ring holds input plane xb-RM+i (mod K) */
+    float ring[K][V];
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const i64 xi = xb - RM + i;
+        if (xi >= 0 && xi < xlim) sf_ld<sfx_t, V, true>(p + xi * a.plane, ring[i]);
+        else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) ring[i][v] = 0.f;
+        }
+    }
+    for (i64 x0 = xb; x0 < xe; x0 += K) {
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const i64 x = x0 + u;
+            if (x < xe) {
+                /* symmetric taps: pair sums shared by all outputs */
+                float ps[RM + 1][V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) ps[0][v] = ring[(u + RM) % K][v];
+#pragma unroll
+                for (int j = 1; j <= RM; ++j)
+#pragma unroll
+                    for (int v = 0; v < V; ++v)
+                        ps[j][v] = ring[(u + RM - j) % K][v] + ring[(u + RM + j) % K][v];
+#pragma unroll
+                for (int k = 0; k < SFX_NOUT; ++k) {
+                    float acc[V];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] = t.g[k][0] * ps[0][v];
+#pragma unroll
+                    for (int j = 1; j <= sfx_r(k); ++j)
+#pragma unroll
+                        for (int v = 0; v < V; ++v) acc[v] = fmaf(t.g[k][j], ps[j][v], acc[v]);
+                    sf_st<sfx_t, V>(reinterpret_cast<sfx_t *>(a.dst[k]) + x * a.plane + lane * V, acc);
+                }
+                /* slot u is free: refill it with plane x - RM + K */
+                const i64 xi = x - RM + K;
+                if (xi < xlim) sf_ld<sfx_t, V, true>(p + xi * a.plane, ring[u]);
+                else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) ring[u][v] = 0.f;
+                }
+            }
+        }
+    }
+}
+#endif /* SF_KERNEL_XPASS */
+
+/* ======================================================================= */
+#if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_FILTER)
+/* Prelude: SFD_WY, SFD_WZ (tile of one plane), SFD_THREADS (= WY*WZ/8),
+ * SFD_NSRC, SFD_NZF, SFD_RYM, SFD_RZM, SFD_HZ (z halo, multiple of SFD_CH),
+ * SFD_CH (elements per cp.async, 0 = synchronous element loads), SFD_SROW,
+ * SFD_UROW, SFD_PY, SFD_SOURCES(X) with X(index, RY, NZ, RZ0, RZ1),
+ * typedef sfd_t; DETECT adds SFD_C, SFD_PL and the shared-memory offsets. */
+
+constexpr int SFD_UW = SFD_WZ + 2 * SFD_HZ;   /* staged columns: z0-HZ .. z0+WZ+HZ */
+constexpr int SFD_NWARP = SFD_THREADS / 32;
+
+struct sfd_taps {
+    float gy[SFD_NSRC][SFD_RYM + 1];             /* y taps by |offset| */
+    float gz[SFD_NSRC][SFD_NZF][SFD_RZM + 1];    /* z taps by |offset| */
+};
+
+__device__ __forceinline__ u32 sf_smem_addr(const void *p)
+{
+    return (u32)__cvta_generic_to_shared(p);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void sf_cp_async(u32 dst, const void *src, u32 n)
+{
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src),
+                     "n"(BYTES), "r"(n)
+                     : "memory");
+}
+__device__ __forceinline__ void sf_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void sf_cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+/* Stage rows y0-RY .. y0+WY+RY-1 and columns z0-HZ .. z0+WZ+HZ-1 of plane x
+ * of `src` into `slab` (row stride SFD_SROW); zeros outside the cube. */
+template <int RY>
+__device__ __forceinline__ void sfd_load_slab(sfd_t *slab, const sfd_t *__restrict__ src, i64 x,
+                                              i64 y0, i64 z0, i64 nx, i64 ny, i64 nz)
+{
+    constexpr int ROWS = SFD_WY + 2 * RY;
+    const bool xin = x >= 0 && x < nx;
+    if constexpr (SFD_CH > 0) {
+        constexpr int NCH = SFD_UW / SFD_CH;
+        constexpr int BYTES = SFD_CH * (int)sizeof(sfd_t);
+        for (int i = threadIdx.x; i < ROWS * NCH; i += SFD_THREADS) {
+            const int r = i / NCH, ch = i - r * NCH;
+            const i64 y = y0 - RY + r;
+            const i64 z = z0 - SFD_HZ + (i64)ch * SFD_CH;
+            const bool in = xin && y >= 0 && y < ny && z >= 0 && z + SFD_CH <= nz;
+            const sfd_t *g = in ? src + ((x * ny + y) * nz + z) : src;
+            sf_cp_async<BYTES>(sf_smem_addr(slab + r * SFD_SROW + ch * SFD_CH), g, in ? BYTES : 0u);
+        }
+    } else {
+        /* element loads for 16-bit storage with an odd nz (no 4-byte chunks) */
+        for (int i = threadIdx.x; i < ROWS * SFD_UW; i += SFD_THREADS) {
+            const int r = i / SFD_UW, c = i - r * SFD_UW;
+            const i64 y = y0 - RY + r;
+            const i64 z = z0 - SFD_HZ + c;
+            sfd_t v;
+            if (xin && y >= 0 && y < ny && z >= 0 && z < nz) v = src[(x * ny + y) * nz + z];
+            else *reinterpret_cast<u16 *>(&v) = 0;
+            slab[r * SFD_SROW + c] = v;
+        }
+    }
+}
+
+/* U[y][c] = sum_j gy[|j|] slab[y + RY + j][c] for the WY output rows and all
+ * SFD_UW staged columns (the z halo is needed by the z pass). */
+template <int SI, int RY>
+__device__ __forceinline__ void sfd_yfilter(const sfd_t *slab, float *U, const sfd_taps &t)
+{
+    constexpr int NQ = SFD_UW / 4;
+    constexpr int NRB = SFD_WY / SFD_PY;
+    for (int task = threadIdx.x; task < NRB * NQ; task += SFD_THREADS) {
+        const int rb = task / NQ, q = task - rb * NQ;
+        float acc[SFD_PY][4];
+#pragma unroll
+        for (int i = 0; i < SFD_PY; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[i][c] = 0.f;
+#pragma unroll
+        for (int r = 0; r < SFD_PY + 2 * RY; ++r) {
+            float v[4];
+            sf_ld<sfd_t, 4, false>(slab + (rb * SFD_PY + r) * SFD_SROW + 4 * q, v);
+#pragma unroll
+            for (int i = 0; i < SFD_PY; ++i) {
+                const int j = r - i;   /* slab row r feeds output row i at offset j-RY */
+                if (j >= 0 && j <= 2 * RY) {
+                    const float g = t.gy[SI][j >= RY ? j - RY : RY - j];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[i][c] = fmaf(g, v[c], acc[i][c]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < SFD_PY; ++i) sf_st<float, 4>(U + (rb * SFD_PY + i) * SFD_UROW + 4 * q, acc[i]);
+    }
+}
+
+__host__ __device__ constexpr int sfd_max4(int a, int b, int c, int d)
+{
+    return (a > b ? a : b) > (c > d ? c : d) ? (a > b ? a : b) : (c > d ? c : d);
+}
+__host__ __device__ constexpr int sfd_pick(int f, int a, int b, int c, int d)
+{
+    return f == 0 ? a : f == 1 ? b : f == 2 ? c : d;
+}
+
+/* Eight consecutive z outputs (z0 + 8*chunk .. +7) of row `row` for the NZ
+ * spectral filters of input SI: c[f][i] = sum_o gz_f[|o|] u[z + o]. */
+template <int SI, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
+__device__ __forceinline__ void sfd_zfilter(const sfd_t *slab, const float *U, int row, int chunk,
+                                            float (&c)[SFD_NZF][8], const sfd_taps &t)
+{
+    constexpr int RZM = sfd_max4(RZ0, RZ1, RZ2, RZ3);
+    constexpr int LO = (SFD_HZ - RZM) & ~3;      /* first staged column used (aligned) */
+    constexpr int HI = SFD_HZ + 7 + RZM;          /* last staged column used */
+    constexpr int NQ = (HI - LO) / 4 + 1;
+    float in[NQ * 4];
+    if constexpr (RY > 0) {
+        const float *p = U + row * SFD_UROW + 8 * chunk + LO;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sf_ld<float, 4, false>(p + 4 * q, in + 4 * q);
+    } else {
+        const sfd_t *p = slab + row * SFD_SROW + 8 * chunk + LO;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sf_ld<sfd_t, 4, false>(p + 4 * q, in + 4 * q);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int ci = SFD_HZ + i - LO;
+        float ps[RZM + 1];
+        ps[0] = in[ci];
+#pragma unroll
+        for (int j = 1; j <= RZM; ++j) ps[j] = in[ci - j] + in[ci + j];
+#pragma unroll
+        for (int f = 0; f < NZ; ++f) {
+            float acc = t.gz[SI][f][0] * ps[0];
+#pragma unroll
+            for (int j = 1; j <= sfd_pick(f, RZ0, RZ1, RZ2, RZ3); ++j)
+                acc = fmaf(t.gz[SI][f][j], ps[j], acc);
+            c[f][i] = acc;
+        }
+    }
+}
+#endif
+
+/* ======================================================================= */
+#ifdef SF_KERNEL_DETECT
+
+constexpr int SFD_SLAB_STRIDE = (SFD_OFF_SLAB1 - SFD_OFF_SLAB0) / (int)sizeof(sfd_t);
+
+/* running (count, mean, M2) of a set of values; Chan et al. pairwise update */
+struct sfd_mom { float n, mean, m2; };
+
+__device__ __forceinline__ sfd_mom sfd_merge(sfd_mom a, sfd_mom b)
+{
+    if (b.n == 0.f) return a;
+    if (a.n == 0.f) return b;
+    const float n = a.n + b.n;
+    const float d = b.mean - a.mean;
+    const float wb = b.n / n;
+    sfd_mom r;
+    r.n = n;
+    r.mean = fmaf(d, wb, a.mean);
+    r.m2 = a.m2 + b.m2 + d * d * a.n * wb;
+    return r;
+}
+
+__device__ __forceinline__ u32 sfd_cluster_rank()
+{
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ u32 sfd_map_rank(u32 saddr, u32 rank)
+{
+    u32 r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void sfd_st_cluster(u32 addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ float sfd_ld_cluster(u32 addr)
+{
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sfd_cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+struct sfd_state {
+    sfd_t *slab0;   /* two slab buffers, SFD_SLAB_STRIDE elements apart */
+    float *U;
+    float4 *cbuf;   /* [PL][NZF][2][THREADS] */
+    float *wred;    /* [NWARP][NZF][3] */
+    float *clus;    /* [NSRC][C][NZF][3], used in rank 0 */
+    float *thr;     /* [NZF] */
+    i64 x0, y0, z0;
+    int npl, wid, row, chunk;
+    u32 rank, vmask;
+    int it;
+    u64 mbits;
+};
+
+/* issue the slab load of input s, plane p into buffer (it & 1) */
+__device__ __forceinline__ void sfd_issue(const sf_dargs &a, sfd_state &S, int s, int p, int it)
+{
+    sfd_t *dst = S.slab0 + (it & 1) * SFD_SLAB_STRIDE;
+    switch (s) {
+#define SFD_ISSUE_CASE(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                         \
+    case IDX:                                                                                    \
+        sfd_load_slab<RY>(dst, reinterpret_cast<const sfd_t *>(a.src[IDX]), S.x0 + p, S.y0, S.z0, \
+                          a.nx, a.ny, a.nz);                                                     \
+        break;
+        SFD_SOURCES(SFD_ISSUE_CASE)
+#undef SFD_ISSUE_CASE
+    default:
+        break;
+    }
+}
+
+template <int SI, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
+__device__ __forceinline__ void sfd_run_source(const sf_dargs &a, const sfd_taps &t, sfd_state &S)
+{
+    sfd_mom acc[NZ];
+#pragma unroll
+    for (int f = 0; f < NZ; ++f) acc[f] = sfd_mom{0.f, 0.f, 0.f};
+
+    for (int p = 0; p < S.npl; ++p) {
+        /* prefetch the next item: next plane, or the first plane of the next input */
+        if (p + 1 < S.npl) sfd_issue(a, S, SI, p + 1, S.it + 1);
+        else if (SI + 1 < SFD_NSRC) sfd_issue(a, S, SI + 1, 0, S.it + 1);
+        sf_cp_commit();
+        sf_cp_wait<1>();
+        __syncthreads();
+        const sfd_t *slab = S.slab0 + (S.it & 1) * SFD_SLAB_STRIDE;
+        if constexpr (RY > 0) {
+            sfd_yfilter<SI, RY>(slab, S.U, t);
+            __syncthreads();
+        }
+        float c[SFD_NZF][8];
+        sfd_zfilter<SI, RY, NZ, RZ0, RZ1, RZ2, RZ3>(slab, S.U, S.row, S.chunk, c, t);
+#pragma unroll
+        for (int f = 0; f < NZ; ++f) {
+            /* moments of this thread's eight values, two passes in registers */
+            float s = 0.f, nv = 0.f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (S.vmask & (1u << i)) { s += c[f][i]; nv += 1.f; }
+            if (nv > 0.f) {
+                const float m = s / nv;
+                float q = 0.f;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (S.vmask & (1u << i)) { const float d = c[f][i] - m; q = fmaf(d, d, q); }
+                acc[f] = sfd_merge(acc[f], sfd_mom{nv, m, q});
+            }
+            float4 *cb = S.cbuf + ((p * SFD_NZF + f) * 2) * SFD_THREADS + threadIdx.x;
+            cb[0] = make_float4(c[f][0], c[f][1], c[f][2], c[f][3]);
+            cb[SFD_THREADS] = make_float4(c[f][4], c[f][5], c[f][6], c[f][7]);
+        }
+        __syncthreads();
+        ++S.it;
+    }
+
+    /* statistics: warp butterfly, then warps in order, then cluster ranks in order */
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int f = 0; f < NZ; ++f) {
+        sfd_mom m = acc[f];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            sfd_mom o;
+            o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
+            o.mean = __shfl_xor_sync(0xffffffffu, m.mean, off);
+            o.m2 = __shfl_xor_sync(0xffffffffu, m.m2, off);
+            m = (lane & off) ? sfd_merge(o, m) : sfd_merge(m, o);
+        }
+        if (lane == 0) {
+            float *w = S.wred + (warp * SFD_NZF + f) * 3;
+            w[0] = m.n; w[1] = m.mean; w[2] = m.m2;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NZ) {
+        const int f = threadIdx.x;
+        sfd_mom m{0.f, 0.f, 0.f};
+        for (int w = 0; w < SFD_NWARP; ++w) {
+            const float *q = S.wred + (w * SFD_NZF + f) * 3;
+            m = sfd_merge(m, sfd_mom{q[0], q[1], q[2]});
+        }
+        const u32 slot = sf_smem_addr(S.clus + ((SI * SFD_C + (int)S.rank) * SFD_NZF + f) * 3);
+        const u32 remote = sfd_map_rank(slot, 0);
+        sfd_st_cluster(remote, m.n);
+        sfd_st_cluster(remote + 4, m.mean);
+        sfd_st_cluster(remote + 8, m.m2);
+    }
+    sfd_cluster_sync();
+    if (threadIdx.x < NZ) {
+        const int f = threadIdx.x;
+        sfd_mom m{0.f, 0.f, 0.f};
+        for (int r = 0; r < SFD_C; ++r) {
+            const u32 remote = sfd_map_rank(sf_smem_addr(S.clus + ((SI * SFD_C + r) * SFD_NZF + f) * 3), 0);
+            m = sfd_merge(m, sfd_mom{sfd_ld_cluster(remote), sfd_ld_cluster(remote + 4),
+                                     sfd_ld_cluster(remote + 8)});
+        }
+        const float sd = m.n > 0.f ? sqrtf(m.m2 / m.n) : 0.f;
+        S.thr[f] = fmaf(a.k, sd, m.mean);
+        if (S.rank == 0 && a.mean != nullptr) {
+            const i64 o = (i64)a.fidx[SI][f] * a.nwin + S.wid;
+            a.mean[o] = m.mean;
+            a.stdv[o] = sd;
+        }
+    }
+    __syncthreads();
+
+    /* threshold the values kept in shared memory */
+    for (int p = 0; p < S.npl; ++p) {
+        u32 bits = 0;
+#pragma unroll
+        for (int f = 0; f < NZ; ++f) {
+            const float T = S.thr[f];
+            const float4 *cb = S.cbuf + ((p * SFD_NZF + f) * 2) * SFD_THREADS + threadIdx.x;
+            const float4 lo = cb[0], hi = cb[SFD_THREADS];
+            bits |= (lo.x > T ? 1u : 0u) | (lo.y > T ? 2u : 0u) | (lo.z > T ? 4u : 0u) |
+                    (lo.w > T ? 8u : 0u) | (hi.x > T ? 16u : 0u) | (hi.y > T ? 32u : 0u) |
+                    (hi.z > T ? 64u : 0u) | (hi.w > T ? 128u : 0u);
+        }
+        S.mbits |= (u64)(bits & S.vmask) << (8 * p);
+    }
+}
+
+extern "C" __global__ void __cluster_dims__(SFD_C, 1, 1) __launch_bounds__(SFD_THREADS, 1)
+sf_yz_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_taps t)
+{
+    extern __shared__ __align__(128) unsigned char sfd_sm[];
+    sfd_state S;
+    S.slab0 = reinterpret_cast<sfd_t *>(sfd_sm + SFD_OFF_SLAB0);
+    S.U = reinterpret_cast<float *>(sfd_sm + SFD_OFF_U);
+    S.cbuf = reinterpret_cast<float4 *>(sfd_sm + SFD_OFF_CBUF);
+    S.wred = reinterpret_cast<float *>(sfd_sm + SFD_OFF_WRED);
+    S.clus = reinterpret_cast<float *>(sfd_sm + SFD_OFF_CLUS);
+    S.thr = reinterpret_cast<float *>(sfd_sm + SFD_OFF_THR);
+
+    S.rank = sfd_cluster_rank();
+    S.wid = (int)(blockIdx.x / SFD_C);
+    const int wz = S.wid % a.nwz, wy = (S.wid / a.nwz) % a.nwy, wx = S.wid / (a.nwz * a.nwy);
+    S.x0 = (i64)wx * (SFD_C * SFD_PL) + (i64)S.rank * SFD_PL;
+    S.y0 = (i64)wy * SFD_WY;
+    S.z0 = (i64)wz * SFD_WZ;
+    const i64 left = a.nx - S.x0;
+    S.npl = left <= 0 ? 0 : (left < SFD_PL ? (int)left : SFD_PL);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int RG = SFD_WY / 8;
+    S.row = (warp % RG) * 8 + (lane & 7);
+    S.chunk = (warp / RG) * 4 + (lane >> 3);
+    const bool rowv = S.y0 + S.row < a.ny;
+    const i64 zb = S.z0 + 8 * S.chunk;
+    S.vmask = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        if (rowv && zb + i < a.nz) S.vmask |= 1u << i;
+    S.mbits = 0;
+    S.it = 0;
+
+    if (S.npl > 0) sfd_issue(a, S, 0, 0, 0);
+    sf_cp_commit();
+
+#define SFD_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3) sfd_run_source<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(a, t, S);
+    SFD_SOURCES(SFD_RUN)
+#undef SFD_RUN
+
+    /* mask words: lanes l, l^8, l^16, l^24 hold 8-voxel pieces of one 32-z word */
+    for (int p = 0; p < S.npl; ++p) {
+        u32 piece = (u32)((S.mbits >> (8 * p)) & 0xffu) << (8 * (lane >> 3));
+        piece |= __shfl_xor_sync(0xffffffffu, piece, 8);
+        piece |= __shfl_xor_sync(0xffffffffu, piece, 16);
+        const i64 wz32 = zb >> 5;
+        if ((lane >> 3) == 0 && rowv && wz32 < a.nw32)
+            a.mask[((S.x0 + p) * a.ny + S.y0 + S.row) * a.nw32 + wz32] = piece;
+    }
+    /* keep this CTA's shared memory alive until every rank has read rank 0's slots */
+    sfd_cluster_sync();
+}
+#endif /* SF_KERNEL_DETECT */
+
+/* ======================================================================= */
+#ifdef SF_KERNEL_FILTER
+/* one CTA per (x, y tile, z tile): y and z passes of a single filter */
+extern "C" __global__ void __launch_bounds__(SFD_THREADS)
+sf_yz_filter(const __grid_constant__ sf_fargs a, const __grid_constant__ sfd_taps t)
+{
+    extern __shared__ __align__(128) unsigned char sff_sm[];
+    sfd_t *slab = reinterpret_cast<sfd_t *>(sff_sm);
+    float *U = reinterpret_cast<float *>(sff_sm + SFD_OFF_U);
+    const i64 x = blockIdx.x;
+    const i64 y0 = (i64)blockIdx.y * SFD_WY, z0 = (i64)blockIdx.z * SFD_WZ;
+    const sfd_t *src = reinterpret_cast<const sfd_t *>(a.src);
+#define SFF_LOAD(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3) sfd_load_slab<RY>(slab, src, x, y0, z0, a.nx, a.ny, a.nz);
+    SFD_SOURCES(SFF_LOAD)
+#undef SFF_LOAD
+    sf_cp_commit();
+    sf_cp_wait<0>();
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int RG = SFD_WY / 8;
+    const int row = (warp % RG) * 8 + (lane & 7);
+    const int chunk = (warp / RG) * 4 + (lane >> 3);
+    float c[SFD_NZF][8];
+#define SFF_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                \
+    if constexpr (RY > 0) {                                                     \
+        sfd_yfilter<IDX, RY>(slab, U, t);                                       \
+        __syncthreads();                                                        \
+    }                                                                           \
+    sfd_zfilter<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(slab, U, row, chunk, c, t);
+    SFD_SOURCES(SFF_RUN)
+#undef SFF_RUN
+    const i64 y = y0 + row, zb = z0 + 8 * chunk;
+    if (y >= a.ny) return;
+    float *out = a.out + (x * a.ny + y) * a.nz + zb;
+    if (zb + 8 <= a.nz && (a.nz & 3) == 0) {
+        sf_st<float, 4>(out, c[0]);
+        sf_st<float, 4>(out + 4, c[0] + 4);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (zb + i < a.nz) out[i] = c[0][i];
+    }
+}
+#endif /* SF_KERNEL_FILTER */

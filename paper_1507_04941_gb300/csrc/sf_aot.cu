@@ -1,0 +1,133 @@
+/*
+ * Kernels compiled ahead of time (their shape does not depend on the filter
+ * radii): window statistics of a filtered cube and the threshold / mask
+ * packing of one filtered cube.  Both back the step-by-step entry points
+ * sf_stats and sf_threshold and the composed path of sf_detect.
+ */
+#include <cuda_runtime.h>
+
+namespace {
+
+typedef long long i64;
+
+struct Mom {
+    float n, mean, m2;
+};
+
+__device__ __forceinline__ Mom merge(Mom a, Mom b)
+{
+    if (b.n == 0.f) return a;
+    if (a.n == 0.f) return b;
+    const float n = a.n + b.n;
+    const float d = b.mean - a.mean;
+    const float wb = b.n / n;
+    return Mom{n, fmaf(d, wb, a.mean), a.m2 + b.m2 + d * d * a.n * wb};
+}
+
+constexpr int kStatThreads = 256;
+
+/* Window mean and population standard deviation (Sec. 3.3): one CTA per
+ * window.  Each thread sums its values shifted by its first value, the
+ * per-thread moments are merged pairwise (Chan et al.) across the warp and
+ * then across warps in a fixed order. */
+__global__ void __launch_bounds__(kStatThreads)
+sf_window_stats_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int wx, int wy, int wz,
+                       int nwy, int nwz, float *__restrict__ mean, float *__restrict__ stdv)
+{
+    __shared__ float red[kStatThreads / 32][3];
+    const int w = blockIdx.x;
+    const int a = w / (nwy * nwz), b = (w / nwz) % nwy, e = w % nwz;
+    const i64 x0 = (i64)a * wx, y0 = (i64)b * wy, z0 = (i64)e * wz;
+    const int ex = (int)min((i64)wx, nx - x0), ey = (int)min((i64)wy, ny - y0),
+              ez = (int)min((i64)wz, nz - z0);
+    const i64 n = (i64)ex * ey * ez;
+    float K = 0.f, s1 = 0.f, s2 = 0.f, cnt = 0.f;
+    for (i64 i = threadIdx.x; i < n; i += kStatThreads) {
+        const int dz = (int)(i % ez);
+        const i64 r = i / ez;
+        const int dy = (int)(r % ey), dx = (int)(r / ey);
+        const float v = __ldg(c + ((x0 + dx) * ny + (y0 + dy)) * nz + (z0 + dz));
+        if (cnt == 0.f) K = v;
+        const float d = v - K;
+        s1 += d;
+        s2 = fmaf(d, d, s2);
+        cnt += 1.f;
+    }
+    Mom m{0.f, 0.f, 0.f};
+    if (cnt > 0.f) {
+        const float mu = s1 / cnt;
+        m = Mom{cnt, K + mu, fmaxf(s2 - s1 * mu, 0.f)};
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        Mom o{__shfl_xor_sync(0xffffffffu, m.n, off), __shfl_xor_sync(0xffffffffu, m.mean, off),
+              __shfl_xor_sync(0xffffffffu, m.m2, off)};
+        m = (lane & off) ? merge(o, m) : merge(m, o);
+    }
+    if (lane == 0) {
+        red[warp][0] = m.n;
+        red[warp][1] = m.mean;
+        red[warp][2] = m.m2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Mom t{0.f, 0.f, 0.f};
+        for (int q = 0; q < kStatThreads / 32; ++q) t = merge(t, Mom{red[q][0], red[q][1], red[q][2]});
+        mean[w] = t.mean;
+        stdv[w] = t.n > 0.f ? sqrtf(t.m2 / t.n) : 0.f;
+    }
+}
+
+constexpr int kThrThreads = 256;
+
+/* One warp per mask word: lane l tests voxel z = 32*word_z + l against
+ * mean + k*std of its window and the warp ballot is the word. */
+__global__ void __launch_bounds__(kThrThreads)
+sf_threshold_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int wx, int wy, int wz,
+                    int nwy, int nwz, const float *__restrict__ mean, const float *__restrict__ stdv,
+                    float k, unsigned int *__restrict__ mask, int accumulate, i64 nw32, i64 nwords)
+{
+    const i64 word = (i64)blockIdx.x * (kThrThreads / 32) + (threadIdx.x >> 5);
+    if (word >= nwords) return;
+    const int lane = threadIdx.x & 31;
+    const i64 xy = word / nw32, zw = word % nw32;
+    const i64 x = xy / ny, y = xy % ny;
+    const i64 z = zw * 32 + lane;
+    bool fire = false;
+    if (z < nz) {
+        const float v = __ldg(c + xy * nz + z);
+        const i64 wi = ((x / wx) * nwy + y / wy) * nwz + z / wz;
+        const float T = fmaf(k, __ldg(stdv + wi), __ldg(mean + wi));
+        fire = v > T;
+    }
+    const unsigned int bits = __ballot_sync(0xffffffffu, fire);
+    if (lane == 0) mask[word] = accumulate ? (mask[word] | bits) : bits;
+}
+
+}  // namespace
+
+cudaError_t sf_launch_stats(const float *c, long long nx, long long ny, long long nz, int wx, int wy,
+                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv,
+                            cudaStream_t st)
+{
+    const long long nwin = (long long)nwx * nwy * nwz;
+    sf_window_stats_kernel<<<(unsigned)nwin, kStatThreads, 0, st>>>(c, nx, ny, nz, wx, wy, wz, nwy,
+                                                                     nwz, mean, stdv);
+    return cudaGetLastError();
+}
+
+cudaError_t sf_launch_threshold(const float *c, long long nx, long long ny, long long nz, int wx,
+                                int wy, int wz, int nwy, int nwz, const float *mean,
+                                const float *stdv, float k, unsigned int *mask, int accumulate,
+                                cudaStream_t st)
+{
+    const long long nw32 = (nz + 31) / 32;
+    const long long nwords = nx * ny * nw32;
+    const long long per = kThrThreads / 32;
+    const long long blocks = (nwords + per - 1) / per;
+    sf_threshold_kernel<<<(unsigned)blocks, kThrThreads, 0, st>>>(c, nx, ny, nz, wx, wy, wz, nwy, nwz,
+                                                                   mean, stdv, k, mask, accumulate,
+                                                                   nw32, nwords);
+    return cudaGetLastError();
+}

@@ -1,0 +1,48 @@
+/*
+ * Parameter blocks shared by the host runtime and the kernels it compiles at
+ * run time.  The same text is compiled into the host library and prepended to
+ * the run-time kernel source, so both sides see one layout.
+ */
+#ifndef SF_KERNEL_ABI_H
+#define SF_KERNEL_ABI_H
+
+#define SF_MAX_SRC 8   /* inputs of the fused kernel: the cube and x-filtered cubes */
+#define SF_MAX_NZF 4   /* spectral filters per input in the fused kernel */
+#define SF_MAX_XOUT 4  /* outputs of one x-pass launch */
+
+/* 16-bit storage types of the cube and the x-filtered scratch cubes */
+struct sf_f16 { unsigned short b; };   /* IEEE binary16 */
+struct sf_bf16 { unsigned short b; };  /* bfloat16 */
+
+/* x pass: dst[k][x][y][z] = sum_o g_k[|o|] src[x+o][y][z]; lanes run over the
+ * y-z plane in groups of V elements. */
+struct sf_xargs {
+    const void *src;
+    void *dst[SF_MAX_XOUT];
+    long long nx;
+    long long plane;   /* ny * nz */
+    long long lanes;   /* plane / V */
+    long long xseg;    /* x positions per grid row */
+};
+
+/* fused y/z filter + window statistics + threshold + mask union */
+struct sf_dargs {
+    const void *src[SF_MAX_SRC];
+    unsigned int *mask;
+    float *mean;       /* [n_filters][nwin] or null */
+    float *stdv;       /* [n_filters][nwin] or null */
+    int fidx[SF_MAX_SRC][SF_MAX_NZF];
+    long long nx, ny, nz, nw32;
+    int nwx, nwy, nwz, nwin;
+    float k;
+    int pad_;
+};
+
+/* y/z filter of one filter, writing float32 filtered values */
+struct sf_fargs {
+    const void *src;
+    float *out;
+    long long nx, ny, nz;
+};
+
+#endif

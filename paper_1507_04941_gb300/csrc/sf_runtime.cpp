@@ -1,0 +1,1011 @@
+/*
+ * Host runtime of the GB300 Gaussian source-finder library: the C ABI of
+ * include/sf.h, the per-context plan (taps, radii, inputs of the fused kernel,
+ * launch shapes, shared-memory layout), run-time compilation of the kernels
+ * for the exact radii of the filter bank, and the launches.
+ *
+ * Plan of sf_detect for a bank of filters (sigma_xy, sigma_z):
+ *   1. x pass (Eq. 2 factor along x) once per distinct non-zero sigma_xy into
+ *      a scratch cube the context owns; one launch handles up to four sigmas
+ *      and reads the cube once;
+ *   2. one fused launch: per statistics window a cluster of CTAs filters the
+ *      inputs (the cube itself for sigma_xy = 0, the scratch cubes otherwise)
+ *      along y and z for every filter, forms the window mean and standard
+ *      deviation (Sec. 3.3), applies c > mean + k*std and writes the OR of
+ *      all filters into the packed mask.
+ * Windows whose shape the fused kernel cannot tile (wy % 8, wz % 32, thread
+ * or shared-memory limits) run the composed path: per filter sf_filter into a
+ * scratch cube, sf_stats, sf_threshold accumulating the mask.
+ */
+#include "sf.h"
+#include "sf_kernel_abi.h"
+
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+extern "C" const char *sf_embedded_kernel_source;   /* sf_kernels.cuh (generated) */
+extern "C" const char *sf_embedded_abi_source;      /* sf_kernel_abi.h (generated) */
+
+/* AOT kernels (sf_aot.cu) */
+cudaError_t sf_launch_stats(const float *c, long long nx, long long ny, long long nz, int wx, int wy,
+                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv,
+                            cudaStream_t st);
+cudaError_t sf_launch_threshold(const float *c, long long nx, long long ny, long long nz, int wx,
+                                int wy, int wz, int nwy, int nwz, const float *mean,
+                                const float *stdv, float k, unsigned int *mask, int accumulate,
+                                cudaStream_t st);
+
+namespace {
+
+constexpr int kMaxRadius = 64;
+constexpr int kMaxFilters = 64;
+constexpr size_t kSmemLimit = 227 * 1024;
+
+std::mutex g_err_mu;
+std::string g_create_error;
+
+/* ------------------------------------------------------------ taps ------ */
+int radius_of(double sigma, double truncation)
+{
+    if (!(sigma > 0.0)) return 0;
+    return (int)std::ceil(truncation * sigma);
+}
+
+/* Sampled Gaussian exp(-o^2 / 2 sigma^2), o = -R..R, scaled to unit sum. */
+std::vector<double> gaussian_taps(double sigma, int R)
+{
+    std::vector<double> g(2 * R + 1, 1.0);
+    if (R == 0) return g;
+    double total = 0.0;
+    for (int o = -R; o <= R; ++o) {
+        g[o + R] = std::exp(-(double)o * o / (2.0 * sigma * sigma));
+        total += g[o + R];
+    }
+    for (double &v : g) v /= total;
+    return g;
+}
+
+struct Filt {
+    float sxy = 0.f, sz = 0.f;
+    int rxy = 0, rz = 0;
+    std::vector<float> gxy, gz;   /* 2R+1 float taps */
+    int slot = -1;                /* x-filtered scratch cube, -1 = none (sigma_xy == 0) */
+};
+
+struct DetectSource {
+    int slot;                     /* -1 = the cube itself */
+    int ry;
+    std::vector<int> filters;     /* <= nzf entries */
+};
+
+struct Launch {
+    cudaKernel_t kernel = nullptr;
+    dim3 grid, block;
+    size_t smem = 0;
+};
+
+/* ------------------------------------------------------------ JIT -------- */
+std::mutex g_jit_mu;
+std::map<std::string, cudaKernel_t> g_jit_cache;
+
+/* tuning override from the environment (launch shapes only, never the math) */
+int env_int(const char *name, int dflt)
+{
+    const char *v = std::getenv(name);
+    return (v && *v) ? std::atoi(v) : dflt;
+}
+
+int device_cc(int dev, int *major, int *minor)
+{
+    if (cudaDeviceGetAttribute(major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) return -1;
+    return 0;
+}
+
+sf_status jit_kernel(const std::string &prelude, const char *name, int dev, cudaKernel_t *out,
+                     std::string &err)
+{
+    int major = 0, minor = 0;
+    if (device_cc(dev, &major, &minor) != 0) {
+        err = "cannot query the compute capability of the device";
+        return SF_ECUDA;
+    }
+    const std::string arch = "--gpu-architecture=sm_" + std::to_string(major * 10 + minor) +
+                             (major >= 9 ? "a" : "");
+    std::string src = std::string(sf_embedded_abi_source) + "\n" + prelude + "\n" +
+                      sf_embedded_kernel_source;
+    const std::string key = arch + "\n" + name + "\n" + src;
+    {
+        std::lock_guard<std::mutex> lk(g_jit_mu);
+        auto it = g_jit_cache.find(key);
+        if (it != g_jit_cache.end()) {
+            *out = it->second;
+            return SF_OK;
+        }
+    }
+    nvrtcProgram prog;
+    if (nvrtcCreateProgram(&prog, src.c_str(), "sf_kernels.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+        err = "nvrtcCreateProgram failed";
+        return SF_EJIT;
+    }
+    const char *opts[] = {arch.c_str(), "-std=c++17", "-lineinfo", "--fmad=true",
+                          "-DSF_JIT=1"};
+    nvrtcResult rc = nvrtcCompileProgram(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
+    if (rc != NVRTC_SUCCESS) {
+        size_t n = 0;
+        nvrtcGetProgramLogSize(prog, &n);
+        std::string log(n, '\0');
+        if (n) nvrtcGetProgramLog(prog, &log[0]);
+        err = std::string("kernel compilation failed (") + nvrtcGetErrorString(rc) + "): " +
+              log.substr(0, 4000);
+        nvrtcDestroyProgram(&prog);
+        return SF_EJIT;
+    }
+    size_t nbin = 0;
+    nvrtcGetCUBINSize(prog, &nbin);
+    std::vector<char> cubin(nbin);
+    nvrtcGetCUBIN(prog, cubin.data());
+    nvrtcDestroyProgram(&prog);
+    cudaLibrary_t lib;
+    cudaError_t ce = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (ce != cudaSuccess) {
+        err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(ce);
+        return SF_ECUDA;
+    }
+    cudaKernel_t k;
+    ce = cudaLibraryGetKernel(&k, lib, name);
+    if (ce != cudaSuccess) {
+        err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(ce);
+        return SF_ECUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_jit_mu);
+    g_jit_cache.emplace(key, k);
+    *out = k;
+    return SF_OK;
+}
+
+const char *storage_ctype(int storage)
+{
+    return storage == SF_F16 ? "sf_f16" : storage == SF_BF16 ? "sf_bf16" : "float";
+}
+
+size_t storage_bytes(int storage) { return storage == SF_F32 ? 4 : 2; }
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+/* smallest stride >= need with (stride / 4) odd: conflict-free 16-byte rows */
+int odd_quad_stride(int need)
+{
+    int s = (need + 3) / 4 * 4;
+    if ((s / 4) % 2 == 0) s += 4;
+    return s;
+}
+
+}  // namespace
+
+/* ============================================================ context === */
+struct sf_ctx {
+    sf_config cfg{};
+    std::vector<Filt> filt;
+    int device = 0;
+    long long nvox = 0, nw32 = 0;
+    int nwx = 0, nwy = 0, nwz = 0, nwin = 0;
+    size_t ebytes = 4;
+
+    /* x pass */
+    std::vector<float> xy_sigma;      /* distinct non-zero sigma_xy, slot order */
+    std::vector<int> xy_radius;
+    void *scratch = nullptr;          /* n_slots cubes, storage dtype */
+    size_t cube_bytes = 0;
+    int xv = 1;                       /* elements per lane */
+    int xpf = 4;                      /* ring prefetch depth */
+    int xthreads = 256;
+    long long xseg = 0;
+    std::vector<std::vector<int>> xgroups;   /* slots per x-pass launch */
+    std::vector<Launch> xlaunch;
+
+    /* fused detect */
+    bool fused = false;
+    std::vector<DetectSource> dsrc;
+    int dnzf = 1, dC = 1, dPL = 1, dthreads = 0, dHZ = 0, dCH = 0, dSROW = 0, dUROW = 0;
+    int dRYM = 0, dRZM = 0;
+    Launch dlaunch;
+    std::vector<float> dtaps;
+
+    /* per-filter y/z filter kernels (sf_filter) and single-sigma x pass */
+    std::map<int, Launch> flaunch;
+    std::map<int, Launch> xsingle;    /* by slot */
+    std::map<int, std::vector<float>> ftaps;
+    float *filt_scratch = nullptr;    /* composed path: one filtered cube */
+    float *stat_scratch = nullptr;    /* composed path: mean/std of one filter */
+
+    /* host-buffer entry point */
+    void *host_cube = nullptr;
+    unsigned int *host_mask = nullptr;
+
+    /* stage timing: pairs of events per recorded stage instance */
+    bool prof = false;
+    struct Rec { int stage; cudaEvent_t a, b; int launches; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+
+    std::string err;
+    bool dead = false;
+};
+
+namespace {
+
+sf_status fail(sf_ctx *c, sf_status s, const char *fmt, ...)
+{
+    char buf[2048];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_create_error = buf;
+    }
+    return s;
+}
+
+sf_status cuda_fail(sf_ctx *c, cudaError_t e, const char *what)
+{
+    if (c) c->dead = true;
+    return fail(c, SF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        if (ok && prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+sf_status launch(sf_ctx *c, const Launch &L, void **args, cudaStream_t st, const char *what)
+{
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = L.grid;
+    lc.blockDim = L.block;
+    lc.dynamicSmemBytes = L.smem;
+    lc.stream = st;
+    cudaError_t e = cudaLaunchKernelExC(&lc, (const void *)L.kernel, args);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return SF_OK;
+}
+
+sf_status set_smem(sf_ctx *c, cudaKernel_t k, size_t smem)
+{
+    cudaError_t e = cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem, c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaKernelSetAttributeForDevice");
+    return SF_OK;
+}
+
+/* ---------------------------------------------------- x pass kernels --- */
+sf_status build_xpass(sf_ctx *c, const std::vector<int> &slots, Launch *L)
+{
+    const int nout = (int)slots.size();
+    int r[4] = {0, 0, 0, 0}, rm = 0;
+    for (int i = 0; i < nout; ++i) {
+        r[i] = c->xy_radius[slots[i]];
+        rm = std::max(rm, r[i]);
+    }
+    std::string p;
+    p += "#define SF_KERNEL_XPASS 1\n";
+    p += "#define SFX_NOUT " + std::to_string(nout) + "\n";
+    for (int i = 0; i < 4; ++i) p += "#define SFX_R" + std::to_string(i) + " " + std::to_string(r[i]) + "\n";
+    p += "#define SFX_RM " + std::to_string(rm) + "\n";
+    p += "#define SFX_PF " + std::to_string(c->xpf) + "\n";
+    p += "#define SFX_V " + std::to_string(c->xv) + "\n";
+    p += "#define SFX_THREADS " + std::to_string(c->xthreads) + "\n";
+    p += std::string("typedef ") + storage_ctype(c->cfg.storage) + " sfx_t;\n";
+    std::string err;
+    sf_status s = jit_kernel(p, "sf_xpass", c->device, &L->kernel, err);
+    if (s != SF_OK) return fail(c, s, "x pass: %s", err.c_str());
+    const long long plane = c->cfg.ny * c->cfg.nz;
+    const long long lanes = plane / c->xv;
+    const long long nseg = (c->cfg.nx + c->xseg - 1) / c->xseg;
+    L->block = dim3(c->xthreads);
+    L->grid = dim3((unsigned)((lanes + c->xthreads - 1) / c->xthreads), (unsigned)nseg);
+    L->smem = 0;
+    return SF_OK;
+}
+
+std::vector<float> xpass_taps(const sf_ctx *c, const std::vector<int> &slots)
+{
+    int rm = 0;
+    for (int s : slots) rm = std::max(rm, c->xy_radius[s]);
+    std::vector<float> t(slots.size() * (rm + 1), 0.f);
+    for (size_t i = 0; i < slots.size(); ++i) {
+        /* any filter of this slot carries its taps */
+        for (const Filt &f : c->filt)
+            if (f.slot == slots[i]) {
+                for (int j = 0; j <= f.rxy; ++j) t[i * (rm + 1) + j] = f.gxy[f.rxy + j];
+                break;
+            }
+    }
+    return t;
+}
+
+sf_status run_xpass(sf_ctx *c, const Launch &L, const std::vector<int> &slots, const void *cube,
+                    cudaStream_t st)
+{
+    sf_xargs xa{};
+    xa.src = cube;
+    for (size_t i = 0; i < slots.size(); ++i)
+        xa.dst[i] = (char *)c->scratch + (size_t)slots[i] * c->cube_bytes;
+    xa.nx = c->cfg.nx;
+    xa.plane = c->cfg.ny * c->cfg.nz;
+    xa.lanes = xa.plane / c->xv;
+    xa.xseg = c->xseg;
+    std::vector<float> taps = xpass_taps(c, slots);
+    void *args[] = {&xa, taps.data()};
+    return launch(c, L, args, st, "x pass launch");
+}
+
+/* ------------------------------------------- y/z kernels: shared bits --- */
+struct YZShape {
+    int WY, WZ, threads, HZ, CH, SROW, UROW, RYM, RZM, nzf, nsrc;
+};
+
+std::string yz_prelude(const sf_ctx *c, const YZShape &sh, const std::vector<DetectSource> &srcs)
+{
+    std::string p;
+    p += "#define SFD_WY " + std::to_string(sh.WY) + "\n";
+    p += "#define SFD_WZ " + std::to_string(sh.WZ) + "\n";
+    p += "#define SFD_THREADS " + std::to_string(sh.threads) + "\n";
+    p += "#define SFD_NSRC " + std::to_string(sh.nsrc) + "\n";
+    p += "#define SFD_NZF " + std::to_string(sh.nzf) + "\n";
+    p += "#define SFD_RYM " + std::to_string(sh.RYM) + "\n";
+    p += "#define SFD_RZM " + std::to_string(sh.RZM) + "\n";
+    p += "#define SFD_HZ " + std::to_string(sh.HZ) + "\n";
+    p += "#define SFD_CH " + std::to_string(sh.CH) + "\n";
+    p += "#define SFD_SROW " + std::to_string(sh.SROW) + "\n";
+    p += "#define SFD_UROW " + std::to_string(sh.UROW) + "\n";
+    p += "#define SFD_PY 4\n";
+    p += std::string("typedef ") + storage_ctype(c->cfg.storage) + " sfd_t;\n";
+    p += "#define SFD_SOURCES(X)";
+    for (size_t i = 0; i < srcs.size(); ++i) {
+        int rz[4] = {0, 0, 0, 0};
+        for (size_t f = 0; f < srcs[i].filters.size(); ++f) rz[f] = c->filt[srcs[i].filters[f]].rz;
+        p += " X(" + std::to_string(i) + ", " + std::to_string(srcs[i].ry) + ", " +
+             std::to_string(srcs[i].filters.size()) + ", " + std::to_string(rz[0]) + ", " +
+             std::to_string(rz[1]) + ", " + std::to_string(rz[2]) + ", " + std::to_string(rz[3]) + ")";
+    }
+    p += "\n";
+    return p;
+}
+
+/* y/z taps parameter block: gy[nsrc][RYM+1], gz[nsrc][nzf][RZM+1] by |offset| */
+std::vector<float> yz_taps(const sf_ctx *c, const YZShape &sh, const std::vector<DetectSource> &srcs)
+{
+    std::vector<float> t(sh.nsrc * (sh.RYM + 1) + sh.nsrc * sh.nzf * (sh.RZM + 1), 0.f);
+    for (size_t i = 0; i < srcs.size(); ++i) {
+        const Filt &f0 = c->filt[srcs[i].filters[0]];
+        for (int j = 0; j <= srcs[i].ry; ++j) t[i * (sh.RYM + 1) + j] = f0.gxy[f0.rxy + j];
+        for (size_t q = 0; q < srcs[i].filters.size(); ++q) {
+            const Filt &f = c->filt[srcs[i].filters[q]];
+            float *g = &t[sh.nsrc * (sh.RYM + 1) + (i * sh.nzf + q) * (sh.RZM + 1)];
+            for (int j = 0; j <= f.rz; ++j) g[j] = f.gz[f.rz + j];
+        }
+    }
+    return t;
+}
+
+void yz_common_shape(const sf_ctx *c, YZShape &sh, int rym, int rzm)
+{
+    const size_t eb = c->ebytes;
+    const int vec = (int)(16 / eb);               /* elements per 16-byte chunk */
+    if (c->cfg.nz % vec == 0) sh.CH = vec;
+    else if (eb == 4 && c->cfg.nz % 2 == 0) sh.CH = 2;
+    else if (eb == 4) sh.CH = 1;
+    else if (c->cfg.nz % 4 == 0) sh.CH = 4;       /* 8-byte chunks of 16-bit */
+    else if (c->cfg.nz % 2 == 0) sh.CH = 2;       /* 4-byte chunks of 16-bit */
+    else sh.CH = 0;                               /* element loads */
+    const int hzq = std::max(4, sh.CH);
+    sh.HZ = (rzm + hzq - 1) / hzq * hzq;
+    sh.RYM = rym;
+    sh.RZM = rzm;
+    const int uw = sh.WZ + 2 * sh.HZ;
+    sh.UROW = odd_quad_stride(uw + 4);
+    if (eb == 4) sh.SROW = odd_quad_stride(uw + 4);
+    else sh.SROW = (int)align_up((size_t)uw + 4, 8);
+}
+
+/* ------------------------------------------------------- sf_filter ----- */
+sf_status build_filter(sf_ctx *c, int fi, Launch *L)
+{
+    const Filt &f = c->filt[fi];
+    YZShape sh{};
+    sh.WY = 32;
+    sh.WZ = 64;
+    sh.threads = sh.WY * sh.WZ / 8;
+    sh.nzf = 1;
+    sh.nsrc = 1;
+    yz_common_shape(c, sh, f.rxy, f.rz);
+    std::vector<DetectSource> srcs{DetectSource{f.slot, f.rxy, {fi}}};
+    const size_t slab_bytes = align_up((size_t)(sh.WY + 2 * sh.RYM) * sh.SROW * c->ebytes, 128);
+    const size_t u_bytes = f.rxy > 0 ? (size_t)sh.WY * sh.UROW * 4 : 0;
+    std::string p = "#define SF_KERNEL_FILTER 1\n" + yz_prelude(c, sh, srcs);
+    p += "#define SFD_OFF_U " + std::to_string(slab_bytes) + "\n";
+    std::string err;
+    sf_status s = jit_kernel(p, "sf_yz_filter", c->device, &L->kernel, err);
+    if (s != SF_OK) return fail(c, s, "filter kernel: %s", err.c_str());
+    L->smem = slab_bytes + u_bytes;
+    if (L->smem > 48 * 1024 && (s = set_smem(c, L->kernel, L->smem)) != SF_OK) return s;
+    L->block = dim3(sh.threads);
+    L->grid = dim3((unsigned)c->cfg.nx, (unsigned)((c->cfg.ny + sh.WY - 1) / sh.WY),
+                   (unsigned)((c->cfg.nz + sh.WZ - 1) / sh.WZ));
+    c->ftaps[fi] = yz_taps(c, sh, srcs);
+    return SF_OK;
+}
+
+/* ------------------------------------------------------- sf_detect ----- */
+sf_status plan_detect(sf_ctx *c)
+{
+    const sf_config &g = c->cfg;
+    c->fused = false;
+    if (g.wy % 8 != 0 || g.wz % 32 != 0) return SF_OK;
+    const long long threads = (long long)g.wy * g.wz / 8;
+    if (threads < 32 || threads > 1024) return SF_OK;
+
+    /* inputs: the cube (sigma_xy = 0) first, then the scratch slots */
+    std::vector<std::pair<int, std::vector<int>>> groups;   /* slot, filters */
+    auto add = [&](int slot, int fi) {
+        for (auto &gr : groups)
+            if (gr.first == slot) { gr.second.push_back(fi); return; }
+        groups.push_back({slot, {fi}});
+    };
+    for (int i = 0; i < (int)c->filt.size(); ++i)
+        if (c->filt[i].slot < 0) add(-1, i);
+    for (int i = 0; i < (int)c->filt.size(); ++i)
+        if (c->filt[i].slot >= 0) add(c->filt[i].slot, i);
+    int maxper = 1;
+    for (auto &gr : groups) maxper = std::max(maxper, (int)gr.second.size());
+
+    for (int nzf = std::min(SF_MAX_NZF, maxper); nzf >= 1; --nzf) {
+        std::vector<DetectSource> srcs;
+        for (auto &gr : groups)
+            for (size_t i = 0; i < gr.second.size(); i += nzf) {
+                DetectSource d;
+                d.slot = gr.first;
+                d.ry = gr.first < 0 ? 0 : c->xy_radius[gr.first];
+                d.filters.assign(gr.second.begin() + i,
+                                 gr.second.begin() + std::min(gr.second.size(), i + (size_t)nzf));
+                srcs.push_back(d);
+            }
+        if ((int)srcs.size() > SF_MAX_SRC) continue;
+        int rym = 0, rzm = 0;
+        bool any_y = false;
+        for (auto &d : srcs) {
+            rym = std::max(rym, d.ry);
+            any_y |= d.ry > 0;
+            for (int fi : d.filters) rzm = std::max(rzm, c->filt[fi].rz);
+        }
+        YZShape sh{};
+        sh.WY = g.wy;
+        sh.WZ = g.wz;
+        sh.threads = (int)threads;
+        sh.nzf = nzf;
+        sh.nsrc = (int)srcs.size();
+        yz_common_shape(c, sh, rym, rzm);
+        const int cpref = env_int("SF_DC", 8);
+        const int cands[] = {cpref, 8, 4, 2, 1};
+        for (int C : cands) {
+            if (C < 1 || C > 8) continue;
+            if (g.wx % C != 0) continue;
+            const int PL = g.wx / C;
+            if (PL > 8) continue;
+            size_t off = 0;
+            const size_t slab = align_up((size_t)(sh.WY + 2 * rym) * sh.SROW * c->ebytes, 128);
+            const size_t off_s0 = off;
+            off += slab;
+            const size_t off_s1 = off;
+            off += slab;
+            const size_t off_u = off;
+            off += any_y ? align_up((size_t)sh.WY * sh.UROW * 4, 128) : 0;
+            const size_t off_cb = off;
+            off += (size_t)PL * nzf * 2 * threads * 16;
+            const size_t off_wr = off;
+            off += align_up((size_t)(threads / 32) * nzf * 3 * 4, 16);
+            const size_t off_cl = off;
+            off += align_up((size_t)sh.nsrc * C * nzf * 3 * 4, 16);
+            const size_t off_th = off;
+            off += align_up((size_t)nzf * 4, 16);
+            if (off > kSmemLimit) continue;
+
+            std::string p = "#define SF_KERNEL_DETECT 1\n" + yz_prelude(c, sh, srcs);
+            p += "#define SFD_C " + std::to_string(C) + "\n";
+            p += "#define SFD_PL " + std::to_string(PL) + "\n";
+            p += "#define SFD_OFF_SLAB0 " + std::to_string(off_s0) + "\n";
+            p += "#define SFD_OFF_SLAB1 " + std::to_string(off_s1) + "\n";
+            p += "#define SFD_OFF_U " + std::to_string(off_u) + "\n";
+            p += "#define SFD_OFF_CBUF " + std::to_string(off_cb) + "\n";
+            p += "#define SFD_OFF_WRED " + std::to_string(off_wr) + "\n";
+            p += "#define SFD_OFF_CLUS " + std::to_string(off_cl) + "\n";
+            p += "#define SFD_OFF_THR " + std::to_string(off_th) + "\n";
+            std::string err;
+            sf_status s = jit_kernel(p, "sf_yz_detect", c->device, &c->dlaunch.kernel, err);
+            if (s != SF_OK) return fail(c, s, "fused kernel: %s", err.c_str());
+            c->dlaunch.smem = off;
+            if (off > 48 * 1024 && (s = set_smem(c, c->dlaunch.kernel, off)) != SF_OK) return s;
+            c->dlaunch.block = dim3((unsigned)threads);
+            c->dlaunch.grid = dim3((unsigned)((long long)c->nwin * C));
+            c->dsrc = srcs;
+            c->dnzf = nzf;
+            c->dC = C;
+            c->dPL = PL;
+            c->dthreads = (int)threads;
+            c->dHZ = sh.HZ;
+            c->dCH = sh.CH;
+            c->dSROW = sh.SROW;
+            c->dUROW = sh.UROW;
+            c->dRYM = rym;
+            c->dRZM = rzm;
+            c->dtaps = yz_taps(c, sh, srcs);
+            c->fused = true;
+            return SF_OK;
+        }
+    }
+    return SF_OK;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+sf_status check_live(sf_ctx *c)
+{
+    if (!c) return SF_EINVAL;
+    if (c->dead) return fail(c, SF_ESTATE, "context unusable after an earlier CUDA error");
+    return SF_OK;
+}
+
+cudaEvent_t take_event(sf_ctx *c)
+{
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+/* begin/end of a timed stage on stream st (no-ops unless profiling) */
+struct StageTimer {
+    sf_ctx *c;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    StageTimer(sf_ctx *c_, int stage_, cudaStream_t st_) : c(c_), stage(stage_), st(st_)
+    {
+        if (c->prof && (a = take_event(c)) != nullptr) cudaEventRecord(a, st);
+    }
+    void done(int launches)
+    {
+        if (!a) return;
+        cudaEvent_t b = take_event(c);
+        if (!b) { c->pool.push_back(a); a = nullptr; return; }
+        cudaEventRecord(b, st);
+        c->recs.push_back(sf_ctx::Rec{stage, a, b, launches});
+        a = nullptr;
+    }
+    ~StageTimer()
+    {
+        if (a) c->pool.push_back(a);
+    }
+};
+
+}  // namespace
+
+/* ============================================================ C ABI ===== */
+extern "C" {
+
+const char *sf_status_str(sf_status s)
+{
+    switch (s) {
+    case SF_OK: return "SF_OK";
+    case SF_EINVAL: return "SF_EINVAL";
+    case SF_ENOMEM: return "SF_ENOMEM";
+    case SF_EBUDGET: return "SF_EBUDGET";
+    case SF_ECUDA: return "SF_ECUDA";
+    case SF_ETIMEOUT: return "SF_ETIMEOUT";
+    case SF_ESTATE: return "SF_ESTATE";
+    case SF_EJIT: return "SF_EJIT";
+    }
+    return "SF_UNKNOWN";
+}
+
+const char *sf_last_error(const sf_ctx *ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    static thread_local std::string copy;
+    copy = g_create_error;
+    return copy.c_str();
+}
+
+sf_status sf_create(const sf_config *cfg, sf_ctx **out)
+{
+    if (!out) return fail(nullptr, SF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, SF_EINVAL, "cfg is NULL");
+    const sf_config &g = *cfg;
+    if (g.nx < 1 || g.ny < 1 || g.nz < 1)
+        return fail(nullptr, SF_EINVAL, "cube dimensions must be >= 1 (got %lld x %lld x %lld)",
+                    (long long)g.nx, (long long)g.ny, (long long)g.nz);
+    if (g.nx > (1LL << 31) || g.ny > (1LL << 31) || g.nz > (1LL << 31))
+        return fail(nullptr, SF_EINVAL, "cube dimension above 2^31");
+    if (g.n_filters < 1 || g.n_filters > kMaxFilters || !g.filters)
+        return fail(nullptr, SF_EINVAL, "n_filters must be in [1, %d] with a filter array", kMaxFilters);
+    if (!(g.truncation > 0.f) || !std::isfinite(g.truncation))
+        return fail(nullptr, SF_EINVAL, "truncation must be positive");
+    if (g.wx < 1 || g.wy < 1 || g.wz < 1) return fail(nullptr, SF_EINVAL, "window sizes must be >= 1");
+    if (!std::isfinite(g.k)) return fail(nullptr, SF_EINVAL, "k must be finite");
+    if (g.storage != SF_F32 && g.storage != SF_F16 && g.storage != SF_BF16)
+        return fail(nullptr, SF_EINVAL, "unknown storage dtype %d", g.storage);
+    if (g.stats_fp64 != 0) return fail(nullptr, SF_EINVAL, "stats_fp64 is reserved and must be 0");
+    for (int i = 0; i < g.n_filters; ++i) {
+        const sf_filter_spec &f = g.filters[i];
+        if (!(f.sigma_xy >= 0.f) || !(f.sigma_z >= 0.f) || !std::isfinite(f.sigma_xy) ||
+            !std::isfinite(f.sigma_z))
+            return fail(nullptr, SF_EINVAL, "filter %d: sigmas must be finite and >= 0", i);
+        if (radius_of(f.sigma_xy, g.truncation) > kMaxRadius || radius_of(f.sigma_z, g.truncation) > kMaxRadius)
+            return fail(nullptr, SF_EINVAL, "filter %d: radius above %d", i, kMaxRadius);
+    }
+    int dev = g.device;
+    if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, SF_ECUDA, "no CUDA device");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || dev >= ndev)
+        return fail(nullptr, SF_ECUDA, "CUDA device %d not available", dev);
+
+    sf_ctx *c = new sf_ctx();
+    c->cfg = g;
+    c->cfg.filters = nullptr;
+    c->device = dev;
+    c->ebytes = storage_bytes(g.storage);
+    c->nvox = g.nx * g.ny * g.nz;
+    c->nw32 = (g.nz + 31) / 32;
+    c->nwx = (int)((g.nx + g.wx - 1) / g.wx);
+    c->nwy = (int)((g.ny + g.wy - 1) / g.wy);
+    c->nwz = (int)((g.nz + g.wz - 1) / g.wz);
+    c->nwin = c->nwx * c->nwy * c->nwz;
+    for (int i = 0; i < g.n_filters; ++i) {
+        Filt f;
+        f.sxy = g.filters[i].sigma_xy;
+        f.sz = g.filters[i].sigma_z;
+        f.rxy = radius_of(f.sxy, g.truncation);
+        f.rz = radius_of(f.sz, g.truncation);
+        for (double v : gaussian_taps(f.sxy, f.rxy)) f.gxy.push_back((float)v);
+        for (double v : gaussian_taps(f.sz, f.rz)) f.gz.push_back((float)v);
+        if (f.rxy > 0) {
+            int slot = -1;
+            for (size_t s = 0; s < c->xy_sigma.size(); ++s)
+                if (c->xy_sigma[s] == f.sxy) slot = (int)s;
+            if (slot < 0) {
+                slot = (int)c->xy_sigma.size();
+                c->xy_sigma.push_back(f.sxy);
+                c->xy_radius.push_back(f.rxy);
+            }
+            f.slot = slot;
+        }
+        c->filt.push_back(f);
+    }
+
+    DeviceGuard dg(dev);
+    if (!dg.ok) {
+        delete c;
+        return fail(nullptr, SF_ECUDA, "cudaSetDevice(%d) failed", dev);
+    }
+    /* x pass shape: the widest vector that divides the y-z plane and keeps
+     * the register ring (V * (2R+1+PF) floats) within about 96 registers */
+    const long long plane = g.ny * g.nz;
+    const int vmax = (int)(16 / c->ebytes);
+    int rxm = 0;
+    for (int r : c->xy_radius) rxm = std::max(rxm, r);
+    c->xpf = env_int("SF_XPF", 4);
+    const int ring = 2 * rxm + 1 + c->xpf;
+    c->xv = 1;
+    for (int v = vmax; v >= 1; v /= 2)
+        if (plane % v == 0 && (v == 1 || v * ring <= 96)) { c->xv = v; break; }
+    const int xv_env = env_int("SF_XV", 0);
+    if (xv_env > 0 && xv_env <= vmax && plane % xv_env == 0) c->xv = xv_env;
+    c->xseg = g.nx;
+    const int nseg = env_int("SF_XSEG", 1);
+    if (nseg > 1) c->xseg = (g.nx + nseg - 1) / nseg;
+    c->cube_bytes = align_up((size_t)c->nvox * c->ebytes, 256);
+    sf_status s = SF_OK;
+    if (!c->xy_sigma.empty()) {
+        cudaError_t e = cudaMalloc(&c->scratch, c->cube_bytes * c->xy_sigma.size());
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return fail(nullptr, SF_ENOMEM, "scratch allocation of %zu bytes failed",
+                        c->cube_bytes * (size_t)c->xy_sigma.size());
+        }
+        for (size_t i = 0; i < c->xy_sigma.size(); i += SF_MAX_XOUT) {
+            std::vector<int> slots;
+            for (size_t j = i; j < std::min(c->xy_sigma.size(), i + SF_MAX_XOUT); ++j) slots.push_back((int)j);
+            Launch L;
+            if ((s = build_xpass(c, slots, &L)) != SF_OK) break;
+            c->xgroups.push_back(slots);
+            c->xlaunch.push_back(L);
+        }
+    }
+    if (s == SF_OK) s = plan_detect(c);
+    if (s != SF_OK) {
+        {
+            std::lock_guard<std::mutex> lk(g_err_mu);
+            g_create_error = c->err;
+        }
+        sf_destroy(c);
+        return s;
+    }
+    *out = c;
+    return SF_OK;
+}
+
+sf_status sf_destroy(sf_ctx *c)
+{
+    if (!c) return SF_OK;
+    DeviceGuard dg(c->device);
+    cudaDeviceSynchronize();
+    cudaGetLastError();
+    cudaFree(c->scratch);
+    cudaFree(c->filt_scratch);
+    cudaFree(c->stat_scratch);
+    cudaFree(c->host_cube);
+    cudaFree(c->host_mask);
+    for (const sf_ctx::Rec &r : c->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+    delete c;
+    return SF_OK;
+}
+
+sf_status sf_taps(const sf_ctx *ctx, int32_t filter, int32_t axis, float *out, int32_t cap,
+                  int32_t *radius)
+{
+    sf_ctx *c = const_cast<sf_ctx *>(ctx);
+    if (!c) return SF_EINVAL;
+    if (filter < 0 || filter >= (int)c->filt.size()) return fail(c, SF_EINVAL, "filter index %d", filter);
+    if (axis < 0 || axis > 2) return fail(c, SF_EINVAL, "axis must be 0, 1 or 2");
+    const Filt &f = c->filt[filter];
+    const std::vector<float> &g = axis == 2 ? f.gz : f.gxy;
+    if (radius) *radius = (int32_t)((g.size() - 1) / 2);
+    if (out) {
+        if (cap < (int32_t)g.size()) return fail(c, SF_EINVAL, "capacity %d below %zu taps", cap, g.size());
+        std::memcpy(out, g.data(), g.size() * sizeof(float));
+    }
+    return SF_OK;
+}
+
+sf_status sf_window_grid(const sf_ctx *c, int32_t *nwx, int32_t *nwy, int32_t *nwz)
+{
+    if (!c) return SF_EINVAL;
+    if (nwx) *nwx = c->nwx;
+    if (nwy) *nwy = c->nwy;
+    if (nwz) *nwz = c->nwz;
+    return SF_OK;
+}
+
+sf_status sf_mask_words(const sf_ctx *c, int64_t *words)
+{
+    if (!c || !words) return SF_EINVAL;
+    *words = c->cfg.nx * c->cfg.ny * c->nw32;
+    return SF_OK;
+}
+
+sf_status sf_filter(sf_ctx *c, const void *d_cube, int32_t filter, float *d_filtered, void *stream)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (filter < 0 || filter >= (int)c->filt.size()) return fail(c, SF_EINVAL, "filter index %d", filter);
+    if (!d_cube || !d_filtered) return fail(c, SF_EINVAL, "NULL buffer");
+    if (!aligned16(d_cube) || !aligned16(d_filtered)) return fail(c, SF_EINVAL, "buffers must be 16-byte aligned");
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Filt &f = c->filt[filter];
+    const void *src = d_cube;
+    if (f.slot >= 0) {
+        auto it = c->xsingle.find(f.slot);
+        if (it == c->xsingle.end()) {
+            Launch L;
+            if ((s = build_xpass(c, {f.slot}, &L)) != SF_OK) return s;
+            it = c->xsingle.emplace(f.slot, L).first;
+        }
+        if ((s = run_xpass(c, it->second, {f.slot}, d_cube, st)) != SF_OK) return s;
+        src = (const char *)c->scratch + (size_t)f.slot * c->cube_bytes;
+    }
+    auto it = c->flaunch.find(filter);
+    if (it == c->flaunch.end()) {
+        Launch L;
+        if ((s = build_filter(c, filter, &L)) != SF_OK) return s;
+        it = c->flaunch.emplace(filter, L).first;
+    }
+    sf_fargs fa{};
+    fa.src = src;
+    fa.out = d_filtered;
+    fa.nx = c->cfg.nx;
+    fa.ny = c->cfg.ny;
+    fa.nz = c->cfg.nz;
+    std::vector<float> &taps = c->ftaps[filter];
+    void *args[] = {&fa, taps.data()};
+    return launch(c, it->second, args, st, "filter launch");
+}
+
+sf_status sf_stats(sf_ctx *c, const float *d_filtered, float *d_mean, float *d_std, void *stream)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (!d_filtered || !d_mean || !d_std) return fail(c, SF_EINVAL, "NULL buffer");
+    DeviceGuard dg(c->device);
+    const sf_config &g = c->cfg;
+    cudaError_t e = sf_launch_stats(d_filtered, g.nx, g.ny, g.nz, g.wx, g.wy, g.wz, c->nwx, c->nwy,
+                                    c->nwz, d_mean, d_std, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stats launch");
+    return SF_OK;
+}
+
+sf_status sf_threshold(sf_ctx *c, const float *d_filtered, const float *d_mean, const float *d_std,
+                       uint32_t *d_mask, int32_t accumulate, void *stream)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (!d_filtered || !d_mean || !d_std || !d_mask) return fail(c, SF_EINVAL, "NULL buffer");
+    DeviceGuard dg(c->device);
+    const sf_config &g = c->cfg;
+    cudaError_t e = sf_launch_threshold(d_filtered, g.nx, g.ny, g.nz, g.wx, g.wy, g.wz, c->nwy, c->nwz,
+                                        d_mean, d_std, g.k, d_mask, accumulate ? 1 : 0,
+                                        (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "threshold launch");
+    return SF_OK;
+}
+
+sf_status sf_detect(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_mean, float *d_std,
+                    void *stream)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (!d_cube || !d_mask) return fail(c, SF_EINVAL, "NULL buffer");
+    if ((d_mean == nullptr) != (d_std == nullptr))
+        return fail(c, SF_EINVAL, "d_mean and d_std must both be NULL or both be set");
+    if (!aligned16(d_cube)) return fail(c, SF_EINVAL, "cube must be 16-byte aligned");
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        StageTimer tx(c, 0, st);
+        for (size_t i = 0; i < c->xlaunch.size(); ++i)
+            if ((s = run_xpass(c, c->xlaunch[i], c->xgroups[i], d_cube, st)) != SF_OK) return s;
+        tx.done((int)c->xlaunch.size());
+    }
+    StageTimer tf(c, 1, st);
+    if (c->fused) {
+        sf_dargs da{};
+        for (size_t i = 0; i < c->dsrc.size(); ++i) {
+            const DetectSource &d = c->dsrc[i];
+            da.src[i] = d.slot < 0 ? d_cube : (const void *)((const char *)c->scratch + (size_t)d.slot * c->cube_bytes);
+            for (size_t q = 0; q < d.filters.size(); ++q) da.fidx[i][q] = d.filters[q];
+        }
+        da.mask = d_mask;
+        da.mean = d_mean;
+        da.stdv = d_std;
+        da.nx = c->cfg.nx;
+        da.ny = c->cfg.ny;
+        da.nz = c->cfg.nz;
+        da.nw32 = c->nw32;
+        da.nwx = c->nwx;
+        da.nwy = c->nwy;
+        da.nwz = c->nwz;
+        da.nwin = c->nwin;
+        da.k = c->cfg.k;
+        void *args[] = {&da, c->dtaps.data()};
+        s = launch(c, c->dlaunch, args, st, "fused detect launch");
+        if (s == SF_OK) tf.done(1);
+        return s;
+    }
+    /* composed path: per filter filter -> stats -> threshold (accumulate) */
+    const size_t nwin = (size_t)c->nwin;
+    if (!c->filt_scratch) {
+        cudaError_t e = cudaMalloc(&c->filt_scratch, (size_t)c->nvox * 4);
+        if (e == cudaSuccess) e = cudaMalloc(&c->stat_scratch, 2 * nwin * 4);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, SF_ENOMEM, "composed-path scratch allocation failed");
+        }
+    }
+    for (int fi = 0; fi < (int)c->filt.size(); ++fi) {
+        if ((s = sf_filter(c, d_cube, fi, c->filt_scratch, stream)) != SF_OK) return s;
+        float *m = d_mean ? d_mean + fi * nwin : c->stat_scratch;
+        float *sd = d_std ? d_std + fi * nwin : c->stat_scratch + nwin;
+        if ((s = sf_stats(c, c->filt_scratch, m, sd, stream)) != SF_OK) return s;
+        if ((s = sf_threshold(c, c->filt_scratch, m, sd, d_mask, fi > 0, stream)) != SF_OK) return s;
+    }
+    int nl = 0;
+    for (const Filt &f : c->filt) nl += 3 + (f.slot >= 0 ? 1 : 0);
+    tf.done(nl);
+    return SF_OK;
+}
+
+sf_status sf_profile_enable(sf_ctx *c, int32_t enable)
+{
+    if (!c) return SF_EINVAL;
+    c->prof = enable != 0;
+    return SF_OK;
+}
+
+sf_status sf_profile_read(sf_ctx *c, double *ms, int64_t *launches, int32_t n_stages)
+{
+    if (!c || n_stages < 0 || (n_stages > 0 && (!ms || !launches))) return SF_EINVAL;
+    DeviceGuard dg(c->device);
+    for (int i = 0; i < n_stages; ++i) {
+        ms[i] = 0.0;
+        launches[i] = 0;
+    }
+    sf_status s = SF_OK;
+    for (const sf_ctx::Rec &r : c->recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess && s == SF_OK) s = cuda_fail(c, e, "profile events");
+        if (r.stage < n_stages) {
+            ms[r.stage] += t;
+            launches[r.stage] += r.launches;
+        }
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->recs.clear();
+    return s;
+}
+
+sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *stream)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (!h_cube || !h_mask) return fail(c, SF_EINVAL, "NULL buffer");
+    DeviceGuard dg(c->device);
+    const size_t cube = (size_t)c->nvox * c->ebytes;
+    const size_t mask = (size_t)(c->cfg.nx * c->cfg.ny * c->nw32) * 4;
+    cudaError_t e;
+    if (!c->host_cube) {
+        e = cudaMalloc(&c->host_cube, cube);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&c->host_mask, mask);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, SF_ENOMEM, "device buffers for the host entry point");
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((e = cudaMemcpyAsync(c->host_cube, h_cube, cube, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(c, e, "host-to-device copy");
+    if ((s = sf_detect(c, c->host_cube, c->host_mask, nullptr, nullptr, stream)) != SF_OK) return s;
+    if ((e = cudaMemcpyAsync(h_mask, c->host_mask, mask, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+    return SF_OK;
+}
+
+}  /* extern "C" */

@@ -1,0 +1,280 @@
+"""Python binding of libsf.so (include/sf.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; PyTorch only
+provides device memory and the current stream.  Importing works without a
+GPU; any call that needs the library raises when it is not built or cannot be
+loaded (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SF_OK, SF_EINVAL, SF_ENOMEM, SF_EBUDGET, SF_ECUDA, SF_ETIMEOUT, SF_ESTATE, SF_EJIT = range(8)
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_str(status)}: {message}")
+        self.status = status
+
+
+class FilterSpec(ctypes.Structure):
+    _fields_ = [("sigma_xy", ctypes.c_float), ("sigma_z", ctypes.c_float)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64),
+                ("n_filters", ctypes.c_int32), ("filters", ctypes.POINTER(FilterSpec)),
+                ("truncation", ctypes.c_float), ("wx", ctypes.c_int32), ("wy", ctypes.c_int32),
+                ("wz", ctypes.c_int32), ("k", ctypes.c_float), ("storage", ctypes.c_int32),
+                ("stats_fp64", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+
+# name -> (restype, argtypes); every function declared in include/sf.h
+SIGNATURES = {
+    "sf_create": (_i32, [ctypes.POINTER(Config), ctypes.POINTER(_vp)]),
+    "sf_destroy": (_i32, [_vp]),
+    "sf_status_str": (ctypes.c_char_p, [_i32]),
+    "sf_last_error": (ctypes.c_char_p, [_vp]),
+    "sf_taps": (_i32, [_vp, _i32, _i32, ctypes.POINTER(ctypes.c_float), _i32,
+                       ctypes.POINTER(_i32)]),
+    "sf_window_grid": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                              ctypes.POINTER(_i32)]),
+    "sf_mask_words": (_i32, [_vp, ctypes.POINTER(_i64)]),
+    "sf_filter": (_i32, [_vp, _vp, _i32, _vp, _vp]),
+    "sf_stats": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "sf_threshold": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp]),
+    "sf_detect": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "sf_detect_host": (_i32, [_vp, _vp, _vp, _vp]),
+    "sf_profile_enable": (_i32, [_vp, _i32]),
+    "sf_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libsf.so (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is not built: call __graft_entry__.build() first")
+        handle = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+        return handle
+
+
+def status_str(status: int) -> str:
+    try:
+        return lib().sf_status_str(int(status)).decode()
+    except Exception:  # noqa: BLE001 - library missing: plain number
+        return f"status {int(status)}"
+
+
+def _check(status: int, ctx=None):
+    if status != SF_OK:
+        msg = lib().sf_last_error(ctx).decode(errors="replace")
+        raise SfError(status, msg)
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+def _stream(device):
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class SourceFinder:
+    """One planned filter bank over cubes of one shape (wraps an sf_ctx)."""
+
+    def __init__(self, shape, bank, truncation: float = 3.0, window=(32, 32, 64), k: float = 4.0,
+                 storage: str = "f32", device=None):
+        import torch
+        self.shape = tuple(int(s) for s in shape)
+        self.bank = tuple((float(a), float(b)) for a, b in bank)
+        self.truncation = float(truncation)
+        self.window = tuple(int(w) for w in window)
+        self.k = float(k)
+        self.storage = storage
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        specs = (FilterSpec * len(self.bank))(*[FilterSpec(a, b) for a, b in self.bank])
+        self._specs = specs
+        cfg = Config(self.shape[0], self.shape[1], self.shape[2], len(self.bank), specs,
+                     self.truncation, self.window[0], self.window[1], self.window[2], self.k,
+                     STORAGE[storage], 0, self.device.index if self.device.index is not None else -1)
+        h = _vp()
+        _check(lib().sf_create(ctypes.byref(cfg), ctypes.byref(h)), None)
+        self._h = h
+        nwx, nwy, nwz = _i32(), _i32(), _i32()
+        _check(lib().sf_window_grid(h, ctypes.byref(nwx), ctypes.byref(nwy), ctypes.byref(nwz)), h)
+        self.grid = (nwx.value, nwy.value, nwz.value)
+        words = _i64()
+        _check(lib().sf_mask_words(h, ctypes.byref(words)), h)
+        self.mask_words = words.value
+
+    # -- helpers --------------------------------------------------------------------
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n_windows(self) -> int:
+        return self.grid[0] * self.grid[1] * self.grid[2]
+
+    @property
+    def mask_shape(self):
+        return (self.shape[0], self.shape[1], -(-self.shape[2] // 32))
+
+    def _torch_dtype(self):
+        import torch
+        return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.storage]
+
+    def _check_cube(self, cube):
+        if tuple(cube.shape) != self.shape or cube.dtype != self._torch_dtype() \
+                or not cube.is_contiguous() or cube.device != self.device:
+            raise ValueError(f"cube must be a contiguous {self._torch_dtype()} tensor of shape "
+                             f"{self.shape} on {self.device}")
+
+    def _check_f32(self, t, shape, name):
+        import torch
+        if tuple(t.shape) != tuple(shape) or t.dtype != torch.float32 or not t.is_contiguous() \
+                or t.device != self.device:
+            raise ValueError(f"{name} must be a contiguous float32 tensor of shape {shape} "
+                             f"on {self.device}")
+
+    def taps(self, filter_index: int, axis: int) -> np.ndarray:
+        r = _i32()
+        _check(lib().sf_taps(self._h, filter_index, axis, None, 0, ctypes.byref(r)), self._h)
+        out = np.empty(2 * r.value + 1, dtype=np.float32)
+        _check(lib().sf_taps(self._h, filter_index, axis,
+                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size,
+                             ctypes.byref(r)), self._h)
+        return out
+
+    # -- entry points --------------------------------------------------------------------
+    def filter(self, cube, filter_index: int, out=None):
+        import torch
+        self._check_cube(cube)
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        self._check_f32(out, self.shape, "out")
+        _check(lib().sf_filter(self._h, _ptr(cube), int(filter_index), _ptr(out),
+                               _stream(self.device)), self._h)
+        return out
+
+    def stats(self, filtered, mean=None, std=None):
+        import torch
+        self._check_f32(filtered, self.shape, "filtered")
+        if mean is None:
+            mean = torch.empty(self.grid, dtype=torch.float32, device=self.device)
+        if std is None:
+            std = torch.empty(self.grid, dtype=torch.float32, device=self.device)
+        self._check_f32(mean, self.grid, "mean")
+        self._check_f32(std, self.grid, "std")
+        _check(lib().sf_stats(self._h, _ptr(filtered), _ptr(mean), _ptr(std),
+                              _stream(self.device)), self._h)
+        return mean, std
+
+    def threshold(self, filtered, mean, std, mask=None, accumulate: bool = False):
+        import torch
+        self._check_f32(filtered, self.shape, "filtered")
+        self._check_f32(mean, self.grid, "mean")
+        self._check_f32(std, self.grid, "std")
+        if mask is None:
+            mask = torch.zeros(self.mask_shape, dtype=torch.int32, device=self.device)
+        _check(lib().sf_threshold(self._h, _ptr(filtered), _ptr(mean), _ptr(std), _ptr(mask),
+                                  int(bool(accumulate)), _stream(self.device)), self._h)
+        return mask
+
+    def detect(self, cube, mask=None, stats: bool = False):
+        """Packed mask (int32 view of the uint32 words); with stats=True also
+        (mean, std) as float32 [n_filters][nwx][nwy][nwz]."""
+        import torch
+        self._check_cube(cube)
+        if mask is None:
+            mask = torch.empty(self.mask_shape, dtype=torch.int32, device=self.device)
+        mean = std = None
+        if stats:
+            shp = (len(self.bank),) + self.grid
+            mean = torch.empty(shp, dtype=torch.float32, device=self.device)
+            std = torch.empty(shp, dtype=torch.float32, device=self.device)
+        _check(lib().sf_detect(self._h, _ptr(cube), _ptr(mask), _ptr(mean), _ptr(std),
+                               _stream(self.device)), self._h)
+        return (mask, mean, std) if stats else mask
+
+    def detect_host(self, cube_host, mask_host=None):
+        """Host tensors in and out (pinned memory makes the copies DMA)."""
+        import torch
+        if tuple(cube_host.shape) != self.shape or cube_host.dtype != self._torch_dtype() \
+                or cube_host.device.type != "cpu" or not cube_host.is_contiguous():
+            raise ValueError("cube_host must be a contiguous CPU tensor of the cube shape/dtype")
+        if mask_host is None:
+            mask_host = torch.empty(self.mask_shape, dtype=torch.int32,
+                                    pin_memory=cube_host.is_pinned())
+        _check(lib().sf_detect_host(self._h, _ptr(cube_host), _ptr(mask_host),
+                                    _stream(self.device)), self._h)
+        return mask_host
+
+    def profile(self, enable: bool = True):
+        """Record CUDA events around the stages of every sf_detect."""
+        _check(lib().sf_profile_enable(self._h, int(bool(enable))), self._h)
+
+    def profile_read(self, n_stages: int = 2):
+        """{stage: (milliseconds, launches)} since the last read (0: x pass, 1: window kernel)."""
+        ms = (ctypes.c_double * n_stages)()
+        nl = (_i64 * n_stages)()
+        _check(lib().sf_profile_read(self._h, ms, nl, n_stages), self._h)
+        return {i: (ms[i], nl[i]) for i in range(n_stages)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def words_to_bits(words, nz: int) -> np.ndarray:
+    """Unpack a packed mask (any integer dtype holding uint32 words) to bool [nx][ny][nz]."""
+    w = np.asarray(words).view(np.uint32) if np.asarray(words).dtype == np.int32 else \
+        np.asarray(words, dtype=np.uint32)
+    bits = (w[..., None] >> np.arange(32, dtype=np.uint32)) & 1
+    nx, ny, nw = w.shape
+    return bits.reshape(nx, ny, nw * 32)[:, :, :nz].astype(bool)
