@@ -129,6 +129,20 @@ def _algorithmic(sf_plan, workload, storage_bytes):
     return {"x": (x_bytes, x_flops), "fused": (f_bytes, f_flops)}
 
 
+def _workload(args):
+    """The tile workload, or the same recipe and bank at --shape (profiling cases)."""
+    import dataclasses
+
+    from paper_1507_04941_gb300 import synth
+    w = synth.TILE
+    if args.shape:
+        shape = tuple(int(s) for s in args.shape)
+        n = max(1, int(w.n_sources * (shape[0] * shape[1] * shape[2]) / w.voxels))
+        w = dataclasses.replace(w, shape=shape, n_sources=n,
+                                name=f"tile-recipe-{shape[0]}x{shape[1]}x{shape[2]}-6filters")
+    return w
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -140,7 +154,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    w = synth.TILE
+    w = _workload(args)
     storage = args.storage
     nvox = w.voxels
     nf = len(w.bank)
@@ -270,7 +284,8 @@ def run_ours(args):
                        "bank_sigma_xy_z": [list(b) for b in w.bank], "truncation": w.truncation,
                        "window": list(w.window), "k": w.k, "storage": storage,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (1 GiB cube, 129 MB L2)"},
+                       "l2": f"inputs larger than L2 ({nvox * sbytes / 2**20:.0f} MiB cube, "
+                             "129 MB L2)"},
             "roofline": roof, "kernels": other, "clocks": clocks,
             "e2e": e2e, "gpu_launches": int(sum(st["launches_per_step"] for st in
                                                 stages.values()) * args.steps),
@@ -358,6 +373,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--shape", type=int, nargs=3, default=None,
+                    help="cube shape for profiling cases (default: the 512x512x1024 workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -121,7 +121,7 @@ def make_cube(shape, seed: int, n_sources: int, peak=(0.5, 3.0), beam_sigma=None
         blob = amp * torch.exp(-(ax[:, None, None] ** 2 + ay[None, :, None] ** 2) / (2 * ss * ss)
                                - az[None, None, :] ** 2 / (2 * sf * sf))
         cube[x0:x1, y0:y1, z0:z1] += blob.to(torch.float32)
-    return cube
+    return cube.contiguous()
 
 
 def make(workload: Workload, device="cpu") -> torch.Tensor:
