@@ -134,6 +134,11 @@ sf_status sf_detect(sf_ctx *ctx, const void *d_cube, uint32_t *d_mask, float *d_
  * the copies asynchronous DMA; pageable ones work too. */
 sf_status sf_detect_host(sf_ctx *ctx, const void *h_cube, uint32_t *h_mask, void *stream);
 
+/* Wait for the work enqueued on `stream`, then report kernel-side failures:
+ * SF_ETIMEOUT when a kernel's bounded wait on its own shared-memory loads
+ * expired since the last call (the flag is cleared). */
+sf_status sf_synchronize(sf_ctx *ctx, void *stream);
+
 /* Stage timing (tracing).  While enabled, every sf_detect records CUDA
  * events on its stream around each of its stages: stage 0 = the x pass
  * launches, stage 1 = the fused window kernel (or the composed per-filter

@@ -215,11 +215,17 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
 
 /* ======================================================================= */
 #if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_FILTER)
-/* Prelude: SFD_WY, SFD_WZ (tile of one plane), SFD_THREADS (= WY*WZ/8),
- * SFD_NSRC, SFD_NZF, SFD_RYM, SFD_RZM, SFD_HZ (z halo, multiple of SFD_CH),
- * SFD_CH (elements per cp.async, 0 = synchronous element loads), SFD_SROW,
- * SFD_UROW, SFD_PY, SFD_SOURCES(X) with X(index, RY, NZ, RZ0, RZ1),
- * typedef sfd_t; DETECT adds SFD_C, SFD_PL and the shared-memory offsets. */
+/* Prelude: SFD_WY, SFD_WZ (tile of one plane), SFD_P (z outputs per thread),
+ * SFD_THREADS (= WY*WZ/P), SFD_NSRC, SFD_NZF, SFD_RYM, SFD_RZM, SFD_HZ (z halo,
+ * multiple of 4 and of SFD_CH), SFD_CH (elements per cp.async, 0 = synchronous
+ * element loads), SFD_SROW, SFD_UROW, SFD_PY, SFD_SOURCES(X) with
+ * X(index, RY, NZ, RZ0, RZ1, RZ2, RZ3), typedef sfd_t; DETECT adds SFD_WX,
+ * SFD_TMA and the shared-memory offsets.
+ *
+ * Thread layout of the z pass: warp w, lane l owns row 8*(w % (WY/8)) + (l&7)
+ * and the chunk of P consecutive z numbered 4*(w / (WY/8)) + (l>>3); the eight
+ * lanes of one shared-memory phase read eight rows of one chunk, conflict-free
+ * because the row strides hold an odd number of 16-byte words. */
 
 constexpr int SFD_UW = SFD_WZ + 2 * SFD_HZ;   /* staged columns: z0-HZ .. z0+WZ+HZ */
 constexpr int SFD_NWARP = SFD_THREADS / 32;
@@ -326,28 +332,30 @@ __host__ __device__ constexpr int sfd_pick(int f, int a, int b, int c, int d)
     return f == 0 ? a : f == 1 ? b : f == 2 ? c : d;
 }
 
-/* Eight consecutive z outputs (z0 + 8*chunk .. +7) of row `row` for the NZ
- * spectral filters of input SI: c[f][i] = sum_o gz_f[|o|] u[z + o]. */
+/* SFD_P consecutive z outputs (z0 + P*chunk ...) of row `row` for the NZ
+ * spectral filters of input SI: c[f][i] = sum_o gz_f[|o|] u[z + o].  The
+ * symmetric taps are applied to pair sums u[z-o] + u[z+o] shared by the NZ
+ * filters of this input. */
 template <int SI, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
 __device__ __forceinline__ void sfd_zfilter(const sfd_t *slab, const float *U, int row, int chunk,
-                                            float (&c)[SFD_NZF][8], const sfd_taps &t)
+                                            float (&c)[SFD_NZF][SFD_P], const sfd_taps &t)
 {
     constexpr int RZM = sfd_max4(RZ0, RZ1, RZ2, RZ3);
-    constexpr int LO = (SFD_HZ - RZM) & ~3;      /* first staged column used (aligned) */
-    constexpr int HI = SFD_HZ + 7 + RZM;          /* last staged column used */
+    constexpr int LO = (SFD_HZ - RZM) & ~3;           /* first staged column used (aligned) */
+    constexpr int HI = SFD_HZ + SFD_P - 1 + RZM;       /* last staged column used */
     constexpr int NQ = (HI - LO) / 4 + 1;
     float in[NQ * 4];
     if constexpr (RY > 0) {
-        const float *p = U + row * SFD_UROW + 8 * chunk + LO;
+        const float *p = U + row * SFD_UROW + SFD_P * chunk + LO;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) sf_ld<float, 4, false>(p + 4 * q, in + 4 * q);
     } else {
-        const sfd_t *p = slab + row * SFD_SROW + 8 * chunk + LO;
+        const sfd_t *p = slab + row * SFD_SROW + SFD_P * chunk + LO;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) sf_ld<sfd_t, 4, false>(p + 4 * q, in + 4 * q);
     }
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < SFD_P; ++i) {
         const int ci = SFD_HZ + i - LO;
         float ps[RZM + 1];
         ps[0] = in[ci];
@@ -367,10 +375,34 @@ __device__ __forceinline__ void sfd_zfilter(const sfd_t *slab, const float *U, i
 
 /* ======================================================================= */
 #ifdef SF_KERNEL_DETECT
+/*
+ * sf_window_detect: one CTA per statistics window (grid = number of windows).
+ * For every input cube of the plan (the cube itself, then each x-filtered
+ * scratch cube), with the window's x-planes streamed through a double-buffered
+ * slab in shared memory:
+ *   pass 1  y and z filters of every plane, per-thread moments of the
+ *           filtered values, and the maximum of each plane per filter;
+ *           the moments are merged (Chan et al.) into the window mean and
+ *           standard deviation and the thresholds T_f = mean_f + k std_f;
+ *   pass 2  only the planes whose maximum exceeds T_f for some filter can
+ *           hold a selected voxel: those planes are filtered again (the same
+ *           arithmetic, so the same values) and c_f > T_f is OR-ed into the
+ *           window's mask words kept in shared memory.
+ * The mask words of the window are written once at the end.  Slabs arrive by
+ * TMA (cp.async.bulk.tensor, zero fill outside the cube) when the cube's
+ * rows are 16-byte multiples, else by cp.async.  Every wait on a TMA
+ * transaction is bounded by %globaltimer; on expiry the CTA records the
+ * failure in *err and leaves.
+ */
+struct __align__(64) sf_tmap { unsigned long long opaque[16]; };
+struct sfw_maps { sf_tmap m[SFD_NSRC]; };
 
-constexpr int SFD_SLAB_STRIDE = (SFD_OFF_SLAB1 - SFD_OFF_SLAB0) / (int)sizeof(sfd_t);
+constexpr int SFW_RG = SFD_WY / 8;                 /* row groups of 8 */
+constexpr int SFW_LPW = 32 / SFD_P;                /* lanes per 32-z mask word */
+constexpr int SFW_NW = SFD_WZ / 32;                /* mask words per window row */
+constexpr int SFW_SLAB_STRIDE = (SFD_OFF_SLAB1 - SFD_OFF_SLAB0) / (int)sizeof(sfd_t);
+constexpr unsigned long long SFW_TIMEOUT_NS = 2000000000ull;
 
-/* running (count, mean, M2) of a set of values; Chan et al. pairwise update */
 struct sfd_mom { float n, mean, m2; };
 
 __device__ __forceinline__ sfd_mom sfd_merge(sfd_mom a, sfd_mom b)
@@ -387,111 +419,152 @@ __device__ __forceinline__ sfd_mom sfd_merge(sfd_mom a, sfd_mom b)
     return r;
 }
 
-__device__ __forceinline__ u32 sfd_cluster_rank()
+__device__ __forceinline__ unsigned long long sfw_clock()
 {
-    u32 r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ u32 sfd_map_rank(u32 saddr, u32 rank)
-{
-    u32 r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(saddr), "r"(rank));
-    return r;
-}
-__device__ __forceinline__ void sfd_st_cluster(u32 addr, float v)
-{
-    asm volatile("st.shared::cluster.f32 [%0], %1;\n" ::"r"(addr), "f"(v) : "memory");
-}
-__device__ __forceinline__ float sfd_ld_cluster(u32 addr)
-{
-    float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];\n" : "=f"(v) : "r"(addr) : "memory");
-    return v;
-}
-__device__ __forceinline__ void sfd_cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n"
-                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-struct sfd_state {
-    sfd_t *slab0;   /* two slab buffers, SFD_SLAB_STRIDE elements apart */
+__device__ __forceinline__ bool sfw_try_wait(u32 bar, u32 parity)
+{
+    u32 ok;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+/* wait for phase `parity` of the barrier; false after SFW_TIMEOUT_NS */
+__device__ __forceinline__ bool sfw_wait(u32 bar, u32 parity)
+{
+    if (sfw_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = sfw_clock();
+    while (!sfw_try_wait(bar, parity))
+        if (sfw_clock() - t0 > SFW_TIMEOUT_NS) return false;
+    return true;
+}
+
+struct sfw_state {
+    sfd_t *slab0;
     float *U;
-    float4 *cbuf;   /* [PL][NZF][2][THREADS] */
-    float *wred;    /* [NWARP][NZF][3] */
-    float *clus;    /* [NSRC][C][NZF][3], used in rank 0 */
+    float *pmax;    /* [WX][NWARP][NZF] */
+    u32 *mask;      /* [WX][WY][NW] */
+    float *red;     /* [NWARP][NZF][3] */
     float *thr;     /* [NZF] */
+    u32 *flags;     /* [2] planes flagged for pass 2 (bit p) */
+    u32 bar;        /* two mbarriers, 8 bytes apart */
+    u32 phase;      /* bit b: parity of the next completion of barrier b */
     i64 x0, y0, z0;
     int npl, wid, row, chunk;
-    u32 rank, vmask;
-    int it;
-    u64 mbits;
+    u32 vmask;      /* valid outputs among this thread's P */
+    int it;         /* slab loads issued so far (buffer = it & 1) */
+    bool dead;
 };
 
-/* issue the slab load of input s, plane p into buffer (it & 1) */
-__device__ __forceinline__ void sfd_issue(const sf_dargs &a, sfd_state &S, int s, int p, int it)
+/* Load plane x0+p of input s into buffer b. */
+template <int IDX, int RY>
+__device__ __forceinline__ void sfw_load(const sf_dargs &a, const sfw_maps &mp, sfw_state &S, int p,
+                                         int b)
 {
-    sfd_t *dst = S.slab0 + (it & 1) * SFD_SLAB_STRIDE;
-    switch (s) {
-#define SFD_ISSUE_CASE(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                         \
-    case IDX:                                                                                    \
-        sfd_load_slab<RY>(dst, reinterpret_cast<const sfd_t *>(a.src[IDX]), S.x0 + p, S.y0, S.z0, \
-                          a.nx, a.ny, a.nz);                                                     \
-        break;
-        SFD_SOURCES(SFD_ISSUE_CASE)
-#undef SFD_ISSUE_CASE
-    default:
-        break;
+    sfd_t *dst = S.slab0 + b * SFW_SLAB_STRIDE;
+#if SFD_TMA
+    if (threadIdx.x == 0) {
+        constexpr u32 BYTES = (u32)(SFD_SROW * (SFD_WY + 2 * RY) * sizeof(sfd_t));
+        const u32 bar = S.bar + 8u * (u32)b;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(BYTES)
+                     : "memory");
+        const int cz = (int)(S.z0 - SFD_HZ), cy = (int)(S.y0 - RY), cx = (int)(S.x0 + p);
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sf_smem_addr(dst)),
+            "l"(reinterpret_cast<unsigned long long>(&mp.m[IDX])), "r"(cz), "r"(cy), "r"(cx),
+            "r"(bar)
+            : "memory");
     }
+#else
+    sfd_load_slab<RY>(dst, reinterpret_cast<const sfd_t *>(a.src[IDX]), S.x0 + p, S.y0, S.z0, a.nx,
+                      a.ny, a.nz);
+    sf_cp_commit();
+#endif
 }
 
-template <int SI, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
-__device__ __forceinline__ void sfd_run_source(const sf_dargs &a, const sfd_taps &t, sfd_state &S)
+/* Wait for buffer b (loaded by this CTA); `more` = another load is in flight. */
+__device__ __forceinline__ bool sfw_wait_buf(sfw_state &S, int b, bool more)
 {
+#if SFD_TMA
+    (void)more;
+    const bool ok = sfw_wait(S.bar + 8u * (u32)b, (S.phase >> b) & 1u);
+    S.phase ^= 1u << b;
+    return ok;
+#else
+    (void)b;
+    if (more) sf_cp_wait<1>();
+    else sf_cp_wait<0>();
+    return true;
+#endif
+}
+
+/* filtered values of this thread's outputs for plane buffer b */
+template <int IDX, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
+__device__ __forceinline__ void sfw_plane(const sfd_taps &t, sfw_state &S, int b,
+                                          float (&c)[SFD_NZF][SFD_P])
+{
+    const sfd_t *slab = S.slab0 + b * SFW_SLAB_STRIDE;
+    if constexpr (RY > 0) {
+        sfd_yfilter<IDX, RY>(slab, S.U, t);
+        __syncthreads();
+    }
+    sfd_zfilter<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(slab, S.U, S.row, S.chunk, c, t);
+}
+
+/* the next input's first load, issued while this input finishes */
+template <int IDX> __device__ __forceinline__ void sfw_first_load(const sf_dargs &a, const sfw_maps &mp,
+                                                                  sfw_state &S, int b);
+
+template <int IDX, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
+__device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, const sfw_maps &mp,
+                                          sfw_state &S)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     sfd_mom acc[NZ];
 #pragma unroll
     for (int f = 0; f < NZ; ++f) acc[f] = sfd_mom{0.f, 0.f, 0.f};
 
+    /* ---- pass 1: statistics and plane maxima (plane 0 was issued already) ---- */
     for (int p = 0; p < S.npl; ++p) {
-        /* prefetch the next item: next plane, or the first plane of the next input */
-        if (p + 1 < S.npl) sfd_issue(a, S, SI, p + 1, S.it + 1);
-        else if (SI + 1 < SFD_NSRC) sfd_issue(a, S, SI + 1, 0, S.it + 1);
-        sf_cp_commit();
-        sf_cp_wait<1>();
-        __syncthreads();
-        const sfd_t *slab = S.slab0 + (S.it & 1) * SFD_SLAB_STRIDE;
-        if constexpr (RY > 0) {
-            sfd_yfilter<SI, RY>(slab, S.U, t);
-            __syncthreads();
-        }
-        float c[SFD_NZF][8];
-        sfd_zfilter<SI, RY, NZ, RZ0, RZ1, RZ2, RZ3>(slab, S.U, S.row, S.chunk, c, t);
+        const int b = S.it & 1;
+        const bool more = p + 1 < S.npl;
+        if (more) sfw_load<IDX, RY>(a, mp, S, p + 1, b ^ 1);
+        const bool ok = sfw_wait_buf(S, b, more);
+        if (__syncthreads_or(!ok)) { S.dead = true; return; }
+        float c[SFD_NZF][SFD_P];
+        sfw_plane<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(t, S, b, c);
 #pragma unroll
         for (int f = 0; f < NZ; ++f) {
-            /* moments of this thread's eight values, two passes in registers */
-            float s = 0.f, nv = 0.f;
+            float s = 0.f, nv = 0.f, mx = -3.402823466e38f;
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (S.vmask & (1u << i)) { s += c[f][i]; nv += 1.f; }
+            for (int i = 0; i < SFD_P; ++i)
+                if (S.vmask & (1u << i)) { s += c[f][i]; nv += 1.f; mx = fmaxf(mx, c[f][i]); }
             if (nv > 0.f) {
                 const float m = s / nv;
                 float q = 0.f;
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < SFD_P; ++i)
                     if (S.vmask & (1u << i)) { const float d = c[f][i] - m; q = fmaf(d, d, q); }
                 acc[f] = sfd_merge(acc[f], sfd_mom{nv, m, q});
             }
-            float4 *cb = S.cbuf + ((p * SFD_NZF + f) * 2) * SFD_THREADS + threadIdx.x;
-            cb[0] = make_float4(c[f][0], c[f][1], c[f][2], c[f][3]);
-            cb[SFD_THREADS] = make_float4(c[f][4], c[f][5], c[f][6], c[f][7]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+            if (lane == 0) S.pmax[(p * SFD_NWARP + warp) * SFD_NZF + f] = mx;
         }
         __syncthreads();
         ++S.it;
     }
 
-    /* statistics: warp butterfly, then warps in order, then cluster ranks in order */
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    /* ---- window statistics and thresholds ---- */
 #pragma unroll
     for (int f = 0; f < NZ; ++f) {
         sfd_mom m = acc[f];
@@ -504,7 +577,7 @@ __device__ __forceinline__ void sfd_run_source(const sf_dargs &a, const sfd_taps
             m = (lane & off) ? sfd_merge(o, m) : sfd_merge(m, o);
         }
         if (lane == 0) {
-            float *w = S.wred + (warp * SFD_NZF + f) * 3;
+            float *w = S.red + (warp * SFD_NZF + f) * 3;
             w[0] = m.n; w[1] = m.mean; w[2] = m.m2;
         }
     }
@@ -513,104 +586,174 @@ __device__ __forceinline__ void sfd_run_source(const sf_dargs &a, const sfd_taps
         const int f = threadIdx.x;
         sfd_mom m{0.f, 0.f, 0.f};
         for (int w = 0; w < SFD_NWARP; ++w) {
-            const float *q = S.wred + (w * SFD_NZF + f) * 3;
+            const float *q = S.red + (w * SFD_NZF + f) * 3;
             m = sfd_merge(m, sfd_mom{q[0], q[1], q[2]});
-        }
-        const u32 slot = sf_smem_addr(S.clus + ((SI * SFD_C + (int)S.rank) * SFD_NZF + f) * 3);
-        const u32 remote = sfd_map_rank(slot, 0);
-        sfd_st_cluster(remote, m.n);
-        sfd_st_cluster(remote + 4, m.mean);
-        sfd_st_cluster(remote + 8, m.m2);
-    }
-    sfd_cluster_sync();
-    if (threadIdx.x < NZ) {
-        const int f = threadIdx.x;
-        sfd_mom m{0.f, 0.f, 0.f};
-        for (int r = 0; r < SFD_C; ++r) {
-            const u32 remote = sfd_map_rank(sf_smem_addr(S.clus + ((SI * SFD_C + r) * SFD_NZF + f) * 3), 0);
-            m = sfd_merge(m, sfd_mom{sfd_ld_cluster(remote), sfd_ld_cluster(remote + 4),
-                                     sfd_ld_cluster(remote + 8)});
         }
         const float sd = m.n > 0.f ? sqrtf(m.m2 / m.n) : 0.f;
         S.thr[f] = fmaf(a.k, sd, m.mean);
-        if (S.rank == 0 && a.mean != nullptr) {
-            const i64 o = (i64)a.fidx[SI][f] * a.nwin + S.wid;
+        if (a.mean != nullptr) {
+            const i64 o = (i64)a.fidx[IDX][f] * a.nwin + S.wid;
             a.mean[o] = m.mean;
             a.stdv[o] = sd;
         }
     }
     __syncthreads();
+    /* planes whose maximum exceeds a threshold (warp 0, one lane per plane) */
+    if (warp == 0) {
+        for (int base = 0; base < SFD_WX; base += 32) {
+            const int p = base + lane;
+            bool hot = false;
+            if (p < S.npl)
+                for (int w = 0; w < SFD_NWARP; ++w)
+#pragma unroll
+                    for (int f = 0; f < NZ; ++f)
+                        hot |= S.pmax[(p * SFD_NWARP + w) * SFD_NZF + f] > S.thr[f];
+            const u32 bits = __ballot_sync(0xffffffffu, hot);
+            if (lane == 0) S.flags[base >> 5] = bits;
+        }
+    }
+    __syncthreads();
+    const u32 fl0 = S.flags[0], fl1 = SFD_WX > 32 ? S.flags[1] : 0u;
+    float T[SFD_NZF];
+#pragma unroll
+    for (int f = 0; f < NZ; ++f) T[f] = S.thr[f];
 
-    /* threshold the values kept in shared memory */
-    for (int p = 0; p < S.npl; ++p) {
+    /* ---- pass 2: recompute the flagged planes and select ---- */
+    /* first flagged plane after `after` (-1: the first one), -1 when none */
+    auto next_flag = [&](int after) -> int {
+        const int from = after + 1;
+        if (from < 32) {
+            const u32 m = fl0 & ~((1u << from) - 1u);
+            if (m) return __ffs(m) - 1;
+        }
+        const int lo = from - 32;
+        const u32 m1 = lo <= 0 ? fl1 : (lo >= 32 ? 0u : (fl1 & ~((1u << lo) - 1u)));
+        return m1 ? 32 + __ffs(m1) - 1 : -1;
+    };
+    int p = next_flag(-1);
+    if (p >= 0) sfw_load<IDX, RY>(a, mp, S, p, S.it & 1);
+    while (p >= 0) {
+        const int b = S.it & 1;
+        const int pn = next_flag(p);
+        if (pn >= 0) sfw_load<IDX, RY>(a, mp, S, pn, b ^ 1);
+        else if (IDX + 1 < SFD_NSRC) sfw_first_load<IDX + 1>(a, mp, S, b ^ 1);
+        const bool ok = sfw_wait_buf(S, b, pn >= 0 || IDX + 1 < SFD_NSRC);
+        if (__syncthreads_or(!ok)) { S.dead = true; return; }
+        float c[SFD_NZF][SFD_P];
+        sfw_plane<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(t, S, b, c);
         u32 bits = 0;
 #pragma unroll
-        for (int f = 0; f < NZ; ++f) {
-            const float T = S.thr[f];
-            const float4 *cb = S.cbuf + ((p * SFD_NZF + f) * 2) * SFD_THREADS + threadIdx.x;
-            const float4 lo = cb[0], hi = cb[SFD_THREADS];
-            bits |= (lo.x > T ? 1u : 0u) | (lo.y > T ? 2u : 0u) | (lo.z > T ? 4u : 0u) |
-                    (lo.w > T ? 8u : 0u) | (hi.x > T ? 16u : 0u) | (hi.y > T ? 32u : 0u) |
-                    (hi.z > T ? 64u : 0u) | (hi.w > T ? 128u : 0u);
+        for (int f = 0; f < NZ; ++f)
+#pragma unroll
+            for (int i = 0; i < SFD_P; ++i) bits |= (c[f][i] > T[f] ? 1u : 0u) << i;
+        bits &= S.vmask;
+        /* the SFW_LPW lanes of one 32-z word combine their pieces */
+        u32 word = bits << (SFD_P * ((lane >> 3) % SFW_LPW));
+#pragma unroll
+        for (int off = 8; off < 8 * SFW_LPW; off <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, off);
+        if ((lane >> 3) % SFW_LPW == 0) {
+            u32 *mw = S.mask + (p * SFD_WY + S.row) * SFW_NW + (S.chunk * SFD_P) / 32;
+            *mw |= word;
         }
-        S.mbits |= (u64)(bits & S.vmask) << (8 * p);
+        __syncthreads();
+        ++S.it;
+        p = pn;
     }
+    /* no plane flagged: the next input's first plane has not been issued yet */
+    if (next_flag(-1) < 0 && IDX + 1 < SFD_NSRC) sfw_first_load<IDX + 1>(a, mp, S, S.it & 1);
 }
 
-extern "C" __global__ void __cluster_dims__(SFD_C, 1, 1) __launch_bounds__(SFD_THREADS, 1)
-sf_yz_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_taps t)
+#define SFW_FIRST(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                               \
+    template <> __device__ __forceinline__ void sfw_first_load<IDX>(const sf_dargs &a,             \
+                                                                    const sfw_maps &mp,            \
+                                                                    sfw_state &S, int b)           \
+    {                                                                                              \
+        sfw_load<IDX, RY>(a, mp, S, 0, b);                                                         \
+    }
+SFD_SOURCES(SFW_FIRST)
+#undef SFW_FIRST
+template <int IDX> __device__ __forceinline__ void sfw_first_load(const sf_dargs &, const sfw_maps &,
+                                                                  sfw_state &, int)
 {
-    extern __shared__ __align__(128) unsigned char sfd_sm[];
-    sfd_state S;
-    S.slab0 = reinterpret_cast<sfd_t *>(sfd_sm + SFD_OFF_SLAB0);
-    S.U = reinterpret_cast<float *>(sfd_sm + SFD_OFF_U);
-    S.cbuf = reinterpret_cast<float4 *>(sfd_sm + SFD_OFF_CBUF);
-    S.wred = reinterpret_cast<float *>(sfd_sm + SFD_OFF_WRED);
-    S.clus = reinterpret_cast<float *>(sfd_sm + SFD_OFF_CLUS);
-    S.thr = reinterpret_cast<float *>(sfd_sm + SFD_OFF_THR);
+}
 
-    S.rank = sfd_cluster_rank();
-    S.wid = (int)(blockIdx.x / SFD_C);
+extern "C" __global__ void __launch_bounds__(SFD_THREADS, SFD_MINB)
+sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_taps t,
+                 const __grid_constant__ sfw_maps mp)
+{
+    extern __shared__ __align__(128) unsigned char sfw_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<unsigned long long>(sfw_raw) + 127ull) & ~127ull);
+    sfw_state S;
+    S.slab0 = reinterpret_cast<sfd_t *>(sm + SFD_OFF_SLAB0);
+    S.U = reinterpret_cast<float *>(sm + SFD_OFF_U);
+    S.pmax = reinterpret_cast<float *>(sm + SFD_OFF_PMAX);
+    S.mask = reinterpret_cast<u32 *>(sm + SFD_OFF_MASK);
+    S.red = reinterpret_cast<float *>(sm + SFD_OFF_RED);
+    S.thr = reinterpret_cast<float *>(sm + SFD_OFF_THR);
+    S.flags = reinterpret_cast<u32 *>(sm + SFD_OFF_FLAGS);
+    S.bar = sf_smem_addr(sm + SFD_OFF_MBAR);
+    S.phase = 0;
+    S.dead = false;
+
+    S.wid = (int)blockIdx.x;
     const int wz = S.wid % a.nwz, wy = (S.wid / a.nwz) % a.nwy, wx = S.wid / (a.nwz * a.nwy);
-    S.x0 = (i64)wx * (SFD_C * SFD_PL) + (i64)S.rank * SFD_PL;
+    S.x0 = (i64)wx * SFD_WX;
     S.y0 = (i64)wy * SFD_WY;
     S.z0 = (i64)wz * SFD_WZ;
     const i64 left = a.nx - S.x0;
-    S.npl = left <= 0 ? 0 : (left < SFD_PL ? (int)left : SFD_PL);
+    S.npl = left < SFD_WX ? (int)left : SFD_WX;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int RG = SFD_WY / 8;
-    S.row = (warp % RG) * 8 + (lane & 7);
-    S.chunk = (warp / RG) * 4 + (lane >> 3);
+    S.row = (warp % SFW_RG) * 8 + (lane & 7);
+    S.chunk = (warp / SFW_RG) * 4 + (lane >> 3);
     const bool rowv = S.y0 + S.row < a.ny;
-    const i64 zb = S.z0 + 8 * S.chunk;
+    const i64 zb = S.z0 + (i64)SFD_P * S.chunk;
     S.vmask = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < SFD_P; ++i)
         if (rowv && zb + i < a.nz) S.vmask |= 1u << i;
-    S.mbits = 0;
     S.it = 0;
 
-    if (S.npl > 0) sfd_issue(a, S, 0, 0, 0);
-    sf_cp_commit();
-
-#define SFD_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3) sfd_run_source<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(a, t, S);
-    SFD_SOURCES(SFD_RUN)
-#undef SFD_RUN
-
-    /* mask words: lanes l, l^8, l^16, l^24 hold 8-voxel pieces of one 32-z word */
-    for (int p = 0; p < S.npl; ++p) {
-        u32 piece = (u32)((S.mbits >> (8 * p)) & 0xffu) << (8 * (lane >> 3));
-        piece |= __shfl_xor_sync(0xffffffffu, piece, 8);
-        piece |= __shfl_xor_sync(0xffffffffu, piece, 16);
-        const i64 wz32 = zb >> 5;
-        if ((lane >> 3) == 0 && rowv && wz32 < a.nw32)
-            a.mask[((S.x0 + p) * a.ny + S.y0 + S.row) * a.nw32 + wz32] = piece;
+    for (int i = threadIdx.x; i < SFD_WX * SFD_WY * SFW_NW; i += SFD_THREADS) S.mask[i] = 0u;
+#if SFD_TMA
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar + 8u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    /* keep this CTA's shared memory alive until every rank has read rank 0's slots */
-    sfd_cluster_sync();
+#endif
+    __syncthreads();
+    sfw_first_load<0>(a, mp, S, 0);
+
+#define SFW_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                                 \
+    if (!S.dead) sfw_input<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(a, t, mp, S);
+    SFD_SOURCES(SFW_RUN)
+#undef SFW_RUN
+
+    if (S.dead) {
+        /* a slab transaction did not complete in time: report it, give the
+         * copies still in flight a bounded time to land, and leave */
+        if (threadIdx.x == 0) {
+            atomicOr(a.err, 1);
+#if SFD_TMA
+            sfw_wait(S.bar, (S.phase >> 0) & 1u);
+            sfw_wait(S.bar + 8u, (S.phase >> 1) & 1u);
+#endif
+        }
+        return;
+    }
+    __syncthreads();
+    /* mask words of the window: one owner lane per (row, word) */
+    if ((lane >> 3) % SFW_LPW == 0 && rowv) {
+        const int wd = (S.chunk * SFD_P) / 32;
+        const i64 gw = (S.z0 >> 5) + wd;
+        if (gw < a.nw32)
+            for (int p = 0; p < S.npl; ++p)
+                a.mask[((S.x0 + p) * a.ny + S.y0 + S.row) * a.nw32 + gw] =
+                    S.mask[(p * SFD_WY + S.row) * SFW_NW + wd];
+    }
 }
 #endif /* SF_KERNEL_DETECT */
-
 /* ======================================================================= */
 #ifdef SF_KERNEL_FILTER
 /* one CTA per (x, y tile, z tile): y and z passes of a single filter */
@@ -633,7 +776,7 @@ sf_yz_filter(const __grid_constant__ sf_fargs a, const __grid_constant__ sfd_tap
     constexpr int RG = SFD_WY / 8;
     const int row = (warp % RG) * 8 + (lane & 7);
     const int chunk = (warp / RG) * 4 + (lane >> 3);
-    float c[SFD_NZF][8];
+    float c[SFD_NZF][SFD_P];
 #define SFF_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                \
     if constexpr (RY > 0) {                                                     \
         sfd_yfilter<IDX, RY>(slab, U, t);                                       \

@@ -35,7 +35,7 @@ struct sf_dargs {
     long long nx, ny, nz, nw32;
     int nwx, nwy, nwz, nwin;
     float k;
-    int pad_;
+    int *err;          /* set non-zero when a bounded wait expires */
 };
 
 /* y/z filter of one filter, writing float32 filtered values */

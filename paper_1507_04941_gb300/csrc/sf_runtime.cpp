@@ -8,11 +8,12 @@
  *   1. x pass (Eq. 2 factor along x) once per distinct non-zero sigma_xy into
  *      a scratch cube the context owns; one launch handles up to four sigmas
  *      and reads the cube once;
- *   2. one fused launch: per statistics window a cluster of CTAs filters the
- *      inputs (the cube itself for sigma_xy = 0, the scratch cubes otherwise)
- *      along y and z for every filter, forms the window mean and standard
- *      deviation (Sec. 3.3), applies c > mean + k*std and writes the OR of
- *      all filters into the packed mask.
+ *   2. one fused launch, one CTA per statistics window: the inputs (the cube
+ *      itself for sigma_xy = 0, the scratch cubes otherwise) are filtered
+ *      along y and z for every filter, the window mean and standard deviation
+ *      are formed (Sec. 3.3), and c > mean + k*std is OR-ed over all filters
+ *      into the packed mask; a second pass over the window refilters only the
+ *      x-planes whose maximum exceeds a threshold.
  * Windows whose shape the fused kernel cannot tile (wy % 8, wz % 32, thread
  * or shared-memory limits) run the composed path: per filter sf_filter into a
  * scratch cube, sf_stats, sf_threshold accumulating the mask.
@@ -21,6 +22,7 @@
 #include "sf_kernel_abi.h"
 
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <nvrtc.h>
 
 #include <algorithm>
@@ -218,10 +220,13 @@ struct sf_ctx {
     /* fused detect */
     bool fused = false;
     std::vector<DetectSource> dsrc;
-    int dnzf = 1, dC = 1, dPL = 1, dthreads = 0, dHZ = 0, dCH = 0, dSROW = 0, dUROW = 0;
+    int dnzf = 1, dP = 16, dthreads = 0, dHZ = 0, dCH = 0, dSROW = 0, dUROW = 0;
     int dRYM = 0, dRZM = 0;
+    bool dtma = false;
     Launch dlaunch;
     std::vector<float> dtaps;
+    std::vector<CUtensorMap> dmaps;   /* per input; the cube's is re-encoded per call */
+    int *err_flag = nullptr;          /* device flag set by kernels whose bounded wait expired */
 
     /* per-filter y/z filter kernels (sf_filter) and single-sigma x pass */
     std::map<int, Launch> flaunch;
@@ -382,7 +387,7 @@ std::string yz_prelude(const sf_ctx *c, const YZShape &sh, const std::vector<Det
     p += "#define SFD_CH " + std::to_string(sh.CH) + "\n";
     p += "#define SFD_SROW " + std::to_string(sh.SROW) + "\n";
     p += "#define SFD_UROW " + std::to_string(sh.UROW) + "\n";
-    p += "#define SFD_PY 4\n";
+    p += "#define SFD_PY 8\n";
     p += std::string("typedef ") + storage_ctype(c->cfg.storage) + " sfd_t;\n";
     p += "#define SFD_SOURCES(X)";
     for (size_t i = 0; i < srcs.size(); ++i) {
@@ -447,6 +452,7 @@ sf_status build_filter(sf_ctx *c, int fi, Launch *L)
     const size_t slab_bytes = align_up((size_t)(sh.WY + 2 * sh.RYM) * sh.SROW * c->ebytes, 128);
     const size_t u_bytes = f.rxy > 0 ? (size_t)sh.WY * sh.UROW * 4 : 0;
     std::string p = "#define SF_KERNEL_FILTER 1\n" + yz_prelude(c, sh, srcs);
+    p += "#define SFD_P 8\n";
     p += "#define SFD_OFF_U " + std::to_string(slab_bytes) + "\n";
     std::string err;
     sf_status s = jit_kernel(p, "sf_yz_filter", c->device, &L->kernel, err);
@@ -461,12 +467,50 @@ sf_status build_filter(sf_ctx *c, int fi, Launch *L)
 }
 
 /* ------------------------------------------------------- sf_detect ----- */
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+/* Tiled 3D tensor map of a cube [x][y][z] with box {SROW, WY + 2 RY, 1}. */
+bool encode_map(const sf_ctx *c, const void *base, int ry, CUtensorMap *out)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = c->cfg.storage == SF_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                   : c->cfg.storage == SF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dims[3] = {(cuuint64_t)c->cfg.nz, (cuuint64_t)c->cfg.ny, (cuuint64_t)c->cfg.nx};
+    const cuuint64_t strides[2] = {(cuuint64_t)(c->cfg.nz * (long long)c->ebytes),
+                                   (cuuint64_t)(c->cfg.ny * c->cfg.nz * (long long)c->ebytes)};
+    const cuuint32_t box[3] = {(cuuint32_t)c->dSROW, (cuuint32_t)(c->cfg.wy + 2 * ry), 1u};
+    const cuuint32_t es[3] = {1u, 1u, 1u};
+    return enc(out, dt, 3, const_cast<void *>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+/* The fused window kernel: one CTA per statistics window (see sf_kernels.cuh). */
 sf_status plan_detect(sf_ctx *c)
 {
     const sf_config &g = c->cfg;
     c->fused = false;
-    if (g.wy % 8 != 0 || g.wz % 32 != 0) return SF_OK;
-    const long long threads = (long long)g.wy * g.wz / 8;
+    if (g.wy % 8 != 0 || g.wz % 32 != 0 || g.wx > 64) return SF_OK;
+    int P = (g.wz % 64 == 0) ? 16 : 8;
+    const int penv = env_int("SF_WP", 0);
+    if ((penv == 8 || penv == 16) && g.wz % (4 * penv) == 0) P = penv;
+    const long long threads = (long long)g.wy * g.wz / P;
     if (threads < 32 || threads > 1024) return SF_OK;
 
     /* inputs: the cube (sigma_xy = 0) first, then the scratch slots */
@@ -480,93 +524,112 @@ sf_status plan_detect(sf_ctx *c)
         if (c->filt[i].slot < 0) add(-1, i);
     for (int i = 0; i < (int)c->filt.size(); ++i)
         if (c->filt[i].slot >= 0) add(c->filt[i].slot, i);
-    int maxper = 1;
-    for (auto &gr : groups) maxper = std::max(maxper, (int)gr.second.size());
-
-    for (int nzf = std::min(SF_MAX_NZF, maxper); nzf >= 1; --nzf) {
-        std::vector<DetectSource> srcs;
-        for (auto &gr : groups)
-            for (size_t i = 0; i < gr.second.size(); i += nzf) {
-                DetectSource d;
-                d.slot = gr.first;
-                d.ry = gr.first < 0 ? 0 : c->xy_radius[gr.first];
-                d.filters.assign(gr.second.begin() + i,
-                                 gr.second.begin() + std::min(gr.second.size(), i + (size_t)nzf));
-                srcs.push_back(d);
-            }
-        if ((int)srcs.size() > SF_MAX_SRC) continue;
-        int rym = 0, rzm = 0;
-        bool any_y = false;
-        for (auto &d : srcs) {
-            rym = std::max(rym, d.ry);
-            any_y |= d.ry > 0;
-            for (int fi : d.filters) rzm = std::max(rzm, c->filt[fi].rz);
+    std::vector<DetectSource> srcs;
+    for (auto &gr : groups)
+        for (size_t i = 0; i < gr.second.size(); i += SF_MAX_NZF) {
+            DetectSource d;
+            d.slot = gr.first;
+            d.ry = gr.first < 0 ? 0 : c->xy_radius[gr.first];
+            d.filters.assign(gr.second.begin() + i,
+                             gr.second.begin() + std::min(gr.second.size(), i + (size_t)SF_MAX_NZF));
+            srcs.push_back(d);
         }
-        YZShape sh{};
-        sh.WY = g.wy;
-        sh.WZ = g.wz;
-        sh.threads = (int)threads;
-        sh.nzf = nzf;
-        sh.nsrc = (int)srcs.size();
-        yz_common_shape(c, sh, rym, rzm);
-        const int cpref = env_int("SF_DC", 8);
-        const int cands[] = {cpref, 8, 4, 2, 1};
-        for (int C : cands) {
-            if (C < 1 || C > 8) continue;
-            if (g.wx % C != 0) continue;
-            const int PL = g.wx / C;
-            if (PL > 8) continue;
-            size_t off = 0;
-            const size_t slab = align_up((size_t)(sh.WY + 2 * rym) * sh.SROW * c->ebytes, 128);
-            const size_t off_s0 = off;
-            off += slab;
-            const size_t off_s1 = off;
-            off += slab;
-            const size_t off_u = off;
-            off += any_y ? align_up((size_t)sh.WY * sh.UROW * 4, 128) : 0;
-            const size_t off_cb = off;
-            off += (size_t)PL * nzf * 2 * threads * 16;
-            const size_t off_wr = off;
-            off += align_up((size_t)(threads / 32) * nzf * 3 * 4, 16);
-            const size_t off_cl = off;
-            off += align_up((size_t)sh.nsrc * C * nzf * 3 * 4, 16);
-            const size_t off_th = off;
-            off += align_up((size_t)nzf * 4, 16);
-            if (off > kSmemLimit) continue;
-
-            std::string p = "#define SF_KERNEL_DETECT 1\n" + yz_prelude(c, sh, srcs);
-            p += "#define SFD_C " + std::to_string(C) + "\n";
-            p += "#define SFD_PL " + std::to_string(PL) + "\n";
-            p += "#define SFD_OFF_SLAB0 " + std::to_string(off_s0) + "\n";
-            p += "#define SFD_OFF_SLAB1 " + std::to_string(off_s1) + "\n";
-            p += "#define SFD_OFF_U " + std::to_string(off_u) + "\n";
-            p += "#define SFD_OFF_CBUF " + std::to_string(off_cb) + "\n";
-            p += "#define SFD_OFF_WRED " + std::to_string(off_wr) + "\n";
-            p += "#define SFD_OFF_CLUS " + std::to_string(off_cl) + "\n";
-            p += "#define SFD_OFF_THR " + std::to_string(off_th) + "\n";
-            std::string err;
-            sf_status s = jit_kernel(p, "sf_yz_detect", c->device, &c->dlaunch.kernel, err);
-            if (s != SF_OK) return fail(c, s, "fused kernel: %s", err.c_str());
-            c->dlaunch.smem = off;
-            if (off > 48 * 1024 && (s = set_smem(c, c->dlaunch.kernel, off)) != SF_OK) return s;
-            c->dlaunch.block = dim3((unsigned)threads);
-            c->dlaunch.grid = dim3((unsigned)((long long)c->nwin * C));
-            c->dsrc = srcs;
-            c->dnzf = nzf;
-            c->dC = C;
-            c->dPL = PL;
-            c->dthreads = (int)threads;
-            c->dHZ = sh.HZ;
-            c->dCH = sh.CH;
-            c->dSROW = sh.SROW;
-            c->dUROW = sh.UROW;
-            c->dRYM = rym;
-            c->dRZM = rzm;
-            c->dtaps = yz_taps(c, sh, srcs);
-            c->fused = true;
-            return SF_OK;
-        }
+    if ((int)srcs.size() > SF_MAX_SRC) return SF_OK;
+    int rym = 0, rzm = 0, nzf = 1;
+    bool any_y = false;
+    for (auto &d : srcs) {
+        rym = std::max(rym, d.ry);
+        any_y |= d.ry > 0;
+        nzf = std::max(nzf, (int)d.filters.size());
+        for (int fi : d.filters) rzm = std::max(rzm, c->filt[fi].rz);
     }
+    YZShape sh{};
+    sh.WY = g.wy;
+    sh.WZ = g.wz;
+    sh.threads = (int)threads;
+    sh.nzf = nzf;
+    sh.nsrc = (int)srcs.size();
+    yz_common_shape(c, sh, rym, rzm);
+    /* TMA needs 16-byte row pitches and boxes of at most 256 elements per axis */
+    const int vec = (int)(16 / c->ebytes);
+    bool tma = (g.nz % vec == 0) && sh.SROW <= 256 && g.wy + 2 * rym <= 256 &&
+               tensor_map_encoder() != nullptr && env_int("SF_NO_TMA", 0) == 0;
+    if (tma) {
+        const int hzq = std::max(4, vec);
+        sh.HZ = (rzm + hzq - 1) / hzq * hzq;
+        const int uw = sh.WZ + 2 * sh.HZ;
+        sh.SROW = c->ebytes == 4 ? odd_quad_stride(uw + 4) : (int)align_up((size_t)uw + 4, 8);
+        sh.UROW = odd_quad_stride(uw + 4);
+        tma = sh.SROW <= 256;
+    }
+    const int nwarp = (int)threads / 32;
+    const int nw = g.wz / 32;
+    size_t off = 0;
+    const size_t slab = align_up((size_t)(sh.WY + 2 * rym) * sh.SROW * c->ebytes, 128);
+    const size_t off_s0 = off;
+    off += slab;
+    const size_t off_s1 = off;
+    off += slab;
+    const size_t off_u = off;
+    off += any_y ? align_up((size_t)sh.WY * sh.UROW * 4, 128) : 0;
+    const size_t off_pm = off;
+    off += align_up((size_t)g.wx * nwarp * nzf * 4, 16);
+    const size_t off_mk = off;
+    off += align_up((size_t)g.wx * g.wy * nw * 4, 16);
+    const size_t off_rd = off;
+    off += align_up((size_t)nwarp * nzf * 3 * 4, 16);
+    const size_t off_th = off;
+    off += align_up((size_t)nzf * 4, 16);
+    const size_t off_fl = off;
+    off += 16;
+    const size_t off_mb = off;
+    off += 16;
+    const size_t smem = off + 128;   /* the kernel aligns its base to 128 bytes */
+    if (smem > kSmemLimit) return SF_OK;
+
+    c->dsrc = srcs;
+    c->dSROW = sh.SROW;
+    c->dtma = tma;
+    std::string p = "#define SF_KERNEL_DETECT 1\n" + yz_prelude(c, sh, srcs);
+    p += "#define SFD_P " + std::to_string(P) + "\n";
+    p += "#define SFD_WX " + std::to_string(g.wx) + "\n";
+    /* resident CTAs per SM the register allocation must allow */
+    const int minb = std::max(1, std::min(8, env_int("SF_WMINB", P == 16 ? 3 : 2)));
+    p += "#define SFD_MINB " + std::to_string(minb) + "\n";
+    p += std::string("#define SFD_TMA ") + (tma ? "1" : "0") + "\n";
+    p += "#define SFD_OFF_SLAB0 " + std::to_string(off_s0) + "\n";
+    p += "#define SFD_OFF_SLAB1 " + std::to_string(off_s1) + "\n";
+    p += "#define SFD_OFF_U " + std::to_string(off_u) + "\n";
+    p += "#define SFD_OFF_PMAX " + std::to_string(off_pm) + "\n";
+    p += "#define SFD_OFF_MASK " + std::to_string(off_mk) + "\n";
+    p += "#define SFD_OFF_RED " + std::to_string(off_rd) + "\n";
+    p += "#define SFD_OFF_THR " + std::to_string(off_th) + "\n";
+    p += "#define SFD_OFF_FLAGS " + std::to_string(off_fl) + "\n";
+    p += "#define SFD_OFF_MBAR " + std::to_string(off_mb) + "\n";
+    std::string err;
+    sf_status s = jit_kernel(p, "sf_window_detect", c->device, &c->dlaunch.kernel, err);
+    if (s != SF_OK) return fail(c, s, "window kernel: %s", err.c_str());
+    c->dlaunch.smem = smem;
+    if (smem > 48 * 1024 && (s = set_smem(c, c->dlaunch.kernel, smem)) != SF_OK) return s;
+    c->dlaunch.block = dim3((unsigned)threads);
+    c->dlaunch.grid = dim3((unsigned)c->nwin);
+    c->dnzf = nzf;
+    c->dP = P;
+    c->dthreads = (int)threads;
+    c->dHZ = sh.HZ;
+    c->dCH = sh.CH;
+    c->dUROW = sh.UROW;
+    c->dRYM = rym;
+    c->dRZM = rzm;
+    c->dtaps = yz_taps(c, sh, srcs);
+    c->dmaps.assign(srcs.size(), CUtensorMap{});
+    if (tma)
+        for (size_t i = 0; i < srcs.size(); ++i)
+            if (srcs[i].slot >= 0 &&
+                !encode_map(c, (const char *)c->scratch + (size_t)srcs[i].slot * c->cube_bytes,
+                            srcs[i].ry, &c->dmaps[i]))
+                return fail(c, SF_ECUDA, "tensor map encoding failed");
+    c->fused = true;
     return SF_OK;
 }
 
@@ -752,6 +815,14 @@ sf_status sf_create(const sf_config *cfg, sf_ctx **out)
             c->xlaunch.push_back(L);
         }
     }
+    if (s == SF_OK) {
+        cudaError_t e = cudaMalloc(&c->err_flag, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->err_flag, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            s = fail(c, SF_ENOMEM, "error flag allocation failed");
+        }
+    }
     if (s == SF_OK) s = plan_detect(c);
     if (s != SF_OK) {
         {
@@ -776,6 +847,7 @@ sf_status sf_destroy(sf_ctx *c)
     cudaFree(c->stat_scratch);
     cudaFree(c->host_cube);
     cudaFree(c->host_mask);
+    cudaFree(c->err_flag);
     for (const sf_ctx::Rec &r : c->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -908,6 +980,8 @@ sf_status sf_detect(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_me
             const DetectSource &d = c->dsrc[i];
             da.src[i] = d.slot < 0 ? d_cube : (const void *)((const char *)c->scratch + (size_t)d.slot * c->cube_bytes);
             for (size_t q = 0; q < d.filters.size(); ++q) da.fidx[i][q] = d.filters[q];
+            if (c->dtma && d.slot < 0 && !encode_map(c, d_cube, d.ry, &c->dmaps[i]))
+                return fail(c, SF_ECUDA, "tensor map encoding of the cube failed");
         }
         da.mask = d_mask;
         da.mean = d_mean;
@@ -921,7 +995,8 @@ sf_status sf_detect(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_me
         da.nwz = c->nwz;
         da.nwin = c->nwin;
         da.k = c->cfg.k;
-        void *args[] = {&da, c->dtaps.data()};
+        da.err = c->err_flag;
+        void *args[] = {&da, c->dtaps.data(), c->dmaps.data()};
         s = launch(c, c->dlaunch, args, st, "fused detect launch");
         if (s == SF_OK) tf.done(1);
         return s;
@@ -1004,7 +1079,23 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
     if ((s = sf_detect(c, c->host_cube, c->host_mask, nullptr, nullptr, stream)) != SF_OK) return s;
     if ((e = cudaMemcpyAsync(h_mask, c->host_mask, mask, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return cuda_fail(c, e, "device-to-host copy");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+    return sf_synchronize(c, stream);
+}
+
+sf_status sf_synchronize(sf_ctx *c, void *stream)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    DeviceGuard dg(c->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+    int flag = 0;
+    if ((e = cudaMemcpy(&flag, c->err_flag, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(c, e, "error flag read");
+    if (flag) {
+        cudaMemset(c->err_flag, 0, sizeof(int));
+        return fail(c, SF_ETIMEOUT, "a kernel's bounded wait for its shared-memory loads expired");
+    }
     return SF_OK;
 }
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "sf_threshold": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp]),
     "sf_detect": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sf_detect_host": (_i32, [_vp, _vp, _vp, _vp]),
+    "sf_synchronize": (_i32, [_vp, _vp]),
     "sf_profile_enable": (_i32, [_vp, _i32]),
     "sf_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
 }
@@ -241,6 +242,10 @@ class SourceFinder:
         _check(lib().sf_detect_host(self._h, _ptr(cube_host), _ptr(mask_host),
                                     _stream(self.device)), self._h)
         return mask_host
+
+    def synchronize(self):
+        """Wait for this context's work on the current stream; raise on kernel-side timeouts."""
+        _check(lib().sf_synchronize(self._h, _stream(self.device)), self._h)
 
     def profile(self, enable: bool = True):
         """Record CUDA events around the stages of every sf_detect."""
