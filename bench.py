@@ -228,7 +228,7 @@ def run_ours(args):
     dominant = "fused" if (fused and (not xs or fused["ms_per_launch"] >= xs["ms_per_launch"])) \
         else "x"
     if dominant == "fused":
-        roof = {"kernel": "sf_yz_detect", "bound": "alu", "achieved": fused["tflops"],
+        roof = {"kernel": "sf_window_detect", "bound": "alu", "achieved": fused["tflops"],
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": fused["tflops"] / alu_peak,
                 "traffic": None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median "
@@ -242,12 +242,48 @@ def run_ours(args):
         else "derived"
     other = {}
     for key, st in stages.items():
-        other[key] = {"kernel": "sf_xpass" if key == "x" else "sf_yz_detect",
+        other[key] = {"kernel": "sf_xpass" if key == "x" else "sf_window_detect",
                       "ms_per_launch": round(st["ms_per_launch"], 5),
                       "launches_per_step": st["launches_per_step"],
                       "hbm_gbs": round(st["gbs"], 1), "hbm_frac": round(st["gbs"] / hbm_peak, 4),
                       "tflops": round(st["tflops"], 2),
                       "alu_frac": round(st["tflops"] / alu_peak, 4)}
+
+    # precision form: the same workload with FP16 / BF16 storage (FP32 arithmetic)
+    forms = {}
+    if not args.no_forms and storage == "f32":
+        for st_name, st_dt in (("f16", torch.float16), ("bf16", torch.bfloat16)):
+            cq = cube.to(st_dt).contiguous()
+            sq = SourceFinder(w.shape, w.bank, w.truncation, w.window, w.k, storage=st_name,
+                              device=dev)
+            for _ in range(3):
+                sq.detect(cq, mask)
+            torch.cuda.synchronize(dev)
+            sq.profile(True)
+            sq.profile_read()
+            n_f = max(10, args.steps // 3)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(n_f):
+                sq.detect(cq, mask)
+            f1.record(stream)
+            torch.cuda.synchronize(dev)
+            msf = f0.elapsed_time(f1) / n_f
+            pq = sq.profile_read()
+            algq = _algorithmic(sq, w, 2)
+            xq = pq[0][0] / n_f
+            wq = pq[1][0] / n_f
+            forms[st_name] = {
+                "value": units / (msf * 1e-3), "unit": UNIT, "ms_per_step": msf, "steps": n_f,
+                "speedup_vs_f32": ms_step / msf,
+                "x_pass": {"ms_per_launch": xq, "hbm_gbs": algq["x"][0] / (xq * 1e-3) / 1e9,
+                           "hbm_frac": algq["x"][0] / (xq * 1e-3) / 1e9 / hbm_peak},
+                "window_kernel": {"ms_per_launch": wq,
+                                  "tflops": algq["fused"][1] / (wq * 1e-3) / 1e12,
+                                  "alu_frac": algq["fused"][1] / (wq * 1e-3) / 1e12 / alu_peak}}
+            sq.close()
+            del cq
 
     # end to end through the host-buffer entry point (pinned memory)
     e2e = None
@@ -286,7 +322,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({nvox * sbytes / 2**20:.0f} MiB cube, "
                              "129 MB L2)"},
-            "roofline": roof, "kernels": other, "clocks": clocks,
+            "roofline": roof, "kernels": other, "clocks": clocks, "storage_forms": forms,
             "e2e": e2e, "gpu_launches": int(sum(st["launches_per_step"] for st in
                                                 stages.values()) * args.steps),
             "cpu_baseline": cpu,
@@ -372,6 +408,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP16/BF16-storage runs of the same workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--shape", type=int, nargs=3, default=None,
                     help="cube shape for profiling cases (default: the 512x512x1024 workload)")

@@ -529,96 +529,17 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
                                           sfw_state &S)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    sfd_mom acc[NZ];
+    constexpr u32 FULL = SFD_P == 32 ? 0xffffffffu : ((1u << SFD_P) - 1u);
+    const bool full = S.vmask == FULL;
+    /* per-thread shifted sums: K = the thread's first value of the window */
+    float K[SFD_NZF], s1[SFD_NZF], s2[SFD_NZF];
+    int cnt = 0;
 #pragma unroll
-    for (int f = 0; f < NZ; ++f) acc[f] = sfd_mom{0.f, 0.f, 0.f};
-
-    /* ---- pass 1: statistics and plane maxima (plane 0 was issued already) ---- */
-    for (int p = 0; p < S.npl; ++p) {
-        const int b = S.it & 1;
-        const bool more = p + 1 < S.npl;
-        if (more) sfw_load<IDX, RY>(a, mp, S, p + 1, b ^ 1);
-        const bool ok = sfw_wait_buf(S, b, more);
-        if (__syncthreads_or(!ok)) { S.dead = true; return; }
-        float c[SFD_NZF][SFD_P];
-        sfw_plane<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(t, S, b, c);
-#pragma unroll
-        for (int f = 0; f < NZ; ++f) {
-            float s = 0.f, nv = 0.f, mx = -3.402823466e38f;
-#pragma unroll
-            for (int i = 0; i < SFD_P; ++i)
-                if (S.vmask & (1u << i)) { s += c[f][i]; nv += 1.f; mx = fmaxf(mx, c[f][i]); }
-            if (nv > 0.f) {
-                const float m = s / nv;
-                float q = 0.f;
-#pragma unroll
-                for (int i = 0; i < SFD_P; ++i)
-                    if (S.vmask & (1u << i)) { const float d = c[f][i] - m; q = fmaf(d, d, q); }
-                acc[f] = sfd_merge(acc[f], sfd_mom{nv, m, q});
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-            if (lane == 0) S.pmax[(p * SFD_NWARP + warp) * SFD_NZF + f] = mx;
-        }
-        __syncthreads();
-        ++S.it;
-    }
-
-    /* ---- window statistics and thresholds ---- */
-#pragma unroll
-    for (int f = 0; f < NZ; ++f) {
-        sfd_mom m = acc[f];
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            sfd_mom o;
-            o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
-            o.mean = __shfl_xor_sync(0xffffffffu, m.mean, off);
-            o.m2 = __shfl_xor_sync(0xffffffffu, m.m2, off);
-            m = (lane & off) ? sfd_merge(o, m) : sfd_merge(m, o);
-        }
-        if (lane == 0) {
-            float *w = S.red + (warp * SFD_NZF + f) * 3;
-            w[0] = m.n; w[1] = m.mean; w[2] = m.m2;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < NZ) {
-        const int f = threadIdx.x;
-        sfd_mom m{0.f, 0.f, 0.f};
-        for (int w = 0; w < SFD_NWARP; ++w) {
-            const float *q = S.red + (w * SFD_NZF + f) * 3;
-            m = sfd_merge(m, sfd_mom{q[0], q[1], q[2]});
-        }
-        const float sd = m.n > 0.f ? sqrtf(m.m2 / m.n) : 0.f;
-        S.thr[f] = fmaf(a.k, sd, m.mean);
-        if (a.mean != nullptr) {
-            const i64 o = (i64)a.fidx[IDX][f] * a.nwin + S.wid;
-            a.mean[o] = m.mean;
-            a.stdv[o] = sd;
-        }
-    }
-    __syncthreads();
-    /* planes whose maximum exceeds a threshold (warp 0, one lane per plane) */
-    if (warp == 0) {
-        for (int base = 0; base < SFD_WX; base += 32) {
-            const int p = base + lane;
-            bool hot = false;
-            if (p < S.npl)
-                for (int w = 0; w < SFD_NWARP; ++w)
-#pragma unroll
-                    for (int f = 0; f < NZ; ++f)
-                        hot |= S.pmax[(p * SFD_NWARP + w) * SFD_NZF + f] > S.thr[f];
-            const u32 bits = __ballot_sync(0xffffffffu, hot);
-            if (lane == 0) S.flags[base >> 5] = bits;
-        }
-    }
-    __syncthreads();
-    const u32 fl0 = S.flags[0], fl1 = SFD_WX > 32 ? S.flags[1] : 0u;
+    for (int f = 0; f < SFD_NZF; ++f) { K[f] = 0.f; s1[f] = 0.f; s2[f] = 0.f; }
     float T[SFD_NZF];
 #pragma unroll
-    for (int f = 0; f < NZ; ++f) T[f] = S.thr[f];
-
-    /* ---- pass 2: recompute the flagged planes and select ---- */
+    for (int f = 0; f < SFD_NZF; ++f) T[f] = 0.f;
+    u32 fl0 = 0u, fl1 = 0u;
     /* first flagged plane after `after` (-1: the first one), -1 when none */
     auto next_flag = [&](int after) -> int {
         const int from = after + 1;
@@ -630,37 +551,144 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
         const u32 m1 = lo <= 0 ? fl1 : (lo >= 32 ? 0u : (fl1 & ~((1u << lo) - 1u)));
         return m1 ? 32 + __ffs(m1) - 1 : -1;
     };
-    int p = next_flag(-1);
-    if (p >= 0) sfw_load<IDX, RY>(a, mp, S, p, S.it & 1);
-    while (p >= 0) {
+
+    /* One loop over the items of both passes, so the filter code exists once:
+     * pass 1 visits planes 0..npl-1 (plane 0 was issued already), pass 2 the
+     * flagged planes. */
+    bool pass2 = false;
+    int p = 0;
+    while (true) {
         const int b = S.it & 1;
-        const int pn = next_flag(p);
-        if (pn >= 0) sfw_load<IDX, RY>(a, mp, S, pn, b ^ 1);
-        else if (IDX + 1 < SFD_NSRC) sfw_first_load<IDX + 1>(a, mp, S, b ^ 1);
-        const bool ok = sfw_wait_buf(S, b, pn >= 0 || IDX + 1 < SFD_NSRC);
+        int np = -1;
+        if (!pass2) np = p + 1 < S.npl ? p + 1 : -1;
+        else np = next_flag(p);
+        bool more = np >= 0;
+        if (more) sfw_load<IDX, RY>(a, mp, S, np, b ^ 1);
+        else if (pass2 && IDX + 1 < SFD_NSRC) { sfw_first_load<IDX + 1>(a, mp, S, b ^ 1); more = true; }
+        const bool ok = sfw_wait_buf(S, b, more);
         if (__syncthreads_or(!ok)) { S.dead = true; return; }
         float c[SFD_NZF][SFD_P];
         sfw_plane<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(t, S, b, c);
-        u32 bits = 0;
+        if (!pass2) {
+            if (p == 0) {
 #pragma unroll
-        for (int f = 0; f < NZ; ++f)
+                for (int f = 0; f < NZ; ++f) K[f] = c[f][0];
+            }
 #pragma unroll
-            for (int i = 0; i < SFD_P; ++i) bits |= (c[f][i] > T[f] ? 1u : 0u) << i;
-        bits &= S.vmask;
-        /* the SFW_LPW lanes of one 32-z word combine their pieces */
-        u32 word = bits << (SFD_P * ((lane >> 3) % SFW_LPW));
+            for (int f = 0; f < NZ; ++f) {
+                float mx = -3.402823466e38f;
+                if (full) {
 #pragma unroll
-        for (int off = 8; off < 8 * SFW_LPW; off <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, off);
-        if ((lane >> 3) % SFW_LPW == 0) {
-            u32 *mw = S.mask + (p * SFD_WY + S.row) * SFW_NW + (S.chunk * SFD_P) / 32;
-            *mw |= word;
+                    for (int i = 0; i < SFD_P; ++i) {
+                        const float d = c[f][i] - K[f];
+                        s1[f] += d;
+                        s2[f] = fmaf(d, d, s2[f]);
+                        mx = fmaxf(mx, c[f][i]);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < SFD_P; ++i)
+                        if (S.vmask & (1u << i)) {
+                            const float d = c[f][i] - K[f];
+                            s1[f] += d;
+                            s2[f] = fmaf(d, d, s2[f]);
+                            mx = fmaxf(mx, c[f][i]);
+                        }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+                if (lane == 0) S.pmax[(p * SFD_NWARP + warp) * SFD_NZF + f] = mx;
+            }
+            cnt += __popc(S.vmask);
+        } else {
+            u32 bits = 0;
+#pragma unroll
+            for (int f = 0; f < NZ; ++f)
+#pragma unroll
+                for (int i = 0; i < SFD_P; ++i) bits |= (c[f][i] > T[f] ? 1u : 0u) << i;
+            bits &= S.vmask;
+            /* the SFW_LPW lanes of one 32-z word combine their pieces */
+            u32 word = bits << (SFD_P * ((lane >> 3) % SFW_LPW));
+#pragma unroll
+            for (int off = 8; off < 8 * SFW_LPW; off <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, off);
+            if ((lane >> 3) % SFW_LPW == 0) {
+                u32 *mw = S.mask + (p * SFD_WY + S.row) * SFW_NW + (S.chunk * SFD_P) / 32;
+                *mw |= word;
+            }
         }
         __syncthreads();
         ++S.it;
-        p = pn;
+
+        if (!pass2 && np < 0) {
+            /* end of pass 1: window statistics, thresholds, flagged planes */
+#pragma unroll
+            for (int f = 0; f < NZ; ++f) {
+                sfd_mom m{0.f, 0.f, 0.f};
+                if (cnt > 0) {
+                    const float n = (float)cnt, mu = s1[f] / n;
+                    m = sfd_mom{n, K[f] + mu, fmaxf(s2[f] - s1[f] * mu, 0.f)};
+                }
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    sfd_mom o;
+                    o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
+                    o.mean = __shfl_xor_sync(0xffffffffu, m.mean, off);
+                    o.m2 = __shfl_xor_sync(0xffffffffu, m.m2, off);
+                    m = (lane & off) ? sfd_merge(o, m) : sfd_merge(m, o);
+                }
+                if (lane == 0) {
+                    float *w = S.red + (warp * SFD_NZF + f) * 3;
+                    w[0] = m.n; w[1] = m.mean; w[2] = m.m2;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x < NZ) {
+                const int f = threadIdx.x;
+                sfd_mom m{0.f, 0.f, 0.f};
+                for (int w = 0; w < SFD_NWARP; ++w) {
+                    const float *q = S.red + (w * SFD_NZF + f) * 3;
+                    m = sfd_merge(m, sfd_mom{q[0], q[1], q[2]});
+                }
+                const float sd = m.n > 0.f ? sqrtf(m.m2 / m.n) : 0.f;
+                S.thr[f] = fmaf(a.k, sd, m.mean);
+                if (a.mean != nullptr) {
+                    const i64 o = (i64)a.fidx[IDX][f] * a.nwin + S.wid;
+                    a.mean[o] = m.mean;
+                    a.stdv[o] = sd;
+                }
+            }
+            __syncthreads();
+            if (warp == 0) {
+                for (int base = 0; base < SFD_WX; base += 32) {
+                    const int q = base + lane;
+                    bool hot = false;
+                    if (q < S.npl)
+                        for (int w = 0; w < SFD_NWARP; ++w)
+#pragma unroll
+                            for (int f = 0; f < NZ; ++f)
+                                hot |= S.pmax[(q * SFD_NWARP + w) * SFD_NZF + f] > S.thr[f];
+                    const u32 bits = __ballot_sync(0xffffffffu, hot);
+                    if (lane == 0) S.flags[base >> 5] = bits;
+                }
+            }
+            __syncthreads();
+            fl0 = S.flags[0];
+            fl1 = SFD_WX > 32 ? S.flags[1] : 0u;
+#pragma unroll
+            for (int f = 0; f < NZ; ++f) T[f] = S.thr[f];
+            pass2 = true;
+            p = next_flag(-1);
+            if (p < 0) {
+                /* nothing can be selected in this window for this input */
+                if (IDX + 1 < SFD_NSRC) sfw_first_load<IDX + 1>(a, mp, S, S.it & 1);
+                return;
+            }
+            sfw_load<IDX, RY>(a, mp, S, p, S.it & 1);
+            continue;
+        }
+        if (pass2 && np < 0) return;
+        p = np;
     }
-    /* no plane flagged: the next input's first plane has not been issued yet */
-    if (next_flag(-1) < 0 && IDX + 1 < SFD_NSRC) sfw_first_load<IDX + 1>(a, mp, S, S.it & 1);
 }
 
 #define SFW_FIRST(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                               \

@@ -507,7 +507,7 @@ sf_status plan_detect(sf_ctx *c)
     const sf_config &g = c->cfg;
     c->fused = false;
     if (g.wy % 8 != 0 || g.wz % 32 != 0 || g.wx > 64) return SF_OK;
-    int P = (g.wz % 64 == 0) ? 16 : 8;
+    int P = 8;
     const int penv = env_int("SF_WP", 0);
     if ((penv == 8 || penv == 16) && g.wz % (4 * penv) == 0) P = penv;
     const long long threads = (long long)g.wy * g.wz / P;
@@ -594,7 +594,7 @@ sf_status plan_detect(sf_ctx *c)
     p += "#define SFD_P " + std::to_string(P) + "\n";
     p += "#define SFD_WX " + std::to_string(g.wx) + "\n";
     /* resident CTAs per SM the register allocation must allow */
-    const int minb = std::max(1, std::min(8, env_int("SF_WMINB", P == 16 ? 3 : 2)));
+    const int minb = std::max(1, std::min(8, env_int("SF_WMINB", P == 16 ? 3 : 3)));
     p += "#define SFD_MINB " + std::to_string(minb) + "\n";
     p += std::string("#define SFD_TMA ") + (tma ? "1" : "0") + "\n";
     p += "#define SFD_OFF_SLAB0 " + std::to_string(off_s0) + "\n";
@@ -786,7 +786,7 @@ sf_status sf_create(const sf_config *cfg, sf_ctx **out)
     const int vmax = (int)(16 / c->ebytes);
     int rxm = 0;
     for (int r : c->xy_radius) rxm = std::max(rxm, r);
-    c->xpf = env_int("SF_XPF", 4);
+    c->xpf = env_int("SF_XPF", 2);
     const int ring = 2 * rxm + 1 + c->xpf;
     c->xv = 1;
     for (int v = vmax; v >= 1; v /= 2)
