@@ -134,6 +134,22 @@ sf_status sf_detect(sf_ctx *ctx, const void *d_cube, uint32_t *d_mask, float *d_
  * the copies asynchronous DMA; pageable ones work too. */
 sf_status sf_detect_host(sf_ctx *ctx, const void *h_cube, uint32_t *h_mask, void *stream);
 
+/* Filtered cube of one filter without allocating anything, for callers that
+ * cannot call cudaMalloc (allocation-free loops, hosts that own every
+ * allocation).  No context: the filter is (sigma_xy, sigma_z, truncation),
+ * radius at most 32 per axis, and the two intermediate cubes live in a fixed
+ * 64 MiB scratch array inside the library (held on every GPU that loads it),
+ * so nx*ny*nz is limited to 8,388,608 voxels; larger cubes return SF_EINVAL
+ * with the reason in sf_last_error(NULL).
+ * d_cube and d_filtered are float32 device buffers of nx*ny*nz elements.
+ * All calls share the scratch array: calls that overlap on the GPU race.
+ * The first call on a device sets up the scratch address with
+ * cudaGetSymbolAddress; make it before any stream capture.  The paper has no
+ * counterpart of this entry point. */
+sf_status sf_filter_noalloc(const float *d_cube, int64_t nx, int64_t ny, int64_t nz,
+                            float sigma_xy, float sigma_z, float truncation, float *d_filtered,
+                            void *stream);
+
 /* Wait for the work enqueued on `stream`, then report kernel-side failures:
  * SF_ETIMEOUT when a kernel's bounded wait on its own shared-memory loads
  * expired since the last call (the flag is cleared). */

@@ -681,6 +681,13 @@ struct StageTimer {
 
 }  // namespace
 
+/* message for sf_last_error(NULL) from entry points that have no context */
+void sf_set_global_error(const char *msg)
+{
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_error = msg;
+}
+
 /* ============================================================ C ABI ===== */
 extern "C" {
 

@@ -61,6 +61,8 @@ SIGNATURES = {
     "sf_detect": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sf_detect_host": (_i32, [_vp, _vp, _vp, _vp]),
     "sf_synchronize": (_i32, [_vp, _vp]),
+    "sf_filter_noalloc": (_i32, [_vp, _i64, _i64, _i64, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, _vp, _vp]),
     "sf_profile_enable": (_i32, [_vp, _i32]),
     "sf_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
 }
