@@ -134,6 +134,36 @@ sf_status sf_detect(sf_ctx *ctx, const void *d_cube, uint32_t *d_mask, float *d_
  * the copies asynchronous DMA; pageable ones work too. */
 sf_status sf_detect_host(sf_ctx *ctx, const void *h_cube, uint32_t *h_mask, void *stream);
 
+/* Batched form.  One context for n cubes of different shapes that share the
+ * filter bank, window, threshold and storage of cfg (cfg->nx, ny, nz are
+ * ignored; dims holds n triples nx, ny, nz).  The context plans one
+ * persistent kernel for all cubes: a device work queue of x-pass items (lane
+ * chunks of one cube) and window items (one statistics window), ordered so
+ * that a cube's x items precede its windows; a window item waits, bounded in
+ * time, for its cube's x pass.  The launch is captured once in a CUDA graph
+ * (counter reset, the per-call cube tables copied from pinned staging, the
+ * kernel) and replayed by sf_detect_batch.  Sec. 4.1 tunes block sizes by a
+ * sweep and Sec. 6 proposes automatic configuration: see sf_tune. */
+sf_status sf_create_batch(const sf_config *cfg, int32_t n, const int64_t *dims, sf_ctx **out);
+
+/* sf_detect over every cube of a batched context.  d_cubes, d_masks: host
+ * arrays of n device pointers (cube i in the storage dtype, mask i of
+ * nx*ny*ceil(nz/32) words).  d_means/d_stds: NULL, or host arrays of n device
+ * pointers (each [n_filters][nwin_i] float32).  A call waits on the host for
+ * the previous call's tables to be consumed before it rewrites them. */
+sf_status sf_detect_batch(sf_ctx *ctx, const void *const *d_cubes, uint32_t *const *d_masks,
+                          float *const *d_means, float *const *d_stds, void *stream);
+
+/* Autotuner (Sec. 6: automatic configuration of the thread topology).  Runs
+ * sf_detect / sf_detect_batch on the given inputs for each candidate launch
+ * shape (for a plain context: the two-kernel path and the persistent kernel
+ * with several x-slab sizes and x-item sizes; for a batched context: the
+ * persistent shapes), keeps the fastest and returns after synchronising.
+ * For a plain context pass one cube and one mask.  sf_tune_report writes the
+ * timings as JSON text into buf. */
+sf_status sf_tune(sf_ctx *ctx, const void *const *d_cubes, uint32_t *const *d_masks, void *stream);
+sf_status sf_tune_report(const sf_ctx *ctx, char *buf, int32_t cap);
+
 /* Filtered cube of one filter without allocating anything, for callers that
  * cannot call cudaMalloc (allocation-free loops, hosts that own every
  * allocation).  No context: the filter is (sigma_xy, sigma_z, truncation),

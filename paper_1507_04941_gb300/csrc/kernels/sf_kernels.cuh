@@ -16,16 +16,16 @@
  *                                   (y, z) lane and marches along x with a
  *                                   register ring of the last 2R+1+PF planes,
  *                                   so every input element is read once.
- *   SF_KERNEL_DETECT  sf_yz_detect  one thread-block cluster per statistics
- *                                   window; each CTA owns wx/C x-planes.  Per
- *                                   input cube: cp.async-staged slab with y and
- *                                   z halo -> y filter in shared memory -> z
- *                                   filters in registers -> values kept in
- *                                   shared memory + per-thread moments ->
- *                                   Chan combine across warps and (through
- *                                   distributed shared memory) across the
- *                                   cluster -> threshold -> mask bits OR-ed in
- *                                   registers; one packed store per word.
+ *   SF_KERNEL_DETECT  sf_window_detect  one CTA per statistics window: per
+ *                                   input cube a TMA-staged slab per x-plane,
+ *                                   y filter in shared memory, z filters in
+ *                                   registers, moments and plane maxima (pass
+ *                                   1), then the flagged planes filtered again
+ *                                   and thresholded (pass 2); one packed store
+ *                                   per mask word.
+ *   SF_KERNEL_PERSIST sf_persist    the x pass and the windows of many cubes
+ *                                   in one persistent launch (a work queue
+ *                                   with per-cube completion counters).
  *   SF_KERNEL_FILTER  sf_yz_filter  y and z passes of one filter writing the
  *                                   float32 filtered cube.
  */
@@ -144,32 +144,31 @@ __device__ __forceinline__ void sf_st(T *p, const float *v)
 }
 
 /* ======================================================================= */
-#ifdef SF_KERNEL_XPASS
-/* Prelude: SFX_NOUT, SFX_R0..SFX_R3 (radii, 0 = unused), SFX_RM (max radius), SFX_PF (prefetch
- * depth), SFX_V (elements per lane), SFX_THREADS, typedef sfx_t. */
+#if defined(SF_KERNEL_XPASS) || defined(SF_KERNEL_PERSIST)
+/* Prelude: SFX_NOUT, SFX_R0..SFX_R3 (radii, 0 = unused), SFX_RM (max radius),
+ * SFX_PF (prefetch depth), typedef sfx_t; the stand-alone kernel adds SFX_V and
+ * SFX_THREADS. */
 struct sfx_taps { float g[SFX_NOUT][SFX_RM + 1]; };   /* g[k][|o|] */
 __host__ __device__ constexpr int sfx_r(int k)
 {
     return k == 0 ? SFX_R0 : k == 1 ? SFX_R1 : k == 2 ? SFX_R2 : SFX_R3;
 }
 
-extern "C" __global__ void __launch_bounds__(SFX_THREADS)
-sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
+/* x pass of one lane (V consecutive z of one (y, z) position) over output
+ * planes [xb, xe): a register ring of the last 2R+1+PF input planes, every
+ * input element read once, pair sums shared by the NOUT outputs. */
+template <int V>
+__device__ __forceinline__ void sfx_lane(const sfx_t *__restrict__ p, void *const *dst, i64 lane_off,
+                                         i64 nx, i64 plane, i64 xb, i64 xe, const sfx_taps &t)
 {
-    constexpr int RM = SFX_RM, V = SFX_V, K = 2 * RM + 1 + SFX_PF;
-    const i64 lane = (i64)blockIdx.x * SFX_THREADS + threadIdx.x;
-    if (lane >= a.lanes) return;
-    const i64 xb = (i64)blockIdx.y * a.xseg;
-    const i64 xe = min(a.nx, xb + a.xseg);
-    const i64 xlim = min(a.nx, xe + RM);            /* inputs used: [xb-RM, xe+RM) */
-    const sfx_t *__restrict__ p = reinterpret_cast<const sfx_t *>(a.src) + lane * V;
-
+    constexpr int RM = SFX_RM, K = 2 * RM + 1 + SFX_PF;
+    const i64 xlim = min(nx, xe + RM);            /* inputs used: [xb-RM, xe+RM) */
     /* slot i of the ring holds input plane xb-RM+i (mod K) */
     float ring[K][V];
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         const i64 xi = xb - RM + i;
-        if (xi >= 0 && xi < xlim) sf_ld<sfx_t, V, true>(p + xi * a.plane, ring[i]);
+        if (xi >= 0 && xi < xlim) sf_ld<sfx_t, V, true>(p + xi * plane, ring[i]);
         else {
 #pragma unroll
             for (int v = 0; v < V; ++v) ring[i][v] = 0.f;
@@ -180,7 +179,6 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
         for (int u = 0; u < K; ++u) {
             const i64 x = x0 + u;
             if (x < xe) {
-                /* symmetric taps: pair sums shared by all outputs */
                 float ps[RM + 1][V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) ps[0][v] = ring[(u + RM) % K][v];
@@ -198,11 +196,11 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
                     for (int j = 1; j <= sfx_r(k); ++j)
 #pragma unroll
                         for (int v = 0; v < V; ++v) acc[v] = fmaf(t.g[k][j], ps[j][v], acc[v]);
-                    sf_st<sfx_t, V>(reinterpret_cast<sfx_t *>(a.dst[k]) + x * a.plane + lane * V, acc);
+                    sf_st<sfx_t, V>(reinterpret_cast<sfx_t *>(dst[k]) + x * plane + lane_off, acc);
                 }
                 /* slot u is free: refill it with plane x - RM + K */
                 const i64 xi = x - RM + K;
-                if (xi < xlim) sf_ld<sfx_t, V, true>(p + xi * a.plane, ring[u]);
+                if (xi < xlim) sf_ld<sfx_t, V, true>(p + xi * plane, ring[u]);
                 else {
 #pragma unroll
                     for (int v = 0; v < V; ++v) ring[u][v] = 0.f;
@@ -211,10 +209,23 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
         }
     }
 }
+#endif
+
+#ifdef SF_KERNEL_XPASS
+extern "C" __global__ void __launch_bounds__(SFX_THREADS)
+sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
+{
+    const i64 lane = (i64)blockIdx.x * SFX_THREADS + threadIdx.x;
+    if (lane >= a.lanes) return;
+    const i64 xb = (i64)blockIdx.y * a.xseg;
+    const i64 xe = min(a.nx, xb + a.xseg);
+    const sfx_t *p = reinterpret_cast<const sfx_t *>(a.src) + lane * SFX_V;
+    sfx_lane<SFX_V>(p, a.dst, lane * SFX_V, a.nx, a.plane, xb, xe, t);
+}
 #endif /* SF_KERNEL_XPASS */
 
 /* ======================================================================= */
-#if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_FILTER)
+#if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_FILTER) || defined(SF_KERNEL_PERSIST)
 /* Prelude: SFD_WY, SFD_WZ (tile of one plane), SFD_P (z outputs per thread),
  * SFD_THREADS (= WY*WZ/P), SFD_NSRC, SFD_NZF, SFD_RYM, SFD_RZM, SFD_HZ (z halo,
  * multiple of 4 and of SFD_CH), SFD_CH (elements per cp.async, 0 = synchronous
@@ -374,7 +385,7 @@ __device__ __forceinline__ void sfd_zfilter(const sfd_t *slab, const float *U, i
 #endif
 
 /* ======================================================================= */
-#ifdef SF_KERNEL_DETECT
+#if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_PERSIST)
 /*
  * sf_window_detect: one CTA per statistics window (grid = number of windows).
  * For every input cube of the plan (the cube itself, then each x-filtered
@@ -461,16 +472,28 @@ struct sfw_state {
     u32 vmask;      /* valid outputs among this thread's P */
     int it;         /* slab loads issued so far (buffer = it & 1) */
     bool dead;
+    bool tma;       /* slabs arrive by TMA (else cp.async) */
 };
+
+/* TMA or cp.async slabs: fixed by the plan, or per cube in the persistent kernel */
+__device__ __forceinline__ bool sfw_tma(const sfw_state &S)
+{
+#if defined(SF_KERNEL_PERSIST)
+    return S.tma;
+#else
+    (void)S;
+    return SFD_TMA != 0;
+#endif
+}
 
 /* Load plane x0+p of input s into buffer b. */
 template <int IDX, int RY>
-__device__ __forceinline__ void sfw_load(const sf_dargs &a, const sfw_maps &mp, sfw_state &S, int p,
+__device__ __forceinline__ void sfw_load(const sf_dargs &a, const sf_tmap *mp, sfw_state &S, int p,
                                          int b)
 {
     sfd_t *dst = S.slab0 + b * SFW_SLAB_STRIDE;
-#if SFD_TMA
-    if (threadIdx.x == 0) {
+    if (sfw_tma(S)) {
+        if (threadIdx.x != 0) return;
         constexpr u32 BYTES = (u32)(SFD_SROW * (SFD_WY + 2 * RY) * sizeof(sfd_t));
         const u32 bar = S.bar + 8u * (u32)b;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -480,31 +503,27 @@ __device__ __forceinline__ void sfw_load(const sf_dargs &a, const sfw_maps &mp, 
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
             " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sf_smem_addr(dst)),
-            "l"(reinterpret_cast<unsigned long long>(&mp.m[IDX])), "r"(cz), "r"(cy), "r"(cx),
+            "l"(reinterpret_cast<unsigned long long>(mp + IDX)), "r"(cz), "r"(cy), "r"(cx),
             "r"(bar)
             : "memory");
+    } else {
+        sfd_load_slab<RY>(dst, reinterpret_cast<const sfd_t *>(a.src[IDX]), S.x0 + p, S.y0, S.z0,
+                          a.nx, a.ny, a.nz);
+        sf_cp_commit();
     }
-#else
-    sfd_load_slab<RY>(dst, reinterpret_cast<const sfd_t *>(a.src[IDX]), S.x0 + p, S.y0, S.z0, a.nx,
-                      a.ny, a.nz);
-    sf_cp_commit();
-#endif
 }
 
 /* Wait for buffer b (loaded by this CTA); `more` = another load is in flight. */
 __device__ __forceinline__ bool sfw_wait_buf(sfw_state &S, int b, bool more)
 {
-#if SFD_TMA
-    (void)more;
-    const bool ok = sfw_wait(S.bar + 8u * (u32)b, (S.phase >> b) & 1u);
-    S.phase ^= 1u << b;
-    return ok;
-#else
-    (void)b;
+    if (sfw_tma(S)) {
+        const bool ok = sfw_wait(S.bar + 8u * (u32)b, (S.phase >> b) & 1u);
+        S.phase ^= 1u << b;
+        return ok;
+    }
     if (more) sf_cp_wait<1>();
     else sf_cp_wait<0>();
     return true;
-#endif
 }
 
 /* filtered values of this thread's outputs for plane buffer b */
@@ -521,11 +540,11 @@ __device__ __forceinline__ void sfw_plane(const sfd_taps &t, sfw_state &S, int b
 }
 
 /* the next input's first load, issued while this input finishes */
-template <int IDX> __device__ __forceinline__ void sfw_first_load(const sf_dargs &a, const sfw_maps &mp,
+template <int IDX> __device__ __forceinline__ void sfw_first_load(const sf_dargs &a, const sf_tmap *mp,
                                                                   sfw_state &S, int b);
 
 template <int IDX, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
-__device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, const sfw_maps &mp,
+__device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, const sf_tmap *mp,
                                           sfw_state &S)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -693,26 +712,23 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
 
 #define SFW_FIRST(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                               \
     template <> __device__ __forceinline__ void sfw_first_load<IDX>(const sf_dargs &a,             \
-                                                                    const sfw_maps &mp,            \
+                                                                    const sf_tmap *mp,            \
                                                                     sfw_state &S, int b)           \
     {                                                                                              \
         sfw_load<IDX, RY>(a, mp, S, 0, b);                                                         \
     }
 SFD_SOURCES(SFW_FIRST)
 #undef SFW_FIRST
-template <int IDX> __device__ __forceinline__ void sfw_first_load(const sf_dargs &, const sfw_maps &,
+template <int IDX> __device__ __forceinline__ void sfw_first_load(const sf_dargs &, const sf_tmap *,
                                                                   sfw_state &, int)
 {
 }
 
-extern "C" __global__ void __launch_bounds__(SFD_THREADS, SFD_MINB)
-sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_taps t,
-                 const __grid_constant__ sfw_maps mp)
+/* shared-memory carve-up, thread roles and barrier set-up (once per CTA) */
+__device__ __forceinline__ void sfw_init(sfw_state &S, unsigned char *raw)
 {
-    extern __shared__ __align__(128) unsigned char sfw_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<unsigned long long>(sfw_raw) + 127ull) & ~127ull);
-    sfw_state S;
+        (reinterpret_cast<unsigned long long>(raw) + 127ull) & ~127ull);
     S.slab0 = reinterpret_cast<sfd_t *>(sm + SFD_OFF_SLAB0);
     S.U = reinterpret_cast<float *>(sm + SFD_OFF_U);
     S.pmax = reinterpret_cast<float *>(sm + SFD_OFF_PMAX);
@@ -723,17 +739,32 @@ sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd
     S.bar = sf_smem_addr(sm + SFD_OFF_MBAR);
     S.phase = 0;
     S.dead = false;
+    S.tma = SFD_TMA != 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    S.row = (warp % SFW_RG) * 8 + (lane & 7);
+    S.chunk = (warp / SFW_RG) * 4 + (lane >> 3);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar + 8u) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
 
-    S.wid = (int)blockIdx.x;
-    const int wz = S.wid % a.nwz, wy = (S.wid / a.nwz) % a.nwy, wx = S.wid / (a.nwz * a.nwy);
+/* One statistics window (index wid of the window grid of the cube `a`
+ * describes): both passes for every input, then the window's mask words.
+ * Returns false when a bounded wait expired (the CTA must stop). */
+__device__ __forceinline__ bool sfw_window(const sf_dargs &a, const sfd_taps &t, const sf_tmap *mp,
+                                           sfw_state &S, int wid)
+{
+    const int lane = threadIdx.x & 31;
+    S.wid = wid;
+    const int wz = wid % a.nwz, wy = (wid / a.nwz) % a.nwy, wx = wid / (a.nwz * a.nwy);
     S.x0 = (i64)wx * SFD_WX;
     S.y0 = (i64)wy * SFD_WY;
     S.z0 = (i64)wz * SFD_WZ;
     const i64 left = a.nx - S.x0;
     S.npl = left < SFD_WX ? (int)left : SFD_WX;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    S.row = (warp % SFW_RG) * 8 + (lane & 7);
-    S.chunk = (warp / SFW_RG) * 4 + (lane >> 3);
     const bool rowv = S.y0 + S.row < a.ny;
     const i64 zb = S.z0 + (i64)SFD_P * S.chunk;
     S.vmask = 0;
@@ -742,14 +773,8 @@ sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd
         if (rowv && zb + i < a.nz) S.vmask |= 1u << i;
     S.it = 0;
 
+    __syncthreads();   /* the previous window's mask words have been written out */
     for (int i = threadIdx.x; i < SFD_WX * SFD_WY * SFW_NW; i += SFD_THREADS) S.mask[i] = 0u;
-#if SFD_TMA
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar + 8u) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-#endif
     __syncthreads();
     sfw_first_load<0>(a, mp, S, 0);
 
@@ -760,15 +785,16 @@ sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd
 
     if (S.dead) {
         /* a slab transaction did not complete in time: report it, give the
-         * copies still in flight a bounded time to land, and leave */
+         * copies still in flight a bounded time to land, and stop */
         if (threadIdx.x == 0) {
             atomicOr(a.err, 1);
-#if SFD_TMA
-            sfw_wait(S.bar, (S.phase >> 0) & 1u);
-            sfw_wait(S.bar + 8u, (S.phase >> 1) & 1u);
-#endif
+            if (S.tma) {
+                sfw_wait(S.bar, (S.phase >> 0) & 1u);
+                sfw_wait(S.bar + 8u, (S.phase >> 1) & 1u);
+            }
         }
-        return;
+        if (!S.tma) sf_cp_wait<0>();
+        return false;
     }
     __syncthreads();
     /* mask words of the window: one owner lane per (row, word) */
@@ -780,8 +806,103 @@ sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd
                 a.mask[((S.x0 + p) * a.ny + S.y0 + S.row) * a.nw32 + gw] =
                     S.mask[(p * SFD_WY + S.row) * SFW_NW + wd];
     }
+    return true;
+}
+#endif
+
+#ifdef SF_KERNEL_DETECT
+extern "C" __global__ void __launch_bounds__(SFD_THREADS, SFD_MINB)
+sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_taps t,
+                 const __grid_constant__ sfw_maps mp)
+{
+    extern __shared__ __align__(128) unsigned char sfw_raw[];
+    sfw_state S;
+    sfw_init(S, sfw_raw);
+    sfw_window(a, t, mp.m, S, (int)blockIdx.x);
 }
 #endif /* SF_KERNEL_DETECT */
+
+/* ======================================================================= */
+#ifdef SF_KERNEL_PERSIST
+/*
+ * sf_persist: every unit's x pass and windows in one persistent launch.
+ * CTAs pull items from a global counter.  Items are ordered so that all x
+ * items of a unit come before its window items; a window item waits (bounded
+ * by %globaltimer) until the unit's x items are all complete.  x items never
+ * wait, and an item is only ever taken by a running CTA, so every wait ends.
+ * HBM-bound x items and ALU-bound window items of different units run side by
+ * side on the SMs.
+ */
+__device__ __forceinline__ bool sfp_wait_count(const int *ctr, int need)
+{
+    unsigned long long t0 = 0ull;
+    while (true) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= need) return true;
+        const unsigned long long now = sfw_clock();
+        if (t0 == 0ull) t0 = now;
+        else if (now - t0 > SFW_TIMEOUT_NS) return false;
+        __nanosleep(200);
+    }
+}
+
+extern "C" __global__ void __launch_bounds__(SFD_THREADS, SFD_MINB)
+sf_persist(const __grid_constant__ sf_pargs pa, const __grid_constant__ sfd_taps t,
+           const __grid_constant__ sfx_taps xt)
+{
+    extern __shared__ __align__(128) unsigned char sfp_raw[];
+    __shared__ int s_item;
+    sfw_state S;
+    sfw_init(S, sfp_raw);
+    const sf_tmap *maps = reinterpret_cast<const sf_tmap *>(pa.maps);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(pa.head, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= pa.n_items) break;
+        const sf_item it = pa.items[item];
+        const sf_unit &u = pa.units[it.unit];
+        if (it.kind == 0) {
+            /* x pass of lanes [index*xlanes, (index+1)*xlanes) over the unit's planes */
+            const i64 l0 = (i64)it.index * u.xlanes;
+            const i64 l1 = min(u.lanes, l0 + u.xlanes);
+            const sfx_t *src = reinterpret_cast<const sfx_t *>(u.xsrc);
+            void *dst[SFX_NOUT];
+#pragma unroll
+            for (int k = 0; k < SFX_NOUT; ++k) dst[k] = u.xdst[k];
+            const i64 nx = u.args.nx, plane = u.plane, x0 = u.x0, x1 = u.x1;
+            if (u.xv == 2) {
+                for (i64 l = l0 + threadIdx.x; l < l1; l += SFD_THREADS)
+                    sfx_lane<2>(src + 2 * l, dst, 2 * l, nx, plane, x0, x1, xt);
+            } else {
+                for (i64 l = l0 + threadIdx.x; l < l1; l += SFD_THREADS)
+                    sfx_lane<1>(src + l, dst, l, nx, plane, x0, x1, xt);
+            }
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(pa.xdone + it.unit, 1);
+        } else {
+            bool ok = true;
+            if (threadIdx.x == 0) {
+                ok = sfp_wait_count(pa.xdone + it.unit, u.n_xitems);
+                /* the x-filtered planes were written through the generic proxy
+                 * by other CTAs; order them before this CTA's TMA reads */
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(pa.err, 1);
+                return;
+            }
+            S.tma = u.tma != 0;
+            const int per = u.args.nwy * u.args.nwz;
+            const int wid = (u.wx0 + it.index / per) * per + it.index % per;
+            if (!sfw_window(u.args, t, maps + u.map_base, S, wid)) return;
+        }
+    }
+}
+#endif /* SF_KERNEL_PERSIST */
 /* ======================================================================= */
 #ifdef SF_KERNEL_FILTER
 /* one CTA per (x, y tile, z tile): y and z passes of a single filter */

@@ -38,6 +38,41 @@ struct sf_dargs {
     int *err;          /* set non-zero when a bounded wait expires */
 };
 
+/* Persistent batched kernel: a unit is one cube (or one x-slab of a cube)
+ * with its x pass split into items of lanes and its windows as items. */
+struct sf_unit {
+    struct sf_dargs args;       /* the cube's window-kernel arguments */
+    const void *xsrc;           /* x-pass input (the cube) */
+    void *xdst[SF_MAX_XOUT];    /* x-pass outputs (scratch slots of this cube) */
+    long long x0, x1;           /* x-planes of this unit (multiples of wx) */
+    long long plane;            /* ny * nz */
+    long long lanes;            /* plane / xv */
+    int xv;                     /* elements per x lane: 1 or 2 */
+    int tma;                    /* slabs by TMA (1) or cp.async (0) */
+    int map_base;               /* first tensor map of this unit */
+    int n_xitems;               /* x items of this unit */
+    int wx0;                    /* first window-grid x of this unit */
+    int xlanes;                 /* lanes per x item */
+};
+
+struct sf_item {
+    int unit;
+    int kind;                   /* 0: x lanes, 1: window */
+    int index;                  /* x item or window of the unit */
+    int pad_;
+};
+
+struct sf_pargs {
+    const struct sf_unit *units;
+    const struct sf_item *items;
+    const void *maps;           /* 64-byte aligned tensor maps */
+    int *head;                  /* next item (reset to 0 before each launch) */
+    int *xdone;                 /* per unit: x items completed (reset to 0) */
+    int *err;
+    int n_items;
+    int pad_;
+};
+
 /* y/z filter of one filter, writing float32 filtered values */
 struct sf_fargs {
     const void *src;

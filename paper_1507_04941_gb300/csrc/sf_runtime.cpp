@@ -245,6 +245,41 @@ struct sf_ctx {
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> pool;
 
+    /* persistent form: the cubes of a batched context (or the one cube of a
+     * plain context when the autotuner prefers it), one launch per call */
+    struct Cube {
+        long long nx, ny, nz, nw32;
+        int nwx, nwy, nwz, nwin;
+        size_t slot_bytes;            /* one x-filtered cube */
+        void *slots;                  /* n_xy scratch cubes */
+        bool tma;
+        int xv;
+    };
+    bool batch = false;               /* created by sf_create_batch */
+    bool use_persist = false;         /* sf_detect runs the persistent kernel */
+    std::vector<Cube> cubes;
+    void *bscratch = nullptr;         /* scratch of all cubes (batched contexts) */
+    struct PersistPlan {
+        int P = 8, minb = 3, pf = 2, xlanes = 1024, slab = 0;
+    } pp;
+    bool pready = false;
+    Launch plaunch;
+    std::vector<float> ptaps, pxtaps;
+    int pnsrc = 0, psrow = 0, prym = 0;
+    std::vector<DetectSource> psrc;
+    std::vector<sf_unit> units;       /* static fields; pointers filled per call */
+    std::vector<int> unit_cube;
+    int n_items = 0;
+    sf_unit *d_units = nullptr, *h_units = nullptr;
+    sf_item *d_items = nullptr;
+    CUtensorMap *d_maps = nullptr, *h_maps = nullptr;
+    int *d_ctr = nullptr;             /* [0] head, [1 + u] x items done of unit u */
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gdone = nullptr;
+    bool gpending = false;
+    std::string tune_report;
+
     std::string err;
     bool dead = false;
 };
@@ -483,37 +518,46 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-/* Tiled 3D tensor map of a cube [x][y][z] with box {SROW, WY + 2 RY, 1}. */
-bool encode_map(const sf_ctx *c, const void *base, int ry, CUtensorMap *out)
+/* Tiled 3D tensor map of a cube [x][y][z] with box {srow, WY + 2 RY, 1}. */
+bool encode_map_dims(const sf_ctx *c, const void *base, long long nx, long long ny, long long nz,
+                     int srow, int ry, CUtensorMap *out)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const CUtensorMapDataType dt = c->cfg.storage == SF_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : c->cfg.storage == SF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const cuuint64_t dims[3] = {(cuuint64_t)c->cfg.nz, (cuuint64_t)c->cfg.ny, (cuuint64_t)c->cfg.nx};
-    const cuuint64_t strides[2] = {(cuuint64_t)(c->cfg.nz * (long long)c->ebytes),
-                                   (cuuint64_t)(c->cfg.ny * c->cfg.nz * (long long)c->ebytes)};
-    const cuuint32_t box[3] = {(cuuint32_t)c->dSROW, (cuuint32_t)(c->cfg.wy + 2 * ry), 1u};
+    const cuuint64_t dims[3] = {(cuuint64_t)nz, (cuuint64_t)ny, (cuuint64_t)nx};
+    const cuuint64_t strides[2] = {(cuuint64_t)(nz * (long long)c->ebytes),
+                                   (cuuint64_t)(ny * nz * (long long)c->ebytes)};
+    const cuuint32_t box[3] = {(cuuint32_t)srow, (cuuint32_t)(c->cfg.wy + 2 * ry), 1u};
     const cuuint32_t es[3] = {1u, 1u, 1u};
     return enc(out, dt, 3, const_cast<void *>(base), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-/* The fused window kernel: one CTA per statistics window (see sf_kernels.cuh). */
-sf_status plan_detect(sf_ctx *c)
+bool encode_map(const sf_ctx *c, const void *base, int ry, CUtensorMap *out)
 {
-    const sf_config &g = c->cfg;
-    c->fused = false;
-    if (g.wy % 8 != 0 || g.wz % 32 != 0 || g.wx > 64) return SF_OK;
-    int P = 8;
-    const int penv = env_int("SF_WP", 0);
-    if ((penv == 8 || penv == 16) && g.wz % (4 * penv) == 0) P = penv;
-    const long long threads = (long long)g.wy * g.wz / P;
-    if (threads < 32 || threads > 1024) return SF_OK;
+    return encode_map_dims(c, base, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->dSROW, ry, out);
+}
 
-    /* inputs: the cube (sigma_xy = 0) first, then the scratch slots */
+/* Shape, shared-memory layout and parameter blocks of the window code (the
+ * stand-alone window kernel and the persistent kernel share it). */
+struct WindowPlan {
+    std::vector<DetectSource> srcs;
+    YZShape sh{};
+    int P = 8, minb = 3, nzf = 1, rym = 0, rzm = 0, threads = 0;
+    bool any_y = false;
+    size_t off_s0 = 0, off_s1 = 0, off_u = 0, off_pm = 0, off_mk = 0, off_rd = 0, off_th = 0,
+           off_fl = 0, off_mb = 0, smem = 0;
+    std::string prelude;        /* SFD_* definitions without the kernel selector */
+    std::vector<float> taps;    /* sfd_taps parameter block */
+};
+
+/* inputs of the window code: the cube (sigma_xy = 0) first, then the scratch slots */
+std::vector<DetectSource> window_sources(const sf_ctx *c)
+{
     std::vector<std::pair<int, std::vector<int>>> groups;   /* slot, filters */
     auto add = [&](int slot, int fi) {
         for (auto &gr : groups)
@@ -534,102 +578,378 @@ sf_status plan_detect(sf_ctx *c)
                              gr.second.begin() + std::min(gr.second.size(), i + (size_t)SF_MAX_NZF));
             srcs.push_back(d);
         }
-    if ((int)srcs.size() > SF_MAX_SRC) return SF_OK;
-    int rym = 0, rzm = 0, nzf = 1;
-    bool any_y = false;
-    for (auto &d : srcs) {
-        rym = std::max(rym, d.ry);
-        any_y |= d.ry > 0;
-        nzf = std::max(nzf, (int)d.filters.size());
-        for (int fi : d.filters) rzm = std::max(rzm, c->filt[fi].rz);
+    return srcs;
+}
+
+/* CH: elements per cp.async copy; tma_shape: halo and row pitch usable by TMA.
+ * Returns false when the window shape cannot be tiled by the window code. */
+bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, WindowPlan &wp)
+{
+    const sf_config &g = c->cfg;
+    if (g.wy % 8 != 0 || g.wz % 32 != 0 || g.wx > 64 || g.wz % (4 * P) != 0) return false;
+    const long long threads = (long long)g.wy * g.wz / P;
+    if (threads < 32 || threads > 1024) return false;
+    wp.srcs = window_sources(c);
+    if ((int)wp.srcs.size() > SF_MAX_SRC) return false;
+    wp.P = P;
+    wp.minb = minb;
+    wp.threads = (int)threads;
+    for (auto &d : wp.srcs) {
+        wp.rym = std::max(wp.rym, d.ry);
+        wp.any_y |= d.ry > 0;
+        wp.nzf = std::max(wp.nzf, (int)d.filters.size());
+        for (int fi : d.filters) wp.rzm = std::max(wp.rzm, c->filt[fi].rz);
     }
-    YZShape sh{};
+    YZShape &sh = wp.sh;
     sh.WY = g.wy;
     sh.WZ = g.wz;
     sh.threads = (int)threads;
-    sh.nzf = nzf;
-    sh.nsrc = (int)srcs.size();
-    yz_common_shape(c, sh, rym, rzm);
-    /* TMA needs 16-byte row pitches and boxes of at most 256 elements per axis */
+    sh.nzf = wp.nzf;
+    sh.nsrc = (int)wp.srcs.size();
+    sh.CH = CH;
     const int vec = (int)(16 / c->ebytes);
-    bool tma = (g.nz % vec == 0) && sh.SROW <= 256 && g.wy + 2 * rym <= 256 &&
-               tensor_map_encoder() != nullptr && env_int("SF_NO_TMA", 0) == 0;
-    if (tma) {
-        const int hzq = std::max(4, vec);
-        sh.HZ = (rzm + hzq - 1) / hzq * hzq;
-        const int uw = sh.WZ + 2 * sh.HZ;
-        sh.SROW = c->ebytes == 4 ? odd_quad_stride(uw + 4) : (int)align_up((size_t)uw + 4, 8);
-        sh.UROW = odd_quad_stride(uw + 4);
-        tma = sh.SROW <= 256;
-    }
+    const int hzq = std::max(std::max(4, CH), tma_shape ? vec : 1);
+    sh.HZ = (wp.rzm + hzq - 1) / hzq * hzq;
+    sh.RYM = wp.rym;
+    sh.RZM = wp.rzm;
+    const int uw = sh.WZ + 2 * sh.HZ;
+    sh.UROW = odd_quad_stride(uw + 4);
+    sh.SROW = c->ebytes == 4 ? odd_quad_stride(uw + 4) : (int)align_up((size_t)uw + 4, 8);
     const int nwarp = (int)threads / 32;
     const int nw = g.wz / 32;
     size_t off = 0;
-    const size_t slab = align_up((size_t)(sh.WY + 2 * rym) * sh.SROW * c->ebytes, 128);
-    const size_t off_s0 = off;
+    const size_t slab = align_up((size_t)(sh.WY + 2 * wp.rym) * sh.SROW * c->ebytes, 128);
+    wp.off_s0 = off;
     off += slab;
-    const size_t off_s1 = off;
+    wp.off_s1 = off;
     off += slab;
-    const size_t off_u = off;
-    off += any_y ? align_up((size_t)sh.WY * sh.UROW * 4, 128) : 0;
-    const size_t off_pm = off;
-    off += align_up((size_t)g.wx * nwarp * nzf * 4, 16);
-    const size_t off_mk = off;
+    wp.off_u = off;
+    off += wp.any_y ? align_up((size_t)sh.WY * sh.UROW * 4, 128) : 0;
+    wp.off_pm = off;
+    off += align_up((size_t)g.wx * nwarp * wp.nzf * 4, 16);
+    wp.off_mk = off;
     off += align_up((size_t)g.wx * g.wy * nw * 4, 16);
-    const size_t off_rd = off;
-    off += align_up((size_t)nwarp * nzf * 3 * 4, 16);
-    const size_t off_th = off;
-    off += align_up((size_t)nzf * 4, 16);
-    const size_t off_fl = off;
+    wp.off_rd = off;
+    off += align_up((size_t)nwarp * wp.nzf * 3 * 4, 16);
+    wp.off_th = off;
+    off += align_up((size_t)wp.nzf * 4, 16);
+    wp.off_fl = off;
     off += 16;
-    const size_t off_mb = off;
+    wp.off_mb = off;
     off += 16;
-    const size_t smem = off + 128;   /* the kernel aligns its base to 128 bytes */
-    if (smem > kSmemLimit) return SF_OK;
-
-    c->dsrc = srcs;
-    c->dSROW = sh.SROW;
-    c->dtma = tma;
-    std::string p = "#define SF_KERNEL_DETECT 1\n" + yz_prelude(c, sh, srcs);
+    wp.smem = off + 128;   /* the kernels align their base to 128 bytes */
+    if (wp.smem > kSmemLimit) return false;
+    std::string p = yz_prelude(c, sh, wp.srcs);
     p += "#define SFD_P " + std::to_string(P) + "\n";
     p += "#define SFD_WX " + std::to_string(g.wx) + "\n";
     /* resident CTAs per SM the register allocation must allow */
-    const int minb = std::max(1, std::min(8, env_int("SF_WMINB", P == 16 ? 3 : 3)));
     p += "#define SFD_MINB " + std::to_string(minb) + "\n";
+    p += "#define SFD_OFF_SLAB0 " + std::to_string(wp.off_s0) + "\n";
+    p += "#define SFD_OFF_SLAB1 " + std::to_string(wp.off_s1) + "\n";
+    p += "#define SFD_OFF_U " + std::to_string(wp.off_u) + "\n";
+    p += "#define SFD_OFF_PMAX " + std::to_string(wp.off_pm) + "\n";
+    p += "#define SFD_OFF_MASK " + std::to_string(wp.off_mk) + "\n";
+    p += "#define SFD_OFF_RED " + std::to_string(wp.off_rd) + "\n";
+    p += "#define SFD_OFF_THR " + std::to_string(wp.off_th) + "\n";
+    p += "#define SFD_OFF_FLAGS " + std::to_string(wp.off_fl) + "\n";
+    p += "#define SFD_OFF_MBAR " + std::to_string(wp.off_mb) + "\n";
+    wp.prelude = p;
+    wp.taps = yz_taps(c, sh, wp.srcs);
+    return true;
+}
+
+/* elements per cp.async copy for rows of nz elements */
+int copy_chunk(size_t ebytes, long long nz)
+{
+    const int vec = (int)(16 / ebytes);
+    if (nz % vec == 0) return vec;
+    if (ebytes == 4) return nz % 2 == 0 ? 2 : 1;
+    if (nz % 4 == 0) return 4;
+    if (nz % 2 == 0) return 2;
+    return 0;
+}
+
+/* TMA needs 16-byte row pitches and boxes of at most 256 elements per axis */
+bool tma_usable(const sf_ctx *c, const WindowPlan &wp, long long nz)
+{
+    const int vec = (int)(16 / c->ebytes);
+    return nz % vec == 0 && wp.sh.SROW <= 256 && c->cfg.wy + 2 * wp.rym <= 256 &&
+           tensor_map_encoder() != nullptr && env_int("SF_NO_TMA", 0) == 0;
+}
+
+/* The fused window kernel: one CTA per statistics window (see sf_kernels.cuh). */
+sf_status plan_detect(sf_ctx *c)
+{
+    const sf_config &g = c->cfg;
+    c->fused = false;
+    int P = 8;
+    const int penv = env_int("SF_WP", 0);
+    if ((penv == 8 || penv == 16) && g.wz % (4 * penv) == 0) P = penv;
+    const int minb = std::max(1, std::min(8, env_int("SF_WMINB", 3)));
+    WindowPlan wp;
+    if (!make_window_plan(c, P, minb, copy_chunk(c->ebytes, g.nz), true, wp)) return SF_OK;
+    const bool tma = tma_usable(c, wp, g.nz);
+    std::string p = "#define SF_KERNEL_DETECT 1\n" + wp.prelude;
     p += std::string("#define SFD_TMA ") + (tma ? "1" : "0") + "\n";
-    p += "#define SFD_OFF_SLAB0 " + std::to_string(off_s0) + "\n";
-    p += "#define SFD_OFF_SLAB1 " + std::to_string(off_s1) + "\n";
-    p += "#define SFD_OFF_U " + std::to_string(off_u) + "\n";
-    p += "#define SFD_OFF_PMAX " + std::to_string(off_pm) + "\n";
-    p += "#define SFD_OFF_MASK " + std::to_string(off_mk) + "\n";
-    p += "#define SFD_OFF_RED " + std::to_string(off_rd) + "\n";
-    p += "#define SFD_OFF_THR " + std::to_string(off_th) + "\n";
-    p += "#define SFD_OFF_FLAGS " + std::to_string(off_fl) + "\n";
-    p += "#define SFD_OFF_MBAR " + std::to_string(off_mb) + "\n";
     std::string err;
     sf_status s = jit_kernel(p, "sf_window_detect", c->device, &c->dlaunch.kernel, err);
     if (s != SF_OK) return fail(c, s, "window kernel: %s", err.c_str());
-    c->dlaunch.smem = smem;
-    if (smem > 48 * 1024 && (s = set_smem(c, c->dlaunch.kernel, smem)) != SF_OK) return s;
-    c->dlaunch.block = dim3((unsigned)threads);
+    c->dlaunch.smem = wp.smem;
+    if (wp.smem > 48 * 1024 && (s = set_smem(c, c->dlaunch.kernel, wp.smem)) != SF_OK) return s;
+    c->dlaunch.block = dim3((unsigned)wp.threads);
     c->dlaunch.grid = dim3((unsigned)c->nwin);
-    c->dnzf = nzf;
+    c->dsrc = wp.srcs;
+    c->dSROW = wp.sh.SROW;
+    c->dtma = tma;
+    c->dnzf = wp.nzf;
     c->dP = P;
-    c->dthreads = (int)threads;
-    c->dHZ = sh.HZ;
-    c->dCH = sh.CH;
-    c->dUROW = sh.UROW;
-    c->dRYM = rym;
-    c->dRZM = rzm;
-    c->dtaps = yz_taps(c, sh, srcs);
-    c->dmaps.assign(srcs.size(), CUtensorMap{});
+    c->dthreads = wp.threads;
+    c->dHZ = wp.sh.HZ;
+    c->dCH = wp.sh.CH;
+    c->dUROW = wp.sh.UROW;
+    c->dRYM = wp.rym;
+    c->dRZM = wp.rzm;
+    c->dtaps = wp.taps;
+    c->dmaps.assign(wp.srcs.size(), CUtensorMap{});
     if (tma)
-        for (size_t i = 0; i < srcs.size(); ++i)
-            if (srcs[i].slot >= 0 &&
-                !encode_map(c, (const char *)c->scratch + (size_t)srcs[i].slot * c->cube_bytes,
-                            srcs[i].ry, &c->dmaps[i]))
+        for (size_t i = 0; i < wp.srcs.size(); ++i)
+            if (wp.srcs[i].slot >= 0 &&
+                !encode_map(c, (const char *)c->scratch + (size_t)wp.srcs[i].slot * c->cube_bytes,
+                            wp.srcs[i].ry, &c->dmaps[i]))
                 return fail(c, SF_ECUDA, "tensor map encoding failed");
     c->fused = true;
+    return SF_OK;
+}
+
+/* ------------------------------------------------- persistent form --- */
+void free_persist(sf_ctx *c)
+{
+    if (c->gpending && c->gdone) cudaEventSynchronize(c->gdone);
+    c->gpending = false;
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->gdone) cudaEventDestroy(c->gdone);
+    cudaFree(c->d_units);
+    cudaFree(c->d_items);
+    cudaFree(c->d_maps);
+    cudaFree(c->d_ctr);
+    cudaFreeHost(c->h_units);
+    cudaFreeHost(c->h_maps);
+    c->gexec = nullptr;
+    c->gstream = nullptr;
+    c->gdone = nullptr;
+    c->d_units = c->h_units = nullptr;
+    c->d_items = nullptr;
+    c->d_maps = c->h_maps = nullptr;
+    c->d_ctr = nullptr;
+    c->units.clear();
+    c->unit_cube.clear();
+    c->pready = false;
+}
+
+/* Plan, compile and capture the persistent kernel for c->cubes. */
+sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
+{
+    free_persist(c);
+    const sf_config &g = c->cfg;
+    const int nxy = (int)c->xy_sigma.size();
+    if (nxy > SF_MAX_XOUT) return fail(c, SF_EINVAL, "the persistent form takes at most %d distinct sigma_xy", SF_MAX_XOUT);
+    /* copies for cubes that cannot use TMA: the largest chunk all their rows allow */
+    const int vec = (int)(16 / c->ebytes);
+    int ch = vec;
+    for (const sf_ctx::Cube &q : c->cubes)
+        if (q.nz % vec != 0) ch = std::min(ch, copy_chunk(c->ebytes, q.nz));
+    WindowPlan wp;
+    if (!make_window_plan(c, pp.P, pp.minb, ch, true, wp))
+        return fail(c, SF_EINVAL, "window %dx%dx%d cannot be tiled by the persistent kernel (wy %% 8, "
+                    "wz %% 32, wx <= 64)", g.wx, g.wy, g.wz);
+    for (sf_ctx::Cube &q : c->cubes) {
+        q.tma = tma_usable(c, wp, q.nz);
+        q.xv = (q.ny * q.nz) % 2 == 0 && c->ebytes == 4 ? 2 : 1;
+    }
+    int r[4] = {0, 0, 0, 0}, rm = 0;
+    for (int i = 0; i < nxy; ++i) {
+        r[i] = c->xy_radius[i];
+        rm = std::max(rm, r[i]);
+    }
+    std::string p = "#define SF_KERNEL_PERSIST 1\n" + wp.prelude + "#define SFD_TMA 1\n";
+    p += "#define SFX_NOUT " + std::to_string(std::max(1, nxy)) + "\n";
+    for (int i = 0; i < 4; ++i) p += "#define SFX_R" + std::to_string(i) + " " + std::to_string(r[i]) + "\n";
+    p += "#define SFX_RM " + std::to_string(rm) + "\n";
+    p += "#define SFX_PF " + std::to_string(pp.pf) + "\n";
+    p += std::string("typedef ") + storage_ctype(g.storage) + " sfx_t;\n";
+    std::string err;
+    sf_status st = jit_kernel(p, "sf_persist", c->device, &c->plaunch.kernel, err);
+    if (st != SF_OK) return fail(c, st, "persistent kernel: %s", err.c_str());
+    if (wp.smem > 48 * 1024 && (st = set_smem(c, c->plaunch.kernel, wp.smem)) != SF_OK) return st;
+    int per_sm = 0, nsm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)c->plaunch.kernel,
+                                                                  wp.threads, wp.smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
+    c->pp = pp;
+    c->ptaps = wp.taps;
+    std::vector<int> all;
+    for (int i = 0; i < nxy; ++i) all.push_back(i);
+    c->pxtaps = nxy ? xpass_taps(c, all) : std::vector<float>(1, 1.f);
+    c->psrc = wp.srcs;
+    c->pnsrc = (int)wp.srcs.size();
+    c->psrow = wp.sh.SROW;
+    c->prym = wp.rym;
+
+    /* units: each cube, or x-slabs of it (multiples of wx) */
+    std::vector<int> unit_windows;
+    for (size_t i = 0; i < c->cubes.size(); ++i) {
+        const sf_ctx::Cube &q = c->cubes[i];
+        long long slab = pp.slab > 0 ? ((long long)pp.slab + g.wx - 1) / g.wx * g.wx : q.nx;
+        if (slab <= 0) slab = q.nx;
+        for (long long x0 = 0; x0 < q.nx; x0 += slab) {
+            sf_unit u{};
+            u.x0 = x0;
+            u.x1 = std::min(q.nx, x0 + slab);
+            u.plane = q.ny * q.nz;
+            u.xv = q.xv;
+            u.lanes = u.plane / q.xv;
+            u.tma = q.tma ? 1 : 0;
+            u.map_base = (int)i * c->pnsrc;
+            u.xlanes = pp.xlanes;
+            u.n_xitems = nxy > 0 ? (int)((u.lanes + pp.xlanes - 1) / pp.xlanes) : 0;
+            u.wx0 = (int)(x0 / g.wx);
+            const int nwxu = (int)((u.x1 - x0 + g.wx - 1) / g.wx);
+            c->units.push_back(u);
+            c->unit_cube.push_back((int)i);
+            unit_windows.push_back(nwxu * q.nwy * q.nwz);
+        }
+    }
+    /* items: x items of unit k+1 come before the windows of unit k */
+    std::vector<sf_item> items;
+    const int nu = (int)c->units.size();
+    auto push_x = [&](int u) {
+        for (int j = 0; j < c->units[u].n_xitems; ++j) items.push_back(sf_item{u, 0, j, 0});
+    };
+    if (nu > 0) push_x(0);
+    for (int u = 0; u < nu; ++u) {
+        if (u + 1 < nu) push_x(u + 1);
+        for (int j = 0; j < unit_windows[u]; ++j) items.push_back(sf_item{u, 1, j, 0});
+    }
+    c->n_items = (int)items.size();
+    const size_t nmaps = c->cubes.size() * (size_t)c->pnsrc;
+    if ((e = cudaMalloc(&c->d_units, sizeof(sf_unit) * nu)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_items, sizeof(sf_item) * std::max<size_t>(1, items.size()))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_maps, sizeof(CUtensorMap) * std::max<size_t>(1, nmaps))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_ctr, sizeof(int) * (1 + nu))) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_units, sizeof(sf_unit) * nu)) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_maps, sizeof(CUtensorMap) * std::max<size_t>(1, nmaps))) != cudaSuccess) {
+        cudaGetLastError();
+        free_persist(c);
+        return fail(c, SF_ENOMEM, "persistent-form tables");
+    }
+    std::memset(c->h_maps, 0, sizeof(CUtensorMap) * std::max<size_t>(1, nmaps));
+    if (!items.empty() &&
+        (e = cudaMemcpy(c->d_items, items.data(), sizeof(sf_item) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(c, e, "item table");
+    /* tensor maps of the scratch inputs do not change between calls */
+    for (size_t i = 0; i < c->cubes.size(); ++i) {
+        const sf_ctx::Cube &q = c->cubes[i];
+        if (!q.tma) continue;
+        for (int sidx = 0; sidx < c->pnsrc; ++sidx) {
+            const DetectSource &d = c->psrc[sidx];
+            if (d.slot < 0) continue;
+            if (!encode_map_dims(c, (const char *)q.slots + (size_t)d.slot * q.slot_bytes, q.nx, q.ny, q.nz,
+                                 c->psrow, d.ry, &c->h_maps[i * c->pnsrc + sidx]))
+                return fail(c, SF_ECUDA, "tensor map encoding failed");
+        }
+    }
+    c->plaunch.block = dim3((unsigned)wp.threads);
+    c->plaunch.grid = dim3((unsigned)std::max(1, std::min(per_sm * nsm, std::max(1, c->n_items))));
+    c->plaunch.smem = wp.smem;
+
+    /* capture: reset the counters, stage the tables, launch */
+    if ((e = cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&c->gdone, cudaEventDisableTiming)) != cudaSuccess)
+        return cuda_fail(c, e, "graph stream");
+    sf_pargs pa{};
+    pa.units = c->d_units;
+    pa.items = c->d_items;
+    pa.maps = c->d_maps;
+    pa.head = c->d_ctr;
+    pa.xdone = c->d_ctr + 1;
+    pa.err = c->err_flag;
+    pa.n_items = c->n_items;
+    cudaGraph_t graph = nullptr;
+    if ((e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+        return cuda_fail(c, e, "graph capture");
+    cudaMemsetAsync(c->d_ctr, 0, sizeof(int) * (1 + nu), c->gstream);
+    cudaMemcpyAsync(c->d_units, c->h_units, sizeof(sf_unit) * nu, cudaMemcpyHostToDevice, c->gstream);
+    cudaMemcpyAsync(c->d_maps, c->h_maps, sizeof(CUtensorMap) * std::max<size_t>(1, nmaps),
+                    cudaMemcpyHostToDevice, c->gstream);
+    void *args[] = {&pa, c->ptaps.data(), c->pxtaps.data()};
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = c->plaunch.grid;
+    lc.blockDim = c->plaunch.block;
+    lc.dynamicSmemBytes = c->plaunch.smem;
+    lc.stream = c->gstream;
+    cudaError_t le = cudaLaunchKernelExC(&lc, (const void *)c->plaunch.kernel, args);
+    e = cudaStreamEndCapture(c->gstream, &graph);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(c, e, "persistent graph");
+    c->pready = true;
+    return SF_OK;
+}
+
+/* One replay of the persistent graph over the given cubes. */
+sf_status run_persist(sf_ctx *c, const void *const *cubes, uint32_t *const *masks, float *const *means,
+                      float *const *stds, cudaStream_t st)
+{
+    if (!c->pready) return fail(c, SF_ESTATE, "persistent form not planned");
+    cudaError_t e;
+    if (c->gpending && (e = cudaEventSynchronize(c->gdone)) != cudaSuccess)
+        return cuda_fail(c, e, "previous batch");
+    c->gpending = false;
+    const sf_config &g = c->cfg;
+    for (size_t u = 0; u < c->units.size(); ++u) {
+        const int i = c->unit_cube[u];
+        const sf_ctx::Cube &q = c->cubes[i];
+        sf_unit h = c->units[u];
+        sf_dargs &a = h.args;
+        for (int sidx = 0; sidx < c->pnsrc; ++sidx) {
+            const DetectSource &d = c->psrc[sidx];
+            a.src[sidx] = d.slot < 0 ? cubes[i] : (const void *)((const char *)q.slots + (size_t)d.slot * q.slot_bytes);
+            for (size_t f = 0; f < d.filters.size(); ++f) a.fidx[sidx][f] = d.filters[f];
+        }
+        a.mask = masks[i];
+        a.mean = means ? means[i] : nullptr;
+        a.stdv = stds ? stds[i] : nullptr;
+        if ((a.mean == nullptr) != (a.stdv == nullptr)) return fail(c, SF_EINVAL, "mean/std of cube %d", i);
+        a.nx = q.nx;
+        a.ny = q.ny;
+        a.nz = q.nz;
+        a.nw32 = q.nw32;
+        a.nwx = q.nwx;
+        a.nwy = q.nwy;
+        a.nwz = q.nwz;
+        a.nwin = q.nwin;
+        a.k = g.k;
+        a.err = c->err_flag;
+        h.xsrc = cubes[i];
+        for (int k = 0; k < SF_MAX_XOUT; ++k)
+            h.xdst[k] = k < (int)c->xy_sigma.size() ? (void *)((char *)q.slots + (size_t)k * q.slot_bytes) : nullptr;
+        c->h_units[u] = h;
+    }
+    for (size_t i = 0; i < c->cubes.size(); ++i) {
+        const sf_ctx::Cube &q = c->cubes[i];
+        if (!q.tma) continue;
+        for (int sidx = 0; sidx < c->pnsrc; ++sidx)
+            if (c->psrc[sidx].slot < 0 &&
+                !encode_map_dims(c, cubes[i], q.nx, q.ny, q.nz, c->psrow, c->psrc[sidx].ry,
+                                 &c->h_maps[i * c->pnsrc + sidx]))
+                return fail(c, SF_ECUDA, "tensor map encoding of cube %zu failed", i);
+    }
+    if ((e = cudaGraphLaunch(c->gexec, st)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    if ((e = cudaEventRecord(c->gdone, st)) != cudaSuccess) return cuda_fail(c, e, "graph event");
+    c->gpending = true;
     return SF_OK;
 }
 
@@ -715,12 +1035,23 @@ const char *sf_last_error(const sf_ctx *ctx)
     return copy.c_str();
 }
 
-sf_status sf_create(const sf_config *cfg, sf_ctx **out)
+/* Plain context (n == 0: the cube of cfg) or batched context (n cubes of dims). */
+static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *dims, sf_ctx **out)
 {
     if (!out) return fail(nullptr, SF_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!cfg) return fail(nullptr, SF_EINVAL, "cfg is NULL");
-    const sf_config &g = *cfg;
+    if (!cfg_in) return fail(nullptr, SF_EINVAL, "cfg is NULL");
+    sf_config g = *cfg_in;
+    if (n < 0 || n > (1 << 20) || (n > 0 && !dims)) return fail(nullptr, SF_EINVAL, "batch of %d cubes", n);
+    for (int i = 0; i < n; ++i)
+        if (dims[3 * i] < 1 || dims[3 * i + 1] < 1 || dims[3 * i + 2] < 1 || dims[3 * i] > (1LL << 31) ||
+            dims[3 * i + 1] > (1LL << 31) || dims[3 * i + 2] > (1LL << 31))
+            return fail(nullptr, SF_EINVAL, "cube %d: dimensions must be in [1, 2^31]", i);
+    if (n > 0) {
+        g.nx = dims[0];
+        g.ny = dims[1];
+        g.nz = dims[2];
+    }
     if (g.nx < 1 || g.ny < 1 || g.nz < 1)
         return fail(nullptr, SF_EINVAL, "cube dimensions must be >= 1 (got %lld x %lld x %lld)",
                     (long long)g.nx, (long long)g.ny, (long long)g.nz);
@@ -805,6 +1136,57 @@ sf_status sf_create(const sf_config *cfg, sf_ctx **out)
     if (nseg > 1) c->xseg = (g.nx + nseg - 1) / nseg;
     c->cube_bytes = align_up((size_t)c->nvox * c->ebytes, 256);
     sf_status s = SF_OK;
+    {
+        cudaError_t e = cudaMalloc(&c->err_flag, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(c->err_flag, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete c;
+            return fail(nullptr, SF_ENOMEM, "error flag allocation failed");
+        }
+    }
+    if (n > 0) {
+        /* batched context: scratch of every cube in one allocation, one persistent plan */
+        c->batch = true;
+        size_t total = 0;
+        for (int i = 0; i < n; ++i) {
+            sf_ctx::Cube q{};
+            q.nx = dims[3 * i];
+            q.ny = dims[3 * i + 1];
+            q.nz = dims[3 * i + 2];
+            q.nw32 = (q.nz + 31) / 32;
+            q.nwx = (int)((q.nx + g.wx - 1) / g.wx);
+            q.nwy = (int)((q.ny + g.wy - 1) / g.wy);
+            q.nwz = (int)((q.nz + g.wz - 1) / g.wz);
+            q.nwin = q.nwx * q.nwy * q.nwz;
+            q.slot_bytes = align_up((size_t)(q.nx * q.ny * q.nz) * c->ebytes, 256);
+            total += q.slot_bytes * c->xy_sigma.size();
+            c->cubes.push_back(q);
+        }
+        if (total > 0) {
+            cudaError_t e = cudaMalloc(&c->bscratch, total);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                s = fail(c, SF_ENOMEM, "batch scratch allocation of %zu bytes failed", total);
+            }
+        }
+        size_t off = 0;
+        for (sf_ctx::Cube &q : c->cubes) {
+            q.slots = c->bscratch ? (char *)c->bscratch + off : nullptr;
+            off += q.slot_bytes * c->xy_sigma.size();
+        }
+        if (s == SF_OK) s = plan_persist(c, sf_ctx::PersistPlan{});
+        if (s != SF_OK) {
+            {
+                std::lock_guard<std::mutex> lk(g_err_mu);
+                g_create_error = c->err;
+            }
+            sf_destroy(c);
+            return s;
+        }
+        *out = c;
+        return SF_OK;
+    }
     if (!c->xy_sigma.empty()) {
         cudaError_t e = cudaMalloc(&c->scratch, c->cube_bytes * c->xy_sigma.size());
         if (e != cudaSuccess) {
@@ -822,14 +1204,6 @@ sf_status sf_create(const sf_config *cfg, sf_ctx **out)
             c->xlaunch.push_back(L);
         }
     }
-    if (s == SF_OK) {
-        cudaError_t e = cudaMalloc(&c->err_flag, sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(c->err_flag, 0, sizeof(int));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            s = fail(c, SF_ENOMEM, "error flag allocation failed");
-        }
-    }
     if (s == SF_OK) s = plan_detect(c);
     if (s != SF_OK) {
         {
@@ -843,12 +1217,28 @@ sf_status sf_create(const sf_config *cfg, sf_ctx **out)
     return SF_OK;
 }
 
+sf_status sf_create(const sf_config *cfg, sf_ctx **out)
+{
+    return create_impl(cfg, 0, nullptr, out);
+}
+
+sf_status sf_create_batch(const sf_config *cfg, int32_t n, const int64_t *dims, sf_ctx **out)
+{
+    if (n < 1) {
+        if (out) *out = nullptr;
+        return fail(nullptr, SF_EINVAL, "a batch needs at least one cube");
+    }
+    return create_impl(cfg, n, dims, out);
+}
+
 sf_status sf_destroy(sf_ctx *c)
 {
     if (!c) return SF_OK;
     DeviceGuard dg(c->device);
     cudaDeviceSynchronize();
     cudaGetLastError();
+    free_persist(c);
+    cudaFree(c->bscratch);
     cudaFree(c->scratch);
     cudaFree(c->filt_scratch);
     cudaFree(c->stat_scratch);
@@ -901,6 +1291,7 @@ sf_status sf_filter(sf_ctx *c, const void *d_cube, int32_t filter, float *d_filt
 {
     sf_status s = check_live(c);
     if (s != SF_OK) return s;
+    if (c->batch) return fail(c, SF_EINVAL, "batched context: use sf_detect_batch");
     if (filter < 0 || filter >= (int)c->filt.size()) return fail(c, SF_EINVAL, "filter index %d", filter);
     if (!d_cube || !d_filtered) return fail(c, SF_EINVAL, "NULL buffer");
     if (!aligned16(d_cube) || !aligned16(d_filtered)) return fail(c, SF_EINVAL, "buffers must be 16-byte aligned");
@@ -939,6 +1330,7 @@ sf_status sf_stats(sf_ctx *c, const float *d_filtered, float *d_mean, float *d_s
 {
     sf_status s = check_live(c);
     if (s != SF_OK) return s;
+    if (c->batch) return fail(c, SF_EINVAL, "batched context: use sf_detect_batch");
     if (!d_filtered || !d_mean || !d_std) return fail(c, SF_EINVAL, "NULL buffer");
     DeviceGuard dg(c->device);
     const sf_config &g = c->cfg;
@@ -953,6 +1345,7 @@ sf_status sf_threshold(sf_ctx *c, const float *d_filtered, const float *d_mean, 
 {
     sf_status s = check_live(c);
     if (s != SF_OK) return s;
+    if (c->batch) return fail(c, SF_EINVAL, "batched context: use sf_detect_batch");
     if (!d_filtered || !d_mean || !d_std || !d_mask) return fail(c, SF_EINVAL, "NULL buffer");
     DeviceGuard dg(c->device);
     const sf_config &g = c->cfg;
@@ -972,8 +1365,19 @@ sf_status sf_detect(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_me
     if ((d_mean == nullptr) != (d_std == nullptr))
         return fail(c, SF_EINVAL, "d_mean and d_std must both be NULL or both be set");
     if (!aligned16(d_cube)) return fail(c, SF_EINVAL, "cube must be 16-byte aligned");
+    if (c->batch) return fail(c, SF_EINVAL, "batched context: use sf_detect_batch");
     DeviceGuard dg(c->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (c->use_persist) {
+        StageTimer tp(c, 1, st);
+        const void *cubes[1] = {d_cube};
+        uint32_t *masks[1] = {d_mask};
+        float *means[1] = {d_mean};
+        float *stds[1] = {d_std};
+        s = run_persist(c, cubes, masks, d_mean ? means : nullptr, d_std ? stds : nullptr, st);
+        if (s == SF_OK) tp.done(1);
+        return s;
+    }
     {
         StageTimer tx(c, 0, st);
         for (size_t i = 0; i < c->xlaunch.size(); ++i)
@@ -1031,6 +1435,137 @@ sf_status sf_detect(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_me
     return SF_OK;
 }
 
+sf_status sf_detect_batch(sf_ctx *c, const void *const *d_cubes, uint32_t *const *d_masks,
+                          float *const *d_means, float *const *d_stds, void *stream)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (!c->batch) return fail(c, SF_EINVAL, "not a batched context (sf_create_batch)");
+    if (!d_cubes || !d_masks) return fail(c, SF_EINVAL, "NULL pointer array");
+    if ((d_means == nullptr) != (d_stds == nullptr))
+        return fail(c, SF_EINVAL, "d_means and d_stds must both be NULL or both be set");
+    for (size_t i = 0; i < c->cubes.size(); ++i) {
+        if (!d_cubes[i] || !d_masks[i]) return fail(c, SF_EINVAL, "cube %zu: NULL buffer", i);
+        if (!aligned16(d_cubes[i])) return fail(c, SF_EINVAL, "cube %zu must be 16-byte aligned", i);
+    }
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    StageTimer tp(c, 1, st);
+    s = run_persist(c, d_cubes, d_masks, d_means, d_stds, st);
+    if (s == SF_OK) tp.done(1);
+    return s;
+}
+
+extern "C++" {
+namespace {
+/* milliseconds per call of fn on stream st (1 warm-up, reps timed) */
+template <class F>
+float time_calls(sf_ctx *c, cudaStream_t st, int reps, F fn, sf_status *s)
+{
+    *s = fn();
+    if (*s != SF_OK) return -1.f;
+    cudaEvent_t a = take_event(c), b = take_event(c);
+    if (!a || !b) {
+        *s = fail(c, SF_ECUDA, "events");
+        return -1.f;
+    }
+    cudaEventRecord(a, st);
+    for (int i = 0; i < reps && *s == SF_OK; ++i) *s = fn();
+    cudaEventRecord(b, st);
+    float ms = -1.f;
+    if (*s == SF_OK && cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess)
+        ms /= reps;
+    c->pool.push_back(a);
+    c->pool.push_back(b);
+    return ms;
+}
+}  // namespace
+}
+
+sf_status sf_tune(sf_ctx *c, const void *const *d_cubes, uint32_t *const *d_masks, void *stream)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (!d_cubes || !d_masks) return fail(c, SF_EINVAL, "NULL pointer array");
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool prof = c->prof;
+    c->prof = false;
+    std::string rep = "[";
+    float best = 1e30f;
+    int best_kind = -1;   /* -1: two-kernel path, else index into cands */
+    std::vector<sf_ctx::PersistPlan> cands;
+    const long long maxnx = c->batch ? 0 : c->cfg.nx;
+    for (int slab : {0, 128, 256}) {
+        if (!c->batch && slab > 0 && slab >= maxnx) continue;
+        for (int xl : {1024, 4096}) {
+            sf_ctx::PersistPlan q;
+            q.slab = slab;
+            q.xlanes = xl;
+            cands.push_back(q);
+        }
+    }
+    if (!c->batch) {
+        /* the two-kernel path is the first candidate of a plain context */
+        c->use_persist = false;
+        const float ms = time_calls(c, st, 3, [&] { return sf_detect(c, d_cubes[0], d_masks[0], nullptr, nullptr, stream); }, &s);
+        if (s != SF_OK) { c->prof = prof; return s; }
+        rep += "{\"path\": \"x pass + window kernel\", \"ms\": " + std::to_string(ms) + "}";
+        best = ms;
+        c->cubes.clear();
+        sf_ctx::Cube q{};
+        q.nx = c->cfg.nx;
+        q.ny = c->cfg.ny;
+        q.nz = c->cfg.nz;
+        q.nw32 = c->nw32;
+        q.nwx = c->nwx;
+        q.nwy = c->nwy;
+        q.nwz = c->nwz;
+        q.nwin = c->nwin;
+        q.slot_bytes = c->cube_bytes;
+        q.slots = c->scratch;
+        c->cubes.push_back(q);
+    }
+    for (size_t k = 0; k < cands.size(); ++k) {
+        if ((s = plan_persist(c, cands[k])) != SF_OK) break;
+        const float ms = time_calls(c, st, 3, [&] {
+            return run_persist(c, d_cubes, d_masks, nullptr, nullptr, st);
+        }, &s);
+        if (s != SF_OK) break;
+        if (rep.size() > 1) rep += ", ";
+        rep += "{\"path\": \"persistent\", \"slab\": " + std::to_string(cands[k].slab) +
+               ", \"x_lanes_per_item\": " + std::to_string(cands[k].xlanes) + ", \"ms\": " + std::to_string(ms) + "}";
+        if (ms > 0.f && ms < best) {
+            best = ms;
+            best_kind = (int)k;
+        }
+    }
+    rep += "]";
+    c->tune_report = rep;
+    if (s == SF_OK) {
+        if (best_kind >= 0) {
+            s = plan_persist(c, cands[best_kind]);
+            c->use_persist = !c->batch;
+        } else {
+            free_persist(c);
+            c->use_persist = false;
+        }
+    }
+    if (s == SF_OK && (s = sf_synchronize(c, stream)) != SF_OK) {
+        c->prof = prof;
+        return s;
+    }
+    c->prof = prof;
+    return s;
+}
+
+sf_status sf_tune_report(const sf_ctx *c, char *buf, int32_t cap)
+{
+    if (!c || !buf || cap < 1) return SF_EINVAL;
+    std::snprintf(buf, (size_t)cap, "%s", c->tune_report.c_str());
+    return (int)c->tune_report.size() < cap ? SF_OK : SF_EINVAL;
+}
+
 sf_status sf_profile_enable(sf_ctx *c, int32_t enable)
 {
     if (!c) return SF_EINVAL;
@@ -1067,6 +1602,7 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
 {
     sf_status s = check_live(c);
     if (s != SF_OK) return s;
+    if (c->batch) return fail(c, SF_EINVAL, "batched context: use sf_detect_batch");
     if (!h_cube || !h_mask) return fail(c, SF_EINVAL, "NULL buffer");
     DeviceGuard dg(c->device);
     const size_t cube = (size_t)c->nvox * c->ebytes;

@@ -61,6 +61,12 @@ SIGNATURES = {
     "sf_detect": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sf_detect_host": (_i32, [_vp, _vp, _vp, _vp]),
     "sf_synchronize": (_i32, [_vp, _vp]),
+    "sf_create_batch": (_i32, [ctypes.POINTER(Config), _i32, ctypes.POINTER(_i64),
+                               ctypes.POINTER(_vp)]),
+    "sf_detect_batch": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                               ctypes.POINTER(_vp), _vp]),
+    "sf_tune": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
+    "sf_tune_report": (_i32, [_vp, ctypes.c_char_p, _i32]),
     "sf_filter_noalloc": (_i32, [_vp, _i64, _i64, _i64, ctypes.c_float, ctypes.c_float,
                                  ctypes.c_float, _vp, _vp]),
     "sf_profile_enable": (_i32, [_vp, _i32]),
@@ -245,6 +251,17 @@ class SourceFinder:
                                     _stream(self.device)), self._h)
         return mask_host
 
+    def tune(self, cube, mask=None):
+        """Autotune the launch path on this cube (blocking); returns the timings report."""
+        import torch
+        self._check_cube(cube)
+        if mask is None:
+            mask = torch.empty(self.mask_shape, dtype=torch.int32, device=self.device)
+        cubes = (_vp * 1)(cube.data_ptr())
+        masks = (_vp * 1)(mask.data_ptr())
+        _check(lib().sf_tune(self._h, cubes, masks, _stream(self.device)), self._h)
+        return tune_report(self._h)
+
     def synchronize(self):
         """Wait for this context's work on the current stream; raise on kernel-side timeouts."""
         _check(lib().sf_synchronize(self._h, _stream(self.device)), self._h)
@@ -259,6 +276,115 @@ class SourceFinder:
         nl = (_i64 * n_stages)()
         _check(lib().sf_profile_read(self._h, ms, nl, n_stages), self._h)
         return {i: (ms[i], nl[i]) for i in range(n_stages)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def tune_report(handle) -> str:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().sf_tune_report(handle, buf, len(buf)), handle)
+    return buf.value.decode()
+
+
+class BatchSourceFinder:
+    """Many cubes of different shapes, one filter bank (wraps a batched sf_ctx)."""
+
+    def __init__(self, shapes, bank, truncation: float = 3.0, window=(32, 32, 64), k: float = 4.0,
+                 storage: str = "f32", device=None):
+        import torch
+        self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
+        self.bank = tuple((float(a), float(b)) for a, b in bank)
+        self.window = tuple(int(w) for w in window)
+        self.storage = storage
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        specs = (FilterSpec * len(self.bank))(*[FilterSpec(a, b) for a, b in self.bank])
+        self._specs = specs
+        cfg = Config(1, 1, 1, len(self.bank), specs, float(truncation), self.window[0],
+                     self.window[1], self.window[2], float(k), STORAGE[storage], 0,
+                     self.device.index if self.device.index is not None else -1)
+        dims = (_i64 * (3 * len(self.shapes)))(*[v for sh in self.shapes for v in sh])
+        h = _vp()
+        _check(lib().sf_create_batch(ctypes.byref(cfg), len(self.shapes), dims, ctypes.byref(h)),
+               None)
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def mask_shape(self, i):
+        nx, ny, nz = self.shapes[i]
+        return (nx, ny, -(-nz // 32))
+
+    def grid(self, i):
+        return tuple(-(-n // w) for n, w in zip(self.shapes[i], self.window))
+
+    def _arrays(self, cubes, masks, means=None, stds=None):
+        n = len(self.shapes)
+        if len(cubes) != n or len(masks) != n:
+            raise ValueError(f"expected {n} cubes and masks")
+        arr = lambda ts: (_vp * n)(*[_ptr(t) for t in ts])  # noqa: E731
+        return (arr(cubes), arr(masks), arr(means) if means is not None else None,
+                arr(stds) if stds is not None else None)
+
+    def detect(self, cubes, masks=None, stats: bool = False):
+        import torch
+        dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.storage]
+        for i, c in enumerate(cubes):
+            if tuple(c.shape) != self.shapes[i] or c.dtype != dt or not c.is_contiguous() \
+                    or c.device != self.device:
+                raise ValueError(f"cube {i} must be a contiguous {dt} tensor of shape "
+                                 f"{self.shapes[i]} on {self.device}")
+        if masks is None:
+            masks = [torch.empty(self.mask_shape(i), dtype=torch.int32, device=self.device)
+                     for i in range(len(cubes))]
+        means = stds = None
+        if stats:
+            means = [torch.empty((len(self.bank),) + self.grid(i), dtype=torch.float32,
+                                 device=self.device) for i in range(len(cubes))]
+            stds = [torch.empty_like(m) for m in means]
+        c_arr, m_arr, me_arr, sd_arr = self._arrays(cubes, masks, means, stds)
+        _check(lib().sf_detect_batch(self._h, c_arr, m_arr, me_arr, sd_arr, _stream(self.device)),
+               self._h)
+        return (masks, means, stds) if stats else masks
+
+    def tune(self, cubes, masks=None):
+        import torch
+        if masks is None:
+            masks = [torch.empty(self.mask_shape(i), dtype=torch.int32, device=self.device)
+                     for i in range(len(cubes))]
+        c_arr, m_arr, _, _ = self._arrays(cubes, masks)
+        _check(lib().sf_tune(self._h, c_arr, m_arr, _stream(self.device)), self._h)
+        return tune_report(self._h)
+
+    def profile(self, enable: bool = True):
+        _check(lib().sf_profile_enable(self._h, int(bool(enable))), self._h)
+
+    def profile_read(self, n_stages: int = 2):
+        ms = (ctypes.c_double * n_stages)()
+        nl = (_i64 * n_stages)()
+        _check(lib().sf_profile_read(self._h, ms, nl, n_stages), self._h)
+        return {i: (ms[i], nl[i]) for i in range(n_stages)}
+
+    def synchronize(self):
+        _check(lib().sf_synchronize(self._h, _stream(self.device)), self._h)
 
     def close(self):
         if getattr(self, "_h", None):

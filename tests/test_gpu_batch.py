@@ -1,0 +1,97 @@
+"""Batched form: many uneven cubes in one persistent launch replayed from a
+CUDA graph, and the autotuner.  The batched path runs the same arithmetic as
+the per-cube path, so masks and statistics must be bit-identical to
+sf_detect on each cube alone; the per-cube path is pinned to the oracle by
+test_gpu_parity.py, and one batch member is compared with the oracle here."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+BANK6 = ((0.0, 2.0), (0.0, 6.0), (1.5, 2.0), (1.5, 6.0), (3.0, 2.0), (3.0, 6.0))
+SHAPES = [(70, 70, 131), (64, 64, 256), (33, 33, 200), (96, 96, 129), (41, 41, 130), (128, 128, 64)]
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1507_04941_gb300 import build
+    build.build()
+    return torch.device("cuda", 0)
+
+
+def _cubes(dev):
+    from paper_1507_04941_gb300 import synth
+    return [synth.make_cube(sh, 700 + i, 6, (0.5, 5.0), 1.5, device=dev) for i, sh in enumerate(SHAPES)]
+
+
+def _single(dev, cube, window=(32, 32, 64)):
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder
+    with SourceFinder(tuple(cube.shape), BANK6, 3.0, window, device=dev) as sf:
+        out = sf.detect(cube, stats=True)
+        torch.cuda.synchronize(dev)
+        return [t.cpu() for t in out]
+
+
+def test_batch_equals_per_cube(dev, oracle):
+    import torch
+    from paper_1507_04941_gb300 import BatchSourceFinder, words_to_bits
+    cubes = _cubes(dev)
+    with BatchSourceFinder(SHAPES, BANK6, 3.0, (32, 32, 64), device=dev) as bf:
+        for rep in range(2):   # the second call replays the graph with fresh tables
+            masks, means, stds = bf.detect(cubes, stats=True)
+            bf.synchronize()
+            for i, cube in enumerate(cubes):
+                m1, me1, sd1 = _single(dev, cube)
+                assert torch.equal(masks[i].cpu(), m1), f"cube {i} mask (call {rep})"
+                assert torch.equal(means[i].cpu(), me1), f"cube {i} mean"
+                assert torch.equal(stds[i].cpu(), sd1), f"cube {i} std"
+    # one member against the oracle
+    i = 0
+    ref = oracle.detect(cubes[i].cpu().numpy(), BANK6, 3.0, (32, 32, 64), 4.0)
+    got = words_to_bits(masks[i].cpu().numpy(), SHAPES[i][2])
+    sure = oracle.unpack_bits(ref["sure"], SHAPES[i][2])
+    want = oracle.unpack_bits(ref["mask"], SHAPES[i][2])
+    assert not ((got != want) & sure).any()
+
+
+def test_batch_single_cube_and_no_spatial_filter(dev):
+    import torch
+    from paper_1507_04941_gb300 import BatchSourceFinder, SourceFinder, synth
+    bank = ((0.0, 2.0), (0.0, 5.0))          # no x pass at all
+    shape = (40, 40, 100)
+    cube = synth.make_cube(shape, 91, 5, (1.0, 5.0), device=dev)
+    with BatchSourceFinder([shape], bank, 3.0, (16, 16, 32), device=dev) as bf, \
+            SourceFinder(shape, bank, 3.0, (16, 16, 32), device=dev) as sf:
+        m = bf.detect([cube])[0]
+        torch.cuda.synchronize(dev)
+        assert torch.equal(m, sf.detect(cube))
+
+
+def test_tune_keeps_results(dev):
+    import json
+
+    import torch
+    from paper_1507_04941_gb300 import BatchSourceFinder, SourceFinder, synth
+    shape = (256, 96, 256)
+    cube = synth.make_cube(shape, 92, 30, (0.5, 5.0), 1.5, device=dev)
+    with SourceFinder(shape, BANK6, 3.0, (32, 32, 64), device=dev) as sf:
+        before = sf.detect(cube, stats=True)
+        rep = json.loads(sf.tune(cube))
+        assert rep[0]["path"].startswith("x pass") and len(rep) >= 3
+        after = sf.detect(cube, stats=True)
+        torch.cuda.synchronize(dev)
+        for x, y in zip(before, after):
+            assert torch.equal(x, y)
+    cubes = _cubes(dev)
+    with BatchSourceFinder(SHAPES, BANK6, 3.0, (32, 32, 64), device=dev) as bf:
+        before = bf.detect(cubes)
+        rep = json.loads(bf.tune(cubes))
+        assert all(r["path"] == "persistent" for r in rep)
+        after = bf.detect(cubes)
+        bf.synchronize()
+        for x, y in zip(before, after):
+            assert torch.equal(x, y)
