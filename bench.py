@@ -303,6 +303,12 @@ def run_ours(args):
     if not args.no_batch and world == 1 and storage == "f32":
         batch = run_batch(args, dev, stream, w)
 
+    # serving form: Poisson arrivals of subcube requests, FP16 storage
+    serving = None
+    if not args.no_serve and world == 1 and storage == "f32":
+        cap = (64 / (batch["ms_per_step"] * 1e-3)) if batch else None
+        serving = run_serving(args, dev, w, cap)
+
     # end to end through the host-buffer entry point (pinned memory)
     e2e = None
     if not args.no_e2e:
@@ -341,6 +347,7 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({nvox * sbytes / 2**20:.0f} MiB cube, "
                              "129 MB L2)"},
             "roofline": roof, "kernels": other, "clocks": clocks, "storage_forms": forms,
+            "serving": serving,
             "path": "persistent (x-pass + windows in one launch)" if persistent else
                     "x pass + window kernel", "autotune": tune_rep, "batched_form": batch,
             "e2e": e2e, "gpu_launches": int(sum(st["launches_per_step"] for st in
@@ -406,6 +413,95 @@ def run_batch(args, dev, stream, w):
     out["masks_identical_to_per_cube"] = bool(same)
     del cubes
     torch.cuda.empty_cache()
+    return out
+
+
+def run_serving(args, dev, w, capacity_rps):
+    """Continuous-batching server under Poisson arrivals at fractions of the
+    batched form's capacity (requests/s); shapes drawn from the batched
+    workload's 64 subcubes; FP16 storage; 150 GB HBM budget."""
+    import numpy as np
+    import torch
+
+    from paper_1507_04941_gb300 import Server, SourceFinder, synth
+    specs = synth.subcube_specs()
+    shapes = [tuple(sp["shape"]) for sp in specs]
+    cubes = [synth.make_subcube(sp, device=dev).to(torch.float16).cpu().pin_memory() for sp in specs]
+    free = {i: [] for i in range(len(shapes))}
+
+    def mask_for(i):
+        if free[i]:
+            return free[i].pop()
+        nx, ny, nz = shapes[i]
+        return torch.empty((nx, ny, -(-nz // 32)), dtype=torch.int32).pin_memory()
+
+    out = {"workload": "Poisson arrivals of the 64 batched-workload subcubes, FP16 storage, "
+                       "150 GB budget, 8 slots",
+           "capacity_rps_of_batched_form": capacity_rps, "levels": []}
+    rng = np.random.Generator(np.random.PCG64(21))
+    with Server(w.bank, w.truncation, w.window, w.k, storage="f16", budget_bytes=150 * 10 ** 9,
+                max_inflight=8, device=dev.index) as srv:
+        # warm-up: every shape once (plans, kernels and buffers become resident)
+        owner = {}
+        for i in range(len(shapes)):
+            m = mask_for(i)
+            owner[srv.submit(cubes[i], m)] = (i, m)
+        got = 0
+        while got < len(shapes):
+            for rid, st, _ in srv.poll(timeout_ms=500):
+                i, m = owner.pop(rid)
+                free[i].append(m)
+                got += 1
+        if capacity_rps is None:
+            capacity_rps = 200.0
+        for frac in (0.25, 0.5, 0.75, 1.0):
+            rate = frac * capacity_rps
+            n = args.serve_requests
+            gaps = rng.exponential(1.0 / rate, n)
+            which = rng.integers(0, len(shapes), n)
+            lat = []
+            fails = 0
+            t0 = time.perf_counter()
+            t_next = t0
+            k = 0
+            while k < n or owner:
+                now = time.perf_counter()
+                while k < n and now >= t_next:
+                    i = int(which[k])
+                    m = mask_for(i)
+                    owner[srv.submit(cubes[i], m)] = (i, m)
+                    t_next += gaps[k]
+                    k += 1
+                wait_ms = 0 if k < n else 50
+                for rid, st, l in srv.poll(timeout_ms=wait_ms):
+                    i, m = owner.pop(rid)
+                    free[i].append(m)
+                    lat.append(l)
+                    fails += st != 0
+                if k < n:
+                    time.sleep(max(0.0, min(0.0005, t_next - time.perf_counter())))
+            el = time.perf_counter() - t0
+            lat_ms = np.sort(np.array(lat) * 1e3)
+            out["levels"].append({
+                "load": frac, "offered_rps": rate, "requests": n, "failed": int(fails),
+                "throughput_rps": n / el,
+                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "mean_ms": float(lat_ms.mean())})
+        out["stats"] = srv.stats()
+        # agreement: a seeded sample of 32 requests served together vs each alone
+        sample = rng.integers(0, len(shapes), 32)
+        sm = [mask_for(int(i)) for i in sample]
+        ids = {srv.submit(cubes[int(i)], m): j for j, (i, m) in enumerate(zip(sample, sm))}
+        got = 0
+        while got < len(ids):
+            got += len(srv.poll(timeout_ms=500))
+    same = 0
+    for i, m in zip(sample, sm):
+        with SourceFinder(shapes[int(i)], w.bank, w.truncation, w.window, w.k, storage="f16",
+                          device=dev) as sf:
+            same += bool(torch.equal(m, sf.detect_host(cubes[int(i)])))
+    out["agreement_with_alone"] = f"{same}/32 sampled requests bit-identical to the request run alone"
+    out["unit"] = "ms"
     return out
 
 
@@ -486,6 +582,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-subcube form")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving form")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests per offered-load level of the serving form")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP16/BF16-storage runs of the same workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -164,6 +164,35 @@ sf_status sf_detect_batch(sf_ctx *ctx, const void *const *d_cubes, uint32_t *con
 sf_status sf_tune(sf_ctx *ctx, const void *const *d_cubes, uint32_t *const *d_masks, void *stream);
 sf_status sf_tune_report(const sf_ctx *ctx, char *buf, int32_t cap);
 
+/* Serving form: a continuous-batching request loop on one GPU.
+ * Requests are cubes of any shape in host memory (storage dtype of proto;
+ * pinned memory makes the copies DMA).  A request is admitted as soon as one
+ * of max_inflight worker slots is free and its device footprint (cube, mask
+ * and one x-filtered scratch cube per distinct non-zero sigma_xy) fits the
+ * HBM budget; admitted requests run concurrently on their own CUDA streams.
+ * Per-shape contexts stay resident after use and count against the budget;
+ * idle ones are destroyed (least recently used first) when an admission
+ * needs the room.  A request larger than the budget completes at once with
+ * SF_EBUDGET.  proto->nx/ny/nz are ignored.  (Sec. 3.1 copies sections one
+ * at a time; Sec. 6 proposes overlapping input with processing.) */
+typedef struct sf_server sf_server;
+sf_status sf_server_create(const sf_config *proto, int64_t budget_bytes, int32_t max_inflight,
+                           sf_server **out);
+/* Queue a request; h_cube and h_mask must stay valid until it completes.
+ * *id receives the request id. */
+sf_status sf_server_submit(sf_server *srv, const void *h_cube, int64_t nx, int64_t ny, int64_t nz,
+                           uint32_t *h_mask, int64_t *id);
+/* Up to cap completed requests: id, status and latency (ns from submit to
+ * the mask being on the host).  Waits at most timeout_ms for a first one. */
+sf_status sf_server_poll(sf_server *srv, int64_t *ids, int32_t *statuses, int64_t *latency_ns,
+                         int32_t cap, int32_t timeout_ms, int32_t *n);
+/* Counters: submitted, admitted, completed, rejected, bytes in use, peak
+ * bytes (in use + idle contexts), idle bytes, evictions, contexts created,
+ * busy slots, queued requests, budget (up to cap values). */
+sf_status sf_server_stats(sf_server *srv, int64_t *out, int32_t cap);
+/* Drain the queue, wait for the requests in flight, free everything. */
+sf_status sf_server_destroy(sf_server *srv);
+
 /* Filtered cube of one filter without allocating anything, for callers that
  * cannot call cudaMalloc (allocation-free loops, hosts that own every
  * allocation).  No context: the filter is (sigma_xy, sigma_z, truncation),

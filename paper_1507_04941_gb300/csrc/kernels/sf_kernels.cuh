@@ -274,29 +274,38 @@ template <int RY>
 __device__ __forceinline__ void sfd_load_slab(sfd_t *slab, const sfd_t *__restrict__ src, i64 x,
                                               i64 y0, i64 z0, i64 nx, i64 ny, i64 nz)
 {
+    /* one warp per slab row, lanes over the row's chunks: no index division */
     constexpr int ROWS = SFD_WY + 2 * RY;
+    constexpr int NWARPS = SFD_THREADS / 32;
+    const int lane = threadIdx.x & 31;
     const bool xin = x >= 0 && x < nx;
     if constexpr (SFD_CH > 0) {
         constexpr int NCH = SFD_UW / SFD_CH;
         constexpr int BYTES = SFD_CH * (int)sizeof(sfd_t);
-        for (int i = threadIdx.x; i < ROWS * NCH; i += SFD_THREADS) {
-            const int r = i / NCH, ch = i - r * NCH;
+        for (int r = threadIdx.x >> 5; r < ROWS; r += NWARPS) {
             const i64 y = y0 - RY + r;
-            const i64 z = z0 - SFD_HZ + (i64)ch * SFD_CH;
-            const bool in = xin && y >= 0 && y < ny && z >= 0 && z + SFD_CH <= nz;
-            const sfd_t *g = in ? src + ((x * ny + y) * nz + z) : src;
-            sf_cp_async<BYTES>(sf_smem_addr(slab + r * SFD_SROW + ch * SFD_CH), g, in ? BYTES : 0u);
+            const bool rin = xin && y >= 0 && y < ny;
+            const sfd_t *row = rin ? src + (x * ny + y) * nz : src;
+            const u32 dst = sf_smem_addr(slab + r * SFD_SROW);
+            for (int ch = lane; ch < NCH; ch += 32) {
+                const i64 z = z0 - SFD_HZ + (i64)ch * SFD_CH;
+                const bool in = rin && z >= 0 && z + SFD_CH <= nz;
+                sf_cp_async<BYTES>(dst + (u32)(ch * BYTES), in ? row + z : src, in ? BYTES : 0u);
+            }
         }
     } else {
         /* element loads for 16-bit storage with an odd nz (no 4-byte chunks) */
-        for (int i = threadIdx.x; i < ROWS * SFD_UW; i += SFD_THREADS) {
-            const int r = i / SFD_UW, c = i - r * SFD_UW;
+        for (int r = threadIdx.x >> 5; r < ROWS; r += NWARPS) {
             const i64 y = y0 - RY + r;
-            const i64 z = z0 - SFD_HZ + c;
-            sfd_t v;
-            if (xin && y >= 0 && y < ny && z >= 0 && z < nz) v = src[(x * ny + y) * nz + z];
-            else *reinterpret_cast<u16 *>(&v) = 0;
-            slab[r * SFD_SROW + c] = v;
+            const bool rin = xin && y >= 0 && y < ny;
+            const sfd_t *row = rin ? src + (x * ny + y) * nz : src;
+            for (int c = lane; c < SFD_UW; c += 32) {
+                const i64 z = z0 - SFD_HZ + c;
+                sfd_t v;
+                if (rin && z >= 0 && z < nz) v = row[z];
+                else *reinterpret_cast<u16 *>(&v) = 0;
+                slab[r * SFD_SROW + c] = v;
+            }
         }
     }
 }

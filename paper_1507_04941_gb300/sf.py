@@ -67,6 +67,12 @@ SIGNATURES = {
                                ctypes.POINTER(_vp), _vp]),
     "sf_tune": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
     "sf_tune_report": (_i32, [_vp, ctypes.c_char_p, _i32]),
+    "sf_server_create": (_i32, [ctypes.POINTER(Config), _i64, _i32, ctypes.POINTER(_vp)]),
+    "sf_server_submit": (_i32, [_vp, _vp, _i64, _i64, _i64, _vp, ctypes.POINTER(_i64)]),
+    "sf_server_poll": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i64),
+                              _i32, _i32, ctypes.POINTER(_i32)]),
+    "sf_server_stats": (_i32, [_vp, ctypes.POINTER(_i64), _i32]),
+    "sf_server_destroy": (_i32, [_vp]),
     "sf_filter_noalloc": (_i32, [_vp, _i64, _i64, _i64, ctypes.c_float, ctypes.c_float,
                                  ctypes.c_float, _vp, _vp]),
     "sf_profile_enable": (_i32, [_vp, _i32]),
@@ -390,6 +396,82 @@ class BatchSourceFinder:
         if getattr(self, "_h", None):
             lib().sf_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+SERVER_STATS = ("submitted", "admitted", "completed", "rejected", "bytes_in_use", "peak_bytes",
+                "idle_bytes", "evictions", "contexts_created", "busy", "queued", "budget")
+
+
+class Server:
+    """Continuous-batching detection server (wraps sf_server)."""
+
+    def __init__(self, bank, truncation: float = 3.0, window=(32, 32, 64), k: float = 4.0,
+                 storage: str = "f16", budget_bytes: int = 150 * 10 ** 9, max_inflight: int = 8,
+                 device: int = 0):
+        self.bank = tuple((float(a), float(b)) for a, b in bank)
+        self.storage = storage
+        specs = (FilterSpec * len(self.bank))(*[FilterSpec(a, b) for a, b in self.bank])
+        self._specs = specs
+        cfg = Config(1, 1, 1, len(self.bank), specs, float(truncation), int(window[0]),
+                     int(window[1]), int(window[2]), float(k), STORAGE[storage], 0, int(device))
+        h = _vp()
+        st = lib().sf_server_create(ctypes.byref(cfg), int(budget_bytes), int(max_inflight),
+                                    ctypes.byref(h))
+        if st != SF_OK:
+            raise SfError(st, "sf_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, cube_host, mask_host) -> int:
+        """Queue a host cube (storage dtype, contiguous); mask_host receives the words."""
+        nx, ny, nz = (int(v) for v in cube_host.shape)
+        rid = _i64()
+        st = lib().sf_server_submit(self._h, _ptr(cube_host), nx, ny, nz, _ptr(mask_host),
+                                    ctypes.byref(rid))
+        if st != SF_OK:
+            raise SfError(st, "sf_server_submit")
+        self._keep[rid.value] = (cube_host, mask_host)
+        return rid.value
+
+    def poll(self, cap: int = 256, timeout_ms: int = 0):
+        """[(id, status, latency_seconds)] of requests completed since the last poll."""
+        ids = (_i64 * cap)()
+        sts = (_i32 * cap)()
+        lat = (_i64 * cap)()
+        n = _i32()
+        st = lib().sf_server_poll(self._h, ids, sts, lat, cap, int(timeout_ms), ctypes.byref(n))
+        if st != SF_OK:
+            raise SfError(st, "sf_server_poll")
+        out = []
+        for i in range(n.value):
+            self._keep.pop(ids[i], None)
+            out.append((ids[i], sts[i], lat[i] * 1e-9))
+        return out
+
+    def stats(self) -> dict:
+        vals = (_i64 * len(SERVER_STATS))()
+        st = lib().sf_server_stats(self._h, vals, len(SERVER_STATS))
+        if st != SF_OK:
+            raise SfError(st, "sf_server_stats")
+        return dict(zip(SERVER_STATS, list(vals)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sf_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -101,3 +101,16 @@ def test_null_arguments(libsf):
     assert lib.sf_destroy(None) == sf.SF_OK
     assert lib.sf_detect(None, None, None, None, None, None) == sf.SF_EINVAL
     assert lib.sf_mask_words(None, None) == sf.SF_EINVAL
+
+
+def test_server_invalid_arguments(libsf):
+    from paper_1507_04941_gb300 import sf
+    lib = sf.lib()
+    cfg, _keep = _cfg(sf)
+    h = ctypes.c_void_p()
+    assert lib.sf_server_create(ctypes.byref(cfg), 0, 4, ctypes.byref(h)) == sf.SF_EINVAL
+    assert lib.sf_server_create(ctypes.byref(cfg), 10 ** 9, 0, ctypes.byref(h)) == sf.SF_EINVAL
+    assert lib.sf_server_create(None, 10 ** 9, 4, ctypes.byref(h)) == sf.SF_EINVAL
+    assert lib.sf_server_destroy(None) == sf.SF_OK
+    n = ctypes.c_int32()
+    assert lib.sf_server_poll(None, None, None, None, 0, 0, ctypes.byref(n)) == sf.SF_EINVAL
