@@ -280,16 +280,17 @@ __device__ __forceinline__ void sfd_load_slab(sfd_t *slab, const sfd_t *__restri
     const int lane = threadIdx.x & 31;
     const bool xin = x >= 0 && x < nx;
     if constexpr (SFD_CH > 0) {
-        constexpr int NCH = SFD_UW / SFD_CH;
-        constexpr int BYTES = SFD_CH * (int)sizeof(sfd_t);
+        constexpr int CHE = SFD_CH > 0 ? SFD_CH : 1;   /* non-dependent: keep it defined */
+        constexpr int NCH = SFD_UW / CHE;
+        constexpr int BYTES = CHE * (int)sizeof(sfd_t);
         for (int r = threadIdx.x >> 5; r < ROWS; r += NWARPS) {
             const i64 y = y0 - RY + r;
             const bool rin = xin && y >= 0 && y < ny;
             const sfd_t *row = rin ? src + (x * ny + y) * nz : src;
             const u32 dst = sf_smem_addr(slab + r * SFD_SROW);
             for (int ch = lane; ch < NCH; ch += 32) {
-                const i64 z = z0 - SFD_HZ + (i64)ch * SFD_CH;
-                const bool in = rin && z >= 0 && z + SFD_CH <= nz;
+                const i64 z = z0 - SFD_HZ + (i64)ch * CHE;
+                const bool in = rin && z >= 0 && z + CHE <= nz;
                 sf_cp_async<BYTES>(dst + (u32)(ch * BYTES), in ? row + z : src, in ? BYTES : 0u);
             }
         }
