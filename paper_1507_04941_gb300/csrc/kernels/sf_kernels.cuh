@@ -217,7 +217,7 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
 {
     const i64 lane = (i64)blockIdx.x * SFX_THREADS + threadIdx.x;
     if (lane >= a.lanes) return;
-    const i64 xb = (i64)blockIdx.y * a.xseg;
+    const i64 xb = a.xoff + (i64)blockIdx.y * a.xseg;
     const i64 xe = min(a.nx, xb + a.xseg);
     const sfx_t *p = reinterpret_cast<const sfx_t *>(a.src) + lane * SFX_V;
     sfx_lane<SFX_V>(p, a.dst, lane * SFX_V, a.nx, a.plane, xb, xe, t);
@@ -226,6 +226,9 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
 
 /* ======================================================================= */
 #if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_FILTER) || defined(SF_KERNEL_PERSIST)
+#ifndef SFD_X2
+#define SFD_X2 0
+#endif
 /* Prelude: SFD_WY, SFD_WZ (tile of one plane), SFD_P (z outputs per thread),
  * SFD_THREADS (= WY*WZ/P), SFD_NSRC, SFD_NZF, SFD_RYM, SFD_RZM, SFD_HZ (z halo,
  * multiple of 4 and of SFD_CH), SFD_CH (elements per cp.async, 0 = synchronous
@@ -351,6 +354,148 @@ __host__ __device__ constexpr int sfd_max4(int a, int b, int c, int d)
 __host__ __device__ constexpr int sfd_pick(int f, int a, int b, int c, int d)
 {
     return f == 0 ? a : f == 1 ? b : f == 2 ? c : d;
+}
+
+/* ---- packed FP32 pairs (f32x2): one instruction for two lanes of work ---- */
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(f2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float f2_hi(f2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+/* four consecutive staged elements as two pairs (low, high) */
+template <class T>
+__device__ __forceinline__ void sf_ld_pairs(const T *p, f2 &lo, f2 &hi)
+{
+    if constexpr (sf_is_f32<T>::v) {
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
+        lo = v.x;
+        hi = v.y;
+    } else {
+        float o[4];
+        sf_ld<T, 4, false>(p, o);
+        lo = f2_pack(o[0], o[1]);
+        hi = f2_pack(o[2], o[3]);
+    }
+}
+
+/* y filter with column pairs: the same taps as sfd_yfilter, two columns per
+ * instruction. */
+template <int SI, int RY>
+__device__ __forceinline__ void sfd_yfilter2(const sfd_t *slab, float *U, const sfd_taps &t)
+{
+    constexpr int NQ = SFD_UW / 4;
+    constexpr int NRB = SFD_WY / SFD_PY;
+    for (int task = threadIdx.x; task < NRB * NQ; task += SFD_THREADS) {
+        const int rb = task / NQ, q = task - rb * NQ;
+        f2 acc[SFD_PY][2];
+#pragma unroll
+        for (int i = 0; i < SFD_PY; ++i) acc[i][0] = acc[i][1] = 0ull;
+#pragma unroll
+        for (int r = 0; r < SFD_PY + 2 * RY; ++r) {
+            f2 v0, v1;
+            sf_ld_pairs<sfd_t>(slab + (rb * SFD_PY + r) * SFD_SROW + 4 * q, v0, v1);
+#pragma unroll
+            for (int i = 0; i < SFD_PY; ++i) {
+                const int j = r - i;
+                if (j >= 0 && j <= 2 * RY) {
+                    const float g = t.gy[SI][j >= RY ? j - RY : RY - j];
+                    const f2 G = f2_pack(g, g);
+                    acc[i][0] = f2_fma(G, v0, acc[i][0]);
+                    acc[i][1] = f2_fma(G, v1, acc[i][1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < SFD_PY; ++i)
+            *reinterpret_cast<ulonglong2 *>(U + (rb * SFD_PY + i) * SFD_UROW + 4 * q) =
+                make_ulonglong2(acc[i][0], acc[i][1]);
+    }
+}
+
+/* z filters with output pairs (z, z+1): pair sums of aligned element pairs for
+ * even taps, of pairs shifted by one element for odd taps. */
+template <int SI, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
+__device__ __forceinline__ void sfd_zfilter2(const sfd_t *slab, const float *U, int row, int chunk,
+                                             float (&c)[SFD_NZF][SFD_P], const sfd_taps &t)
+{
+    static_assert(SFD_P % 2 == 0, "output pairs");
+    constexpr int RZM = sfd_max4(RZ0, RZ1, RZ2, RZ3);
+    constexpr int LO = (SFD_HZ - RZM) & ~3;
+    constexpr int HI = SFD_HZ + SFD_P - 1 + RZM;
+    constexpr int NQ = (HI - LO) / 4 + 1;
+    f2 E[2 * NQ];          /* E[k] = (in[2k], in[2k+1]) */
+    if constexpr (RY > 0) {
+        const float *p = U + row * SFD_UROW + SFD_P * chunk + LO;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sf_ld_pairs<float>(p + 4 * q, E[2 * q], E[2 * q + 1]);
+    } else {
+        const sfd_t *p = slab + row * SFD_SROW + SFD_P * chunk + LO;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) sf_ld_pairs<sfd_t>(p + 4 * q, E[2 * q], E[2 * q + 1]);
+    }
+    f2 O[2 * NQ - 1];      /* O[k] = (in[2k+1], in[2k+2]) */
+#pragma unroll
+    for (int k = 0; k < 2 * NQ - 1; ++k) O[k] = f2_pack(f2_hi(E[k]), f2_lo(E[k + 1]));
+    f2 acc[SFD_NZF][SFD_P / 2];
+#pragma unroll
+    for (int j = 0; j <= RZM; ++j) {
+#pragma unroll
+        for (int m = 0; m < SFD_P / 2; ++m) {
+            const int ci = SFD_HZ + 2 * m - LO;       /* even */
+            f2 ps;
+            if (j == 0) ps = E[ci / 2];
+            else if ((j & 1) == 0) ps = f2_add(E[(ci - j) / 2], E[(ci + j) / 2]);
+            else ps = f2_add(O[(ci - j - 1) / 2], O[(ci + j - 1) / 2]);
+#pragma unroll
+            for (int f = 0; f < NZ; ++f) {
+                if (j <= sfd_pick(f, RZ0, RZ1, RZ2, RZ3)) {
+                    const float g = t.gz[SI][f][j];
+                    const f2 G = f2_pack(g, g);
+                    acc[f][m] = j == 0 ? f2_mul(G, ps) : f2_fma(G, ps, acc[f][m]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < NZ; ++f)
+#pragma unroll
+        for (int m = 0; m < SFD_P / 2; ++m) {
+            c[f][2 * m] = f2_lo(acc[f][m]);
+            c[f][2 * m + 1] = f2_hi(acc[f][m]);
+        }
 }
 
 /* SFD_P consecutive z outputs (z0 + P*chunk ...) of row `row` for the NZ
@@ -542,11 +687,19 @@ __device__ __forceinline__ void sfw_plane(const sfd_taps &t, sfw_state &S, int b
                                           float (&c)[SFD_NZF][SFD_P])
 {
     const sfd_t *slab = S.slab0 + b * SFW_SLAB_STRIDE;
+#if SFD_X2
+    if constexpr (RY > 0) {
+        sfd_yfilter2<IDX, RY>(slab, S.U, t);
+        __syncthreads();
+    }
+    sfd_zfilter2<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(slab, S.U, S.row, S.chunk, c, t);
+#else
     if constexpr (RY > 0) {
         sfd_yfilter<IDX, RY>(slab, S.U, t);
         __syncthreads();
     }
     sfd_zfilter<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(slab, S.U, S.row, S.chunk, c, t);
+#endif
 }
 
 /* the next input's first load, issued while this input finishes */
@@ -586,16 +739,20 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
      * flagged planes. */
     bool pass2 = false;
     int p = 0;
+    f2 s1p[SFD_NZF], s2p[SFD_NZF];   /* packed partial sums of the full-tile path */
+#pragma unroll
+    for (int f = 0; f < SFD_NZF; ++f) s1p[f] = s2p[f] = 0ull;
     while (true) {
         const int b = S.it & 1;
         int np = -1;
         if (!pass2) np = p + 1 < S.npl ? p + 1 : -1;
         else np = next_flag(p);
-        bool more = np >= 0;
-        if (more) sfw_load<IDX, RY>(a, mp, S, np, b ^ 1);
-        else if (pass2 && IDX + 1 < SFD_NSRC) { sfw_first_load<IDX + 1>(a, mp, S, b ^ 1); more = true; }
-        const bool ok = sfw_wait_buf(S, b, more);
+        /* wait for this plane, then (everyone being past the previous plane)
+         * start the next load into the other buffer */
+        const bool ok = sfw_wait_buf(S, b, false);
         if (__syncthreads_or(!ok)) { S.dead = true; return; }
+        if (np >= 0) sfw_load<IDX, RY>(a, mp, S, np, b ^ 1);
+        else if (pass2 && IDX + 1 < SFD_NSRC) sfw_first_load<IDX + 1>(a, mp, S, b ^ 1);
         float c[SFD_NZF][SFD_P];
         sfw_plane<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(t, S, b, c);
         if (!pass2) {
@@ -607,12 +764,13 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
             for (int f = 0; f < NZ; ++f) {
                 float mx = -3.402823466e38f;
                 if (full) {
+                    const f2 NK = f2_pack(-K[f], -K[f]);
 #pragma unroll
-                    for (int i = 0; i < SFD_P; ++i) {
-                        const float d = c[f][i] - K[f];
-                        s1[f] += d;
-                        s2[f] = fmaf(d, d, s2[f]);
-                        mx = fmaxf(mx, c[f][i]);
+                    for (int i = 0; i < SFD_P; i += 2) {
+                        const f2 d = f2_add(f2_pack(c[f][i], c[f][i + 1]), NK);
+                        s1p[f] = f2_add(s1p[f], d);
+                        s2p[f] = f2_fma(d, d, s2p[f]);
+                        mx = fmaxf(mx, fmaxf(c[f][i], c[f][i + 1]));
                     }
                 } else {
 #pragma unroll
@@ -645,13 +803,14 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
                 *mw |= word;
             }
         }
-        __syncthreads();
         ++S.it;
 
         if (!pass2 && np < 0) {
             /* end of pass 1: window statistics, thresholds, flagged planes */
 #pragma unroll
             for (int f = 0; f < NZ; ++f) {
+                s1[f] += f2_lo(s1p[f]) + f2_hi(s1p[f]);
+                s2[f] += f2_lo(s2p[f]) + f2_hi(s2p[f]);
                 sfd_mom m{0.f, 0.f, 0.f};
                 if (cnt > 0) {
                     const float n = (float)cnt, mu = s1[f] / n;
@@ -828,7 +987,7 @@ sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd
     extern __shared__ __align__(128) unsigned char sfw_raw[];
     sfw_state S;
     sfw_init(S, sfw_raw);
-    sfw_window(a, t, mp.m, S, (int)blockIdx.x);
+    sfw_window(a, t, mp.m, S, a.wid0 + (int)blockIdx.x);
 }
 #endif /* SF_KERNEL_DETECT */
 

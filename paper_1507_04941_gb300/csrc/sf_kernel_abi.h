@@ -23,6 +23,7 @@ struct sf_xargs {
     long long plane;   /* ny * nz */
     long long lanes;   /* plane / V */
     long long xseg;    /* x positions per grid row */
+    long long xoff;    /* first output plane of grid row 0 */
 };
 
 /* fused y/z filter + window statistics + threshold + mask union */
@@ -36,6 +37,8 @@ struct sf_dargs {
     int nwx, nwy, nwz, nwin;
     float k;
     int *err;          /* set non-zero when a bounded wait expires */
+    int wid0;          /* window of block 0 (launches over a range of windows) */
+    int pad_;
 };
 
 /* Persistent batched kernel: a unit is one cube (or one x-slab of a cube)

@@ -235,9 +235,11 @@ struct sf_ctx {
     float *filt_scratch = nullptr;    /* composed path: one filtered cube */
     float *stat_scratch = nullptr;    /* composed path: mean/std of one filter */
 
-    /* host-buffer entry point */
+    /* host-buffer entry point (pipelined along x) */
     void *host_cube = nullptr;
     unsigned int *host_mask = nullptr;
+    cudaStream_t hcopy[2] = {nullptr, nullptr}, hback = nullptr;
+    std::vector<cudaEvent_t> hev;
 
     /* stage timing: pairs of events per recorded stage instance */
     bool prof = false;
@@ -388,7 +390,7 @@ std::vector<float> xpass_taps(const sf_ctx *c, const std::vector<int> &slots)
 }
 
 sf_status run_xpass(sf_ctx *c, const Launch &L, const std::vector<int> &slots, const void *cube,
-                    cudaStream_t st)
+                    cudaStream_t st, long long x0 = 0, long long x1 = -1)
 {
     sf_xargs xa{};
     xa.src = cube;
@@ -398,9 +400,17 @@ sf_status run_xpass(sf_ctx *c, const Launch &L, const std::vector<int> &slots, c
     xa.plane = c->cfg.ny * c->cfg.nz;
     xa.lanes = xa.plane / c->xv;
     xa.xseg = c->xseg;
+    xa.xoff = 0;
+    Launch LL = L;
+    if (x1 >= 0) {
+        /* one grid row over output planes [x0, x1) */
+        xa.xoff = x0;
+        xa.xseg = x1 - x0;
+        LL.grid.y = 1;
+    }
     std::vector<float> taps = xpass_taps(c, slots);
     void *args[] = {&xa, taps.data()};
-    return launch(c, L, args, st, "x pass launch");
+    return launch(c, LL, args, st, "x pass launch");
 }
 
 /* ------------------------------------------- y/z kernels: shared bits --- */
@@ -644,6 +654,8 @@ bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, 
     p += "#define SFD_WX " + std::to_string(g.wx) + "\n";
     /* resident CTAs per SM the register allocation must allow */
     p += "#define SFD_MINB " + std::to_string(minb) + "\n";
+    /* packed FP32 pairs (fma/add/mul .f32x2) for the y and z filters */
+    p += std::string("#define SFD_X2 ") + (env_int("SF_NO_X2", 0) ? "0" : "1") + "\n";
     p += "#define SFD_OFF_SLAB0 " + std::to_string(wp.off_s0) + "\n";
     p += "#define SFD_OFF_SLAB1 " + std::to_string(wp.off_s1) + "\n";
     p += "#define SFD_OFF_U " + std::to_string(wp.off_u) + "\n";
@@ -962,6 +974,38 @@ sf_status check_live(sf_ctx *c)
     return SF_OK;
 }
 
+/* the window kernel over windows [w0, w1) of the plain context's cube */
+sf_status launch_windows(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_mean, float *d_std,
+                         cudaStream_t st, int w0, int w1)
+{
+    sf_dargs da{};
+    for (size_t i = 0; i < c->dsrc.size(); ++i) {
+        const DetectSource &d = c->dsrc[i];
+        da.src[i] = d.slot < 0 ? d_cube : (const void *)((const char *)c->scratch + (size_t)d.slot * c->cube_bytes);
+        for (size_t q = 0; q < d.filters.size(); ++q) da.fidx[i][q] = d.filters[q];
+        if (c->dtma && d.slot < 0 && !encode_map(c, d_cube, d.ry, &c->dmaps[i]))
+            return fail(c, SF_ECUDA, "tensor map encoding of the cube failed");
+    }
+    da.mask = d_mask;
+    da.mean = d_mean;
+    da.stdv = d_std;
+    da.nx = c->cfg.nx;
+    da.ny = c->cfg.ny;
+    da.nz = c->cfg.nz;
+    da.nw32 = c->nw32;
+    da.nwx = c->nwx;
+    da.nwy = c->nwy;
+    da.nwz = c->nwz;
+    da.nwin = c->nwin;
+    da.k = c->cfg.k;
+    da.err = c->err_flag;
+    da.wid0 = w0;
+    Launch L = c->dlaunch;
+    L.grid = dim3((unsigned)(w1 - w0));
+    void *args[] = {&da, c->dtaps.data(), c->dmaps.data()};
+    return launch(c, L, args, st, "window kernel launch");
+}
+
 cudaEvent_t take_event(sf_ctx *c)
 {
     if (!c->pool.empty()) {
@@ -1245,6 +1289,10 @@ sf_status sf_destroy(sf_ctx *c)
     cudaFree(c->host_cube);
     cudaFree(c->host_mask);
     cudaFree(c->err_flag);
+    for (cudaStream_t x : c->hcopy)
+        if (x) cudaStreamDestroy(x);
+    if (c->hback) cudaStreamDestroy(c->hback);
+    for (cudaEvent_t ev : c->hev) cudaEventDestroy(ev);
     for (const sf_ctx::Rec &r : c->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -1386,29 +1434,7 @@ sf_status sf_detect(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_me
     }
     StageTimer tf(c, 1, st);
     if (c->fused) {
-        sf_dargs da{};
-        for (size_t i = 0; i < c->dsrc.size(); ++i) {
-            const DetectSource &d = c->dsrc[i];
-            da.src[i] = d.slot < 0 ? d_cube : (const void *)((const char *)c->scratch + (size_t)d.slot * c->cube_bytes);
-            for (size_t q = 0; q < d.filters.size(); ++q) da.fidx[i][q] = d.filters[q];
-            if (c->dtma && d.slot < 0 && !encode_map(c, d_cube, d.ry, &c->dmaps[i]))
-                return fail(c, SF_ECUDA, "tensor map encoding of the cube failed");
-        }
-        da.mask = d_mask;
-        da.mean = d_mean;
-        da.stdv = d_std;
-        da.nx = c->cfg.nx;
-        da.ny = c->cfg.ny;
-        da.nz = c->cfg.nz;
-        da.nw32 = c->nw32;
-        da.nwx = c->nwx;
-        da.nwy = c->nwy;
-        da.nwz = c->nwz;
-        da.nwin = c->nwin;
-        da.k = c->cfg.k;
-        da.err = c->err_flag;
-        void *args[] = {&da, c->dtaps.data(), c->dmaps.data()};
-        s = launch(c, c->dlaunch, args, st, "fused detect launch");
+        s = launch_windows(c, d_cube, d_mask, d_mean, d_std, st, 0, c->nwin);
         if (s == SF_OK) tf.done(1);
         return s;
     }
@@ -1605,8 +1631,10 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
     if (c->batch) return fail(c, SF_EINVAL, "batched context: use sf_detect_batch");
     if (!h_cube || !h_mask) return fail(c, SF_EINVAL, "NULL buffer");
     DeviceGuard dg(c->device);
-    const size_t cube = (size_t)c->nvox * c->ebytes;
-    const size_t mask = (size_t)(c->cfg.nx * c->cfg.ny * c->nw32) * 4;
+    const size_t plane = (size_t)(c->cfg.ny * c->cfg.nz) * c->ebytes;
+    const size_t mplane = (size_t)(c->cfg.ny * c->nw32) * 4;
+    const size_t cube = plane * (size_t)c->cfg.nx;
+    const size_t mask = mplane * (size_t)c->cfg.nx;
     cudaError_t e;
     if (!c->host_cube) {
         e = cudaMalloc(&c->host_cube, cube);
@@ -1617,11 +1645,68 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
         }
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if ((e = cudaMemcpyAsync(c->host_cube, h_cube, cube, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_fail(c, e, "host-to-device copy");
-    if ((s = sf_detect(c, c->host_cube, c->host_mask, nullptr, nullptr, stream)) != SF_OK) return s;
-    if ((e = cudaMemcpyAsync(h_mask, c->host_mask, mask, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-        return cuda_fail(c, e, "device-to-host copy");
+    if (c->use_persist || !c->fused) {
+        /* whole-cube copies around one sf_detect */
+        if ((e = cudaMemcpyAsync(c->host_cube, h_cube, cube, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(c, e, "host-to-device copy");
+        if ((s = sf_detect(c, c->host_cube, c->host_mask, nullptr, nullptr, stream)) != SF_OK) return s;
+        if ((e = cudaMemcpyAsync(h_mask, c->host_mask, mask, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(c, e, "device-to-host copy");
+        return sf_synchronize(c, stream);
+    }
+    /* Pipelined along x (Sec. 6: overlap input with processing): chunks of
+     * whole windows go host-to-device on two copy streams; chunk k's x pass
+     * starts once the chunks holding its planes and x halo have landed, its
+     * window kernel follows, and its mask rows go back on a third stream. */
+    const long long wx = c->cfg.wx;
+    const long long nx = c->cfg.nx;
+    long long S = (nx + 7) / 8;
+    S = std::max(wx, (S + wx - 1) / wx * wx);
+    const int K = (int)((nx + S - 1) / S);
+    int rxm = 0;
+    for (int r : c->xy_radius) rxm = std::max(rxm, r);
+    if (!c->hback) {
+        for (int i = 0; i < 2; ++i)
+            if ((e = cudaStreamCreateWithFlags(&c->hcopy[i], cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(c, e, "copy stream");
+        if ((e = cudaStreamCreateWithFlags(&c->hback, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(c, e, "copy stream");
+    }
+    while ((int)c->hev.size() < 2 * K + 1) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "pipeline events");
+        c->hev.push_back(ev);
+    }
+    /* the copies must not overtake earlier work on the caller's stream */
+    cudaEventRecord(c->hev[2 * K], st);
+    for (int i = 0; i < 2; ++i) cudaStreamWaitEvent(c->hcopy[i], c->hev[2 * K], 0);
+    for (int k = 0; k < K; ++k) {
+        const long long x0 = k * S, x1 = std::min(nx, x0 + S);
+        cudaStream_t cs = c->hcopy[k & 1];
+        if ((e = cudaMemcpyAsync((char *)c->host_cube + (size_t)x0 * plane, (const char *)h_cube + (size_t)x0 * plane,
+                                 (size_t)(x1 - x0) * plane, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+            return cuda_fail(c, e, "host-to-device copy");
+        cudaEventRecord(c->hev[k], cs);
+    }
+    int waited = -1;
+    for (int k = 0; k < K; ++k) {
+        const long long x0 = k * S, x1 = std::min(nx, x0 + S);
+        const int need = (int)(std::min(nx, x1 + rxm) - 1) / (int)S;
+        for (int j = waited + 1; j <= need; ++j) cudaStreamWaitEvent(st, c->hev[j], 0);
+        waited = std::max(waited, need);
+        for (size_t i = 0; i < c->xlaunch.size(); ++i)
+            if ((s = run_xpass(c, c->xlaunch[i], c->xgroups[i], c->host_cube, st, x0, x1)) != SF_OK) return s;
+        const int w0 = (int)(x0 / wx) * c->nwy * c->nwz;
+        const int w1 = (int)((x1 + wx - 1) / wx) * c->nwy * c->nwz;
+        if ((s = launch_windows(c, c->host_cube, c->host_mask, nullptr, nullptr, st, w0, w1)) != SF_OK) return s;
+        cudaEventRecord(c->hev[K + k], st);
+        cudaStreamWaitEvent(c->hback, c->hev[K + k], 0);
+        if ((e = cudaMemcpyAsync((char *)h_mask + (size_t)x0 * mplane, (const char *)c->host_mask + (size_t)x0 * mplane,
+                                 (size_t)(x1 - x0) * mplane, cudaMemcpyDeviceToHost, c->hback)) != cudaSuccess)
+            return cuda_fail(c, e, "device-to-host copy");
+    }
+    if ((e = cudaStreamSynchronize(c->hback)) != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
     return sf_synchronize(c, stream);
 }
 

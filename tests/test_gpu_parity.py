@@ -182,6 +182,18 @@ def test_detect_constant_cube_fires_nothing(dev):
         assert int(mask.count_nonzero()) == 0
 
 
+@pytest.mark.parametrize("shape,window", [((100, 40, 96), (16, 16, 32)), ((37, 33, 70), (8, 8, 32))])
+def test_detect_host_pipelined_chunks(dev, shape, window):
+    """sf_detect_host copies and computes in x chunks with an x halo."""
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder
+    cube = _cube(shape, seed=33, n_sources=10, peak=(2.0, 5.0))
+    with SourceFinder(shape, BANK6, 3.0, window, device=dev) as sf:
+        m_dev = sf.detect(cube.to(dev)).cpu()
+        for _ in range(2):
+            assert torch.equal(sf.detect_host(cube.pin_memory()), m_dev)
+
+
 def test_detect_host_equals_device(dev):
     import torch
     from paper_1507_04941_gb300 import SourceFinder

@@ -73,9 +73,16 @@ def test_budget_admission_rejection_and_eviction(dev):
     import torch
     from paper_1507_04941_gb300 import Server
     cubes, masks = _requests("f16")
-    # room for about two of the larger requests at a time: admissions wait and
+
+    def footprint(sh):
+        # the server's accounting: cube + two x-filtered scratch cubes + mask
+        up = lambda v: (v + 255) // 256 * 256  # noqa: E731
+        cube = up(sh[0] * sh[1] * sh[2] * 2)
+        return 3 * cube + up(sh[0] * sh[1] * (-(-sh[2] // 32)) * 4) + 4096
+
+    # room for the largest request and a little more: admissions wait and
     # idle contexts of other shapes are evicted
-    budget = 3 * (96 * 96 * 257 * 2) * 3
+    budget = int(1.5 * max(footprint(sh) for sh in SHAPES))
     with Server(BANK6, storage="f16", budget_bytes=budget, max_inflight=4, device=0) as srv:
         ids = [srv.submit(c, m) for c, m in zip(cubes, masks)]
         big = torch.zeros((512, 512, 1024), dtype=torch.float16)
