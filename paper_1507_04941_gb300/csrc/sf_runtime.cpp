@@ -432,7 +432,9 @@ std::string yz_prelude(const sf_ctx *c, const YZShape &sh, const std::vector<Det
     p += "#define SFD_CH " + std::to_string(sh.CH) + "\n";
     p += "#define SFD_SROW " + std::to_string(sh.SROW) + "\n";
     p += "#define SFD_UROW " + std::to_string(sh.UROW) + "\n";
-    p += "#define SFD_PY 8\n";
+    /* output rows per y-filter task: 4 (default), or 8 (half the tasks, fewer
+     * slab reads per output) */
+    p += "#define SFD_PY " + std::to_string(env_int("SF_PY", 4) == 8 ? 8 : 4) + "\n";
     p += std::string("typedef ") + storage_ctype(c->cfg.storage) + " sfd_t;\n";
     p += "#define SFD_SOURCES(X)";
     for (size_t i = 0; i < srcs.size(); ++i) {
