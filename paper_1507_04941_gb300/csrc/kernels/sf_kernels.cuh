@@ -143,6 +143,45 @@ __device__ __forceinline__ void sf_st(T *p, const float *v)
     }
 }
 
+/* ---- packed FP32 pairs (f32x2): one instruction for two lanes of work ---- */
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 f2_pack(float a, float b)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(f2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float f2_hi(f2 v)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 /* ======================================================================= */
 #if defined(SF_KERNEL_XPASS) || defined(SF_KERNEL_PERSIST)
 /* Prelude: SFX_NOUT, SFX_R0..SFX_R3 (radii, 0 = unused), SFX_RM (max radius),
@@ -212,6 +251,116 @@ __device__ __forceinline__ void sfx_lane(const sfx_t *__restrict__ p, void *cons
 #endif
 
 #ifdef SF_KERNEL_XPASS
+#if SFX_D > 0
+/* Staged form (SFX_D >= 3): the input planes of a lane stream through SFX_D
+ * slots of shared memory filled by cp.async (zero fill outside [0, xlim)),
+ * SFX_D - 1 planes ahead of use, so the loads in flight cost no registers;
+ * the register ring then holds exactly the 2R+1 planes the filter reads.
+ * Each thread only ever reads the slots its own copies wrote, so a
+ * cp.async.wait_group is the whole synchronisation; a slot is refilled one
+ * step after it was read. */
+constexpr int SFX_VB = SFX_V * (int)sizeof(sfx_t);   /* bytes per lane and plane */
+static_assert(SFX_VB == 4 || SFX_VB == 8 || SFX_VB == 16, "cp.async sizes");
+static_assert(SFX_D >= 3, "staging depth");
+extern __shared__ __align__(16) unsigned char sfx_smem[];
+
+__device__ __forceinline__ void sfx_stage(u32 dst, const void *src, bool in)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src), "n"(SFX_VB),
+                 "r"(in ? SFX_VB : 0)
+                 : "memory");
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void sfx_lane_staged(const sfx_t *__restrict__ p, void *const *dst,
+                                                i64 lane_off, i64 nx, i64 plane, i64 xb, i64 xe,
+                                                const sfx_taps &t)
+{
+    constexpr int RM = SFX_RM, K = 2 * RM + 1, D = SFX_D, V = SFX_V;
+    constexpr u32 STRIDE = SFX_THREADS * SFX_VB;
+    const i64 xlim = min(nx, xe + RM);                 /* inputs used: [xb-RM, xlim) */
+    const u32 sb = (u32)__cvta_generic_to_shared(sfx_smem) + threadIdx.x * SFX_VB;
+    const unsigned char *sp = sfx_smem + threadIdx.x * SFX_VB;
+    /* step s of the stream consumes input plane xb - RM + s */
+    auto stage = [&](i64 s, int slot) {
+        const i64 xi = xb - RM + s;
+        const bool in = xi >= 0 && xi < xlim;
+        sfx_stage(sb + (u32)slot * STRIDE, in ? p + xi * plane : p, in);
+    };
+#pragma unroll
+    for (int i = 0; i < D - 1; ++i) stage(i, i);
+    float ring[K][V];                                  /* ring[s % K] = plane of step s */
+    const i64 S = (xe - xb) + 2 * RM;
+    int slot = 0;
+    for (i64 s0 = 0; s0 < S; s0 += K) {
+#pragma unroll
+        for (int u = 0; u < K; ++u) {
+            const i64 s = s0 + u;
+            if (s < S) {
+                asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 2) : "memory");
+                sf_ld<sfx_t, V, false>(reinterpret_cast<const sfx_t *>(sp + slot * STRIDE), ring[u]);
+                stage(s + D - 1, slot == 0 ? D - 1 : slot - 1);
+                slot = slot + 1 == D ? 0 : slot + 1;
+                if (s >= 2 * RM) {
+                    /* output plane x = xb + s - 2R, centred on ring slot c */
+                    const i64 x = xb + s - 2 * RM;
+                    const int c = (u + RM + 1) % K;
+                    float o[SFX_NOUT][V];
+                    if constexpr (V % 2 == 0) {
+                        constexpr int H = V / 2 > 0 ? V / 2 : 1;
+                        f2 acc[SFX_NOUT][H];
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            const f2 m = f2_pack(ring[c][2 * h], ring[c][2 * h + 1]);
+#pragma unroll
+                            for (int k = 0; k < SFX_NOUT; ++k)
+                                acc[k][h] = f2_mul(f2_pack(t.g[k][0], t.g[k][0]), m);
+                        }
+#pragma unroll
+                        for (int j = 1; j <= RM; ++j)
+#pragma unroll
+                            for (int h = 0; h < H; ++h) {
+                                const int a0 = (c + j) % K, a1 = (c + K - j) % K;
+                                const f2 ps = f2_add(f2_pack(ring[a0][2 * h], ring[a0][2 * h + 1]),
+                                                     f2_pack(ring[a1][2 * h], ring[a1][2 * h + 1]));
+#pragma unroll
+                                for (int k = 0; k < SFX_NOUT; ++k)
+                                    if (j <= sfx_r(k))
+                                        acc[k][h] = f2_fma(f2_pack(t.g[k][j], t.g[k][j]), ps, acc[k][h]);
+                            }
+#pragma unroll
+                        for (int k = 0; k < SFX_NOUT; ++k)
+#pragma unroll
+                            for (int h = 0; h < H; ++h) {
+                                o[k][2 * h] = f2_lo(acc[k][h]);
+                                o[k][2 * h + 1] = f2_hi(acc[k][h]);
+                            }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+#pragma unroll
+                            for (int k = 0; k < SFX_NOUT; ++k) o[k][v] = t.g[k][0] * ring[c][v];
+#pragma unroll
+                            for (int j = 1; j <= RM; ++j) {
+                                const float ps = ring[(c + j) % K][v] + ring[(c + K - j) % K][v];
+#pragma unroll
+                                for (int k = 0; k < SFX_NOUT; ++k)
+                                    if (j <= sfx_r(k)) o[k][v] = fmaf(t.g[k][j], ps, o[k][v]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < SFX_NOUT; ++k)
+                        sf_st<sfx_t, V>(reinterpret_cast<sfx_t *>(dst[k]) + x * plane + lane_off, o[k]);
+                }
+            }
+        }
+    }
+    /* copies of planes past the end may still be in flight */
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+#endif
+
 extern "C" __global__ void __launch_bounds__(SFX_THREADS)
 sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
 {
@@ -220,7 +369,11 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
     const i64 xb = a.xoff + (i64)blockIdx.y * a.xseg;
     const i64 xe = min(a.nx, xb + a.xseg);
     const sfx_t *p = reinterpret_cast<const sfx_t *>(a.src) + lane * SFX_V;
+#if SFX_D > 0
+    sfx_lane_staged(p, a.dst, lane * SFX_V, a.nx, a.plane, xb, xe, t);
+#else
     sfx_lane<SFX_V>(p, a.dst, lane * SFX_V, a.nx, a.plane, xb, xe, t);
+#endif
 }
 #endif /* SF_KERNEL_XPASS */
 
@@ -354,45 +507,6 @@ __host__ __device__ constexpr int sfd_max4(int a, int b, int c, int d)
 __host__ __device__ constexpr int sfd_pick(int f, int a, int b, int c, int d)
 {
     return f == 0 ? a : f == 1 ? b : f == 2 ? c : d;
-}
-
-/* ---- packed FP32 pairs (f32x2): one instruction for two lanes of work ---- */
-typedef unsigned long long f2;
-__device__ __forceinline__ f2 f2_pack(float a, float b)
-{
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float f2_lo(f2 v)
-{
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return a;
-}
-__device__ __forceinline__ float f2_hi(f2 v)
-{
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-    return b;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c)
-{
-    f2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
-{
-    f2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
-{
-    f2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
 }
 
 /* four consecutive staged elements as two pairs (low, high) */

@@ -211,7 +211,8 @@ struct sf_ctx {
     void *scratch = nullptr;          /* n_slots cubes, storage dtype */
     size_t cube_bytes = 0;
     int xv = 1;                       /* elements per lane */
-    int xpf = 4;                      /* ring prefetch depth */
+    int xpf = 4;                      /* ring prefetch depth (register-ring form) */
+    int xd = 0;                       /* shared-memory staging depth, 0 = register ring */
     int xthreads = 256;
     long long xseg = 0;
     std::vector<std::vector<int>> xgroups;   /* slots per x-pass launch */
@@ -360,6 +361,7 @@ sf_status build_xpass(sf_ctx *c, const std::vector<int> &slots, Launch *L)
     p += "#define SFX_PF " + std::to_string(c->xpf) + "\n";
     p += "#define SFX_V " + std::to_string(c->xv) + "\n";
     p += "#define SFX_THREADS " + std::to_string(c->xthreads) + "\n";
+    p += "#define SFX_D " + std::to_string(c->xd) + "\n";
     p += std::string("typedef ") + storage_ctype(c->cfg.storage) + " sfx_t;\n";
     std::string err;
     sf_status s = jit_kernel(p, "sf_xpass", c->device, &L->kernel, err);
@@ -369,7 +371,9 @@ sf_status build_xpass(sf_ctx *c, const std::vector<int> &slots, Launch *L)
     const long long nseg = (c->cfg.nx + c->xseg - 1) / c->xseg;
     L->block = dim3(c->xthreads);
     L->grid = dim3((unsigned)((lanes + c->xthreads - 1) / c->xthreads), (unsigned)nseg);
-    L->smem = 0;
+    /* staged form: xd slots of one vector per thread */
+    L->smem = c->xd > 0 ? (size_t)c->xd * c->xthreads * c->xv * c->ebytes : 0;
+    if (L->smem > 48 * 1024 && (s = set_smem(c, L->kernel, L->smem)) != SF_OK) return s;
     return SF_OK;
 }
 
@@ -1171,12 +1175,20 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
     int rxm = 0;
     for (int r : c->xy_radius) rxm = std::max(rxm, r);
     c->xpf = env_int("SF_XPF", 2);
-    const int ring = 2 * rxm + 1 + c->xpf;
+    /* staged form: input planes stream through xd shared-memory slots per
+     * thread, so the register ring holds just the 2R+1 planes in use */
+    c->xd = std::max(0, std::min(16, env_int("SF_XD", 8)));
+    if (c->xd > 0 && c->xd < 3) c->xd = 3;
+    const int ring = 2 * rxm + 1 + (c->xd > 0 ? 0 : c->xpf);
     c->xv = 1;
     for (int v = vmax; v >= 1; v /= 2)
         if (plane % v == 0 && (v == 1 || v * ring <= 96)) { c->xv = v; break; }
     const int xv_env = env_int("SF_XV", 0);
     if (xv_env > 0 && xv_env <= vmax && plane % xv_env == 0) c->xv = xv_env;
+    /* cp.async copies 4, 8 or 16 bytes */
+    if (c->xv * (int)c->ebytes < 4) c->xd = 0;
+    const int xt_env = env_int("SF_XT", 128);
+    c->xthreads = (xt_env == 64 || xt_env == 128 || xt_env == 256 || xt_env == 512) ? xt_env : 128;
     c->xseg = g.nx;
     const int nseg = env_int("SF_XSEG", 1);
     if (nseg > 1) c->xseg = (g.nx + nseg - 1) / nseg;
