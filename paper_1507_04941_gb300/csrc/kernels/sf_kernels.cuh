@@ -680,6 +680,16 @@ struct sfw_maps { sf_tmap m[SFD_NSRC]; };
 constexpr int SFW_RG = SFD_WY / 8;                 /* row groups of 8 */
 constexpr int SFW_LPW = 32 / SFD_P;                /* lanes per 32-z mask word */
 constexpr int SFW_NW = SFD_WZ / 32;                /* mask words per window row */
+#ifndef SFD_ZMAP
+#define SFD_ZMAP 0
+#endif
+constexpr int SFW_RPW = 32 / (SFD_WZ / SFD_P);     /* rows per warp (layout 1) */
+/* lanes of one mask word: stride SFW_LST, position sfw_la(lane) */
+constexpr int SFW_LST = SFD_ZMAP == 1 ? 1 : 8;
+__device__ __forceinline__ int sfw_la(int lane)
+{
+    return SFD_ZMAP == 1 ? lane % SFW_LPW : (lane >> 3) % SFW_LPW;
+}
 constexpr int SFW_SLAB_STRIDE = (SFD_OFF_SLAB1 - SFD_OFF_SLAB0) / (int)sizeof(sfd_t);
 constexpr unsigned long long SFW_TIMEOUT_NS = 2000000000ull;
 
@@ -909,10 +919,11 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
                 for (int i = 0; i < SFD_P; ++i) bits |= (c[f][i] > T[f] ? 1u : 0u) << i;
             bits &= S.vmask;
             /* the SFW_LPW lanes of one 32-z word combine their pieces */
-            u32 word = bits << (SFD_P * ((lane >> 3) % SFW_LPW));
+            u32 word = bits << (SFD_P * sfw_la(lane));
 #pragma unroll
-            for (int off = 8; off < 8 * SFW_LPW; off <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, off);
-            if ((lane >> 3) % SFW_LPW == 0) {
+            for (int off = SFW_LST; off < SFW_LST * SFW_LPW; off <<= 1)
+                word |= __shfl_xor_sync(0xffffffffu, word, off);
+            if (sfw_la(lane) == 0) {
                 u32 *mw = S.mask + (p * SFD_WY + S.row) * SFW_NW + (S.chunk * SFD_P) / 32;
                 *mw |= word;
             }
@@ -1024,8 +1035,15 @@ __device__ __forceinline__ void sfw_init(sfw_state &S, unsigned char *raw)
     S.dead = false;
     S.tma = SFD_TMA != 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#if SFD_ZMAP == 1
+    /* warp w owns whole rows: lane l takes row w*RPW + (l/CA) % RPW and chunk
+     * (l % CA) + CA*(l / (CA*RPW)); an 8-lane phase reads four chunks of two rows */
+    S.row = warp * SFW_RPW + (lane / SFW_LPW) % SFW_RPW;
+    S.chunk = lane % SFW_LPW + SFW_LPW * (lane / (SFW_LPW * SFW_RPW));
+#else
     S.row = (warp % SFW_RG) * 8 + (lane & 7);
     S.chunk = (warp / SFW_RG) * 4 + (lane >> 3);
+#endif
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar + 8u) : "memory");
@@ -1081,7 +1099,7 @@ __device__ __forceinline__ bool sfw_window(const sf_dargs &a, const sfd_taps &t,
     }
     __syncthreads();
     /* mask words of the window: one owner lane per (row, word) */
-    if ((lane >> 3) % SFW_LPW == 0 && rowv) {
+    if (sfw_la(lane) == 0 && rowv) {
         const int wd = (S.chunk * SFD_P) / 32;
         const i64 gw = (S.z0 >> 5) + wd;
         if (gw < a.nw32)

@@ -660,6 +660,8 @@ bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, 
     p += "#define SFD_WX " + std::to_string(g.wx) + "\n";
     /* resident CTAs per SM the register allocation must allow */
     p += "#define SFD_MINB " + std::to_string(minb) + "\n";
+    /* z-pass thread layout: whole rows per warp where the tile allows it */
+    if (env_int("SF_ZMAP", 1) == 1 && 32 % (g.wz / P) == 0) p += "#define SFD_ZMAP 1\n";
     /* packed FP32 pairs (fma/add/mul .f32x2) for the y and z filters */
     p += std::string("#define SFD_X2 ") + (env_int("SF_NO_X2", 0) ? "0" : "1") + "\n";
     p += "#define SFD_OFF_SLAB0 " + std::to_string(wp.off_s0) + "\n";
