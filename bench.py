@@ -28,6 +28,9 @@ METRIC = ("voxels·filters/s and % of HBM roofline (FP32 vs FP16-stored); "
 UNIT = "voxels·filters/s"
 SMS = 152
 FP32_LANES_PER_SM = 128
+# sf_window_detect DRAM traffic, read + write, per voxel of the cube (ncu capture
+# of the 608x256x384 tile-recipe case: 745.546 MB / 59,768,832 voxels)
+WINDOW_TRAFFIC_PER_VOXEL = 745.546e6 / 59768832
 
 
 def _peaks():
@@ -240,10 +243,18 @@ def run_ours(args):
     dominant = "fused" if (fused and (not xs or fused["ms_per_launch"] >= xs["ms_per_launch"])) \
         else "x"
     kname = "sf_persist" if persistent else "sf_window_detect"
+    # DRAM bytes per launch from the committed ncu capture of this kernel
+    # (profiles/sf_window_detect_sf_xpass_tile-recipe-608x256x384.md): 745.5 MB
+    # for the 608x256x384 case of the same recipe, bank and windows, scaled by
+    # voxels; only for that configuration of the window kernel
+    traffic = None
+    if (kname == "sf_window_detect" and storage == "f32" and tuple(w.bank) == synth.BANK6
+            and tuple(w.window) == (32, 32, 64)):
+        traffic = WINDOW_TRAFFIC_PER_VOXEL * w.voxels
     if dominant == "fused":
         roof = {"kernel": kname, "bound": "alu", "achieved": fused["tflops"],
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": fused["tflops"] / alu_peak,
-                "traffic": None,
+                "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median "
                                "SM clock sampled during the timed region)",
                 "hbm_view": {"achieved_gbs": fused["gbs"], "peak_gbs": hbm_peak,
