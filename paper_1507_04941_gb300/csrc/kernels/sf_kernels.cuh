@@ -183,7 +183,7 @@ __device__ __forceinline__ f2 f2_add(f2 a, f2 b)
 }
 
 /* ======================================================================= */
-#if defined(SF_KERNEL_XPASS) || defined(SF_KERNEL_PERSIST)
+#if defined(SF_KERNEL_XPASS) || defined(SF_KERNEL_PERSIST) || defined(SF_KERNEL_XBATCH)
 /* Prelude: SFX_NOUT, SFX_R0..SFX_R3 (radii, 0 = unused), SFX_RM (max radius),
  * SFX_PF (prefetch depth), typedef sfx_t; the stand-alone kernel adds SFX_V and
  * SFX_THREADS. */
@@ -248,44 +248,40 @@ __device__ __forceinline__ void sfx_lane(const sfx_t *__restrict__ p, void *cons
         }
     }
 }
-#endif
 
-#ifdef SF_KERNEL_XPASS
-#if SFX_D > 0
-/* Staged form (SFX_D >= 3): the input planes of a lane stream through SFX_D
- * slots of shared memory filled by cp.async (zero fill outside [0, xlim)),
- * SFX_D - 1 planes ahead of use, so the loads in flight cost no registers;
- * the register ring then holds exactly the 2R+1 planes the filter reads.
- * Each thread only ever reads the slots its own copies wrote, so a
- * cp.async.wait_group is the whole synchronisation; a slot is refilled one
- * step after it was read. */
-constexpr int SFX_VB = SFX_V * (int)sizeof(sfx_t);   /* bytes per lane and plane */
-static_assert(SFX_VB == 4 || SFX_VB == 8 || SFX_VB == 16, "cp.async sizes");
-static_assert(SFX_D >= 3, "staging depth");
-extern __shared__ __align__(16) unsigned char sfx_smem[];
-
+/* Staged form: the input planes of a lane stream through D slots of shared
+ * memory filled by cp.async (zero fill outside [0, xlim)), D - 1 planes ahead
+ * of use, so the loads in flight cost no registers; the register ring then
+ * holds exactly the 2R+1 planes the filter reads.  Each thread only ever
+ * reads the slots its own copies wrote, so a cp.async.wait_group is the whole
+ * synchronisation; a slot is refilled one step after it was read.  sb / sp:
+ * the thread's slot 0 (shared address / pointer), slots THREADS*V elements
+ * apart. */
+template <int V>
 __device__ __forceinline__ void sfx_stage(u32 dst, const void *src, bool in)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src), "n"(SFX_VB),
-                 "r"(in ? SFX_VB : 0)
+    constexpr int VB = V * (int)sizeof(sfx_t);
+    static_assert(VB == 4 || VB == 8 || VB == 16, "cp.async sizes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src), "n"(VB),
+                 "r"(in ? VB : 0)
                  : "memory");
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
+template <int V, int THREADS, int D>
 __device__ __forceinline__ void sfx_lane_staged(const sfx_t *__restrict__ p, void *const *dst,
                                                 i64 lane_off, i64 nx, i64 plane, i64 xb, i64 xe,
-                                                const sfx_taps &t)
+                                                const sfx_taps &t, u32 sb, const unsigned char *sp)
 {
-    constexpr int RM = SFX_RM, K = 2 * RM + 1, D = SFX_D, V = SFX_V;
-    constexpr u32 STRIDE = SFX_THREADS * SFX_VB;
+    static_assert(D >= 3, "staging depth");
+    constexpr int RM = SFX_RM, K = 2 * RM + 1;
+    constexpr u32 STRIDE = THREADS * V * (u32)sizeof(sfx_t);
     const i64 xlim = min(nx, xe + RM);                 /* inputs used: [xb-RM, xlim) */
-    const u32 sb = (u32)__cvta_generic_to_shared(sfx_smem) + threadIdx.x * SFX_VB;
-    const unsigned char *sp = sfx_smem + threadIdx.x * SFX_VB;
     /* step s of the stream consumes input plane xb - RM + s */
     auto stage = [&](i64 s, int slot) {
         const i64 xi = xb - RM + s;
         const bool in = xi >= 0 && xi < xlim;
-        sfx_stage(sb + (u32)slot * STRIDE, in ? p + xi * plane : p, in);
+        sfx_stage<V>(sb + (u32)slot * STRIDE, in ? p + xi * plane : p, in);
     };
 #pragma unroll
     for (int i = 0; i < D - 1; ++i) stage(i, i);
@@ -361,6 +357,10 @@ __device__ __forceinline__ void sfx_lane_staged(const sfx_t *__restrict__ p, voi
 }
 #endif
 
+#ifdef SF_KERNEL_XPASS
+#if SFX_D > 0
+extern __shared__ __align__(16) unsigned char sfx_smem[];
+#endif
 extern "C" __global__ void __launch_bounds__(SFX_THREADS)
 sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
 {
@@ -370,12 +370,59 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
     const i64 xe = min(a.nx, xb + a.xseg);
     const sfx_t *p = reinterpret_cast<const sfx_t *>(a.src) + lane * SFX_V;
 #if SFX_D > 0
-    sfx_lane_staged(p, a.dst, lane * SFX_V, a.nx, a.plane, xb, xe, t);
+    constexpr u32 VB = SFX_V * (u32)sizeof(sfx_t);
+    sfx_lane_staged<SFX_V, SFX_THREADS, SFX_D>(
+        p, a.dst, lane * SFX_V, a.nx, a.plane, xb, xe, t,
+        (u32)__cvta_generic_to_shared(sfx_smem) + threadIdx.x * VB, sfx_smem + threadIdx.x * VB);
 #else
     sfx_lane<SFX_V>(p, a.dst, lane * SFX_V, a.nx, a.plane, xb, xe, t);
 #endif
 }
 #endif /* SF_KERNEL_XPASS */
+
+#ifdef SF_KERNEL_XBATCH
+/* sf_xpass_batch: the staged x pass of every cube of a batch in one launch
+ * (SFX_THREADS threads, SFX_D slots per thread, lanes of two elements, or one
+ * where the y-z plane is odd).  Block b finds its cube by bisection of the
+ * block0 column of the table. */
+extern __shared__ __align__(16) unsigned char sfx_smem[];
+
+template <int V>
+__device__ __forceinline__ void sfx_batch_lane(const sf_xcube &q, i64 lane, const sfx_taps &t)
+{
+    constexpr u32 VB = V * (u32)sizeof(sfx_t);
+    const sfx_t *p = reinterpret_cast<const sfx_t *>(q.src) + lane * V;
+    sfx_lane_staged<V, SFX_THREADS, SFX_D>(p, q.dst, lane * V, q.nx, q.plane, q.x0, q.x1, t,
+                                           (u32)__cvta_generic_to_shared(sfx_smem) + threadIdx.x * VB,
+                                           sfx_smem + threadIdx.x * VB);
+}
+
+extern "C" __global__ void __launch_bounds__(SFX_THREADS, 6)
+sf_xpass_batch(const __grid_constant__ sf_xbargs a, const __grid_constant__ sfx_taps t)
+{
+    const int blk = (int)blockIdx.x;
+    int lo = 0, hi = a.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.cubes[mid].block0 <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const sf_xcube &q = a.cubes[lo];
+    const i64 lane = (i64)(blk - q.block0) * SFX_THREADS + threadIdx.x;
+    if (lane >= q.lanes) return;
+    if constexpr (sizeof(sfx_t) == 4) {
+        if (q.v == 2) sfx_batch_lane<2>(q, lane, t);
+        else sfx_batch_lane<1>(q, lane, t);
+    } else {
+        if (q.v == 2) sfx_batch_lane<2>(q, lane, t);
+        else {
+            /* two-byte lanes are below the cp.async size: register ring */
+            const sfx_t *p = reinterpret_cast<const sfx_t *>(q.src) + lane;
+            sfx_lane<1>(p, q.dst, lane, q.nx, q.plane, q.x0, q.x1, t);
+        }
+    }
+}
+#endif /* SF_KERNEL_XBATCH */
 
 /* ======================================================================= */
 #if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_FILTER) || defined(SF_KERNEL_PERSIST)
@@ -1019,7 +1066,7 @@ template <int IDX> __device__ __forceinline__ void sfw_first_load(const sf_dargs
 }
 
 /* shared-memory carve-up, thread roles and barrier set-up (once per CTA) */
-__device__ __forceinline__ void sfw_init(sfw_state &S, unsigned char *raw)
+__device__ __forceinline__ void sfw_init(sfw_state &S, unsigned char *raw, bool barriers = true)
 {
     unsigned char *sm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<unsigned long long>(raw) + 127ull) & ~127ull);
@@ -1044,6 +1091,7 @@ __device__ __forceinline__ void sfw_init(sfw_state &S, unsigned char *raw)
     S.row = (warp % SFW_RG) * 8 + (lane & 7);
     S.chunk = (warp / SFW_RG) * 4 + (lane >> 3);
 #endif
+    if (!barriers) return;
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar + 8u) : "memory");
@@ -1125,8 +1173,13 @@ sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd
 
 /* ======================================================================= */
 #ifdef SF_KERNEL_PERSIST
+#ifndef SFP_XITEMS
+#define SFP_XITEMS 1
+#endif
 /*
- * sf_persist: every unit's x pass and windows in one persistent launch.
+ * sf_persist: every unit's windows, and (SFP_XITEMS) its x pass, in one
+ * persistent launch.  Without x items the x pass of the batch runs as
+ * sf_xpass_batch just before, in the same graph.
  * CTAs pull items from a global counter.  Items are ordered so that all x
  * items of a unit come before its window items; a window item waits (bounded
  * by %globaltimer) until the unit's x items are all complete.  x items never
@@ -1154,8 +1207,11 @@ sf_persist(const __grid_constant__ sf_pargs pa, const __grid_constant__ sfd_taps
 {
     extern __shared__ __align__(128) unsigned char sfp_raw[];
     __shared__ int s_item;
-    sfw_state S;
-    sfw_init(S, sfp_raw);
+    u32 phase = 0;   /* mbarrier parities, carried from one window item to the next */
+    {
+        sfw_state S0;
+        sfw_init(S0, sfp_raw);
+    }
     const sf_tmap *maps = reinterpret_cast<const sf_tmap *>(pa.maps);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(pa.head, 1);
@@ -1166,6 +1222,7 @@ sf_persist(const __grid_constant__ sf_pargs pa, const __grid_constant__ sfd_taps
         const sf_item it = pa.items[item];
         const sf_unit &u = pa.units[it.unit];
         if (it.kind == 0) {
+#if SFP_XITEMS
             /* x pass of lanes [index*xlanes, (index+1)*xlanes) over the unit's planes */
             const i64 l0 = (i64)it.index * u.xlanes;
             const i64 l1 = min(u.lanes, l0 + u.xlanes);
@@ -1184,9 +1241,10 @@ sf_persist(const __grid_constant__ sf_pargs pa, const __grid_constant__ sfd_taps
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) atomicAdd(pa.xdone + it.unit, 1);
+#endif
         } else {
             bool ok = true;
-            if (threadIdx.x == 0) {
+            if (SFP_XITEMS && threadIdx.x == 0) {
                 ok = sfp_wait_count(pa.xdone + it.unit, u.n_xitems);
                 /* the x-filtered planes were written through the generic proxy
                  * by other CTAs; order them before this CTA's TMA reads */
@@ -1196,10 +1254,14 @@ sf_persist(const __grid_constant__ sf_pargs pa, const __grid_constant__ sfd_taps
                 if (threadIdx.x == 0) atomicOr(pa.err, 1);
                 return;
             }
+            sfw_state S;
+            sfw_init(S, sfp_raw, false);
+            S.phase = phase;
             S.tma = u.tma != 0;
             const int per = u.args.nwy * u.args.nwz;
             const int wid = (u.wx0 + it.index / per) * per + it.index % per;
             if (!sfw_window(u.args, t, maps + u.map_base, S, wid)) return;
+            phase = S.phase;
         }
     }
 }

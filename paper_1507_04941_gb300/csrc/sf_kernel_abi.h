@@ -26,6 +26,25 @@ struct sf_xargs {
     long long xoff;    /* first output plane of grid row 0 */
 };
 
+/* x pass of many cubes in one launch: blocks [block0, next block0) of the
+ * grid take the lanes of one cube, V elements per lane. */
+struct sf_xcube {
+    const void *src;
+    void *dst[SF_MAX_XOUT];
+    long long nx;
+    long long x0, x1;  /* output planes [x0, x1) (the whole cube: 0, nx) */
+    long long plane;   /* ny * nz */
+    long long lanes;   /* plane / v */
+    int v;             /* elements per lane: 2, or 1 for an odd y-z plane */
+    int block0;        /* first block of this cube */
+};
+
+struct sf_xbargs {
+    const struct sf_xcube *cubes;   /* ordered by block0 */
+    int n;
+    int pad_;
+};
+
 /* fused y/z filter + window statistics + threshold + mask union */
 struct sf_dargs {
     const void *src[SF_MAX_SRC];

@@ -264,6 +264,7 @@ struct sf_ctx {
     void *bscratch = nullptr;         /* scratch of all cubes (batched contexts) */
     struct PersistPlan {
         int P = 8, minb = 3, pf = 2, xlanes = 1024, slab = 0;
+        bool xbatch = false;   /* x pass as one batched launch before the windows */
     } pp;
     bool pready = false;
     Launch plaunch;
@@ -277,6 +278,8 @@ struct sf_ctx {
     sf_item *d_items = nullptr;
     CUtensorMap *d_maps = nullptr, *h_maps = nullptr;
     int *d_ctr = nullptr;             /* [0] head, [1 + u] x items done of unit u */
+    sf_xcube *d_xcubes = nullptr, *h_xcubes = nullptr;   /* batched x pass table */
+    Launch xblaunch;                  /* batched x pass */
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gstream = nullptr;
     cudaEvent_t gdone = nullptr;
@@ -753,8 +756,11 @@ void free_persist(sf_ctx *c)
     cudaFree(c->d_items);
     cudaFree(c->d_maps);
     cudaFree(c->d_ctr);
+    cudaFree(c->d_xcubes);
     cudaFreeHost(c->h_units);
     cudaFreeHost(c->h_maps);
+    cudaFreeHost(c->h_xcubes);
+    c->d_xcubes = c->h_xcubes = nullptr;
     c->gexec = nullptr;
     c->gstream = nullptr;
     c->gdone = nullptr;
@@ -792,15 +798,30 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
         r[i] = c->xy_radius[i];
         rm = std::max(rm, r[i]);
     }
-    std::string p = "#define SF_KERNEL_PERSIST 1\n" + wp.prelude + "#define SFD_TMA 1\n";
-    p += "#define SFX_NOUT " + std::to_string(std::max(1, nxy)) + "\n";
-    for (int i = 0; i < 4; ++i) p += "#define SFX_R" + std::to_string(i) + " " + std::to_string(r[i]) + "\n";
-    p += "#define SFX_RM " + std::to_string(rm) + "\n";
-    p += "#define SFX_PF " + std::to_string(pp.pf) + "\n";
-    p += std::string("typedef ") + storage_ctype(g.storage) + " sfx_t;\n";
+    std::string xp = "#define SFX_NOUT " + std::to_string(std::max(1, nxy)) + "\n";
+    for (int i = 0; i < 4; ++i) xp += "#define SFX_R" + std::to_string(i) + " " + std::to_string(r[i]) + "\n";
+    xp += "#define SFX_RM " + std::to_string(rm) + "\n";
+    xp += "#define SFX_PF " + std::to_string(pp.pf) + "\n";
+    xp += std::string("typedef ") + storage_ctype(g.storage) + " sfx_t;\n";
+    const bool xbatch = pp.xbatch && nxy > 0;
+    std::string p = "#define SF_KERNEL_PERSIST 1\n" + wp.prelude + "#define SFD_TMA 1\n" + xp;
+    if (xbatch) p += "#define SFP_XITEMS 0\n";
     std::string err;
     sf_status st = jit_kernel(p, "sf_persist", c->device, &c->plaunch.kernel, err);
     if (st != SF_OK) return fail(c, st, "persistent kernel: %s", err.c_str());
+    constexpr int kXbThreads = 128, kXbDepth = 8;
+    if (xbatch) {
+        /* the staged x pass of every cube in one launch, 16 bytes per slot */
+        const std::string xb = "#define SF_KERNEL_XBATCH 1\n" + xp + "#define SFX_THREADS " +
+                               std::to_string(kXbThreads) + "\n#define SFX_D " +
+                               std::to_string(kXbDepth) + "\n";
+        if ((st = jit_kernel(xb, "sf_xpass_batch", c->device, &c->xblaunch.kernel, err)) != SF_OK)
+            return fail(c, st, "batched x pass: %s", err.c_str());
+        c->xblaunch.block = dim3(kXbThreads);
+        c->xblaunch.smem = (size_t)kXbDepth * kXbThreads * 2 * c->ebytes;
+        if (c->xblaunch.smem > 48 * 1024 && (st = set_smem(c, c->xblaunch.kernel, c->xblaunch.smem)) != SF_OK)
+            return st;
+    }
     if (wp.smem > 48 * 1024 && (st = set_smem(c, c->plaunch.kernel, wp.smem)) != SF_OK) return st;
     int per_sm = 0, nsm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)c->plaunch.kernel,
@@ -833,7 +854,7 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
             u.tma = q.tma ? 1 : 0;
             u.map_base = (int)i * c->pnsrc;
             u.xlanes = pp.xlanes;
-            u.n_xitems = nxy > 0 ? (int)((u.lanes + pp.xlanes - 1) / pp.xlanes) : 0;
+            u.n_xitems = nxy > 0 && !xbatch ? (int)((u.lanes + pp.xlanes - 1) / pp.xlanes) : 0;
             u.wx0 = (int)(x0 / g.wx);
             const int nwxu = (int)((u.x1 - x0 + g.wx - 1) / g.wx);
             c->units.push_back(u);
@@ -865,6 +886,33 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
         return fail(c, SF_ENOMEM, "persistent-form tables");
     }
     std::memset(c->h_maps, 0, sizeof(CUtensorMap) * std::max<size_t>(1, nmaps));
+    long long xblocks = 0;
+    if (xbatch) {
+        const size_t nc = c->cubes.size();
+        if ((e = cudaMalloc(&c->d_xcubes, sizeof(sf_xcube) * nc)) != cudaSuccess ||
+            (e = cudaMallocHost(&c->h_xcubes, sizeof(sf_xcube) * nc)) != cudaSuccess) {
+            cudaGetLastError();
+            free_persist(c);
+            return fail(c, SF_ENOMEM, "batched x-pass table");
+        }
+        /* per cube: lanes of two elements, or one where the y-z plane is odd */
+        for (size_t i = 0; i < nc; ++i) {
+            const sf_ctx::Cube &q = c->cubes[i];
+            sf_xcube &xc = c->h_xcubes[i];
+            std::memset(&xc, 0, sizeof(xc));
+            const long long plane = q.ny * q.nz;
+            xc.v = plane % 2 == 0 ? 2 : 1;
+            xc.nx = q.nx;
+            xc.x0 = 0;
+            xc.x1 = q.nx;
+            xc.plane = plane;
+            xc.lanes = plane / xc.v;
+            xc.block0 = (int)xblocks;
+            xblocks += (xc.lanes + kXbThreads - 1) / kXbThreads;
+        }
+        if (xblocks > INT32_MAX) return fail(c, SF_EINVAL, "batched x pass: too many blocks");
+        c->xblaunch.grid = dim3((unsigned)xblocks);
+    }
     if (!items.empty() &&
         (e = cudaMemcpy(c->d_items, items.data(), sizeof(sf_item) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(c, e, "item table");
@@ -903,6 +951,21 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
     cudaMemcpyAsync(c->d_units, c->h_units, sizeof(sf_unit) * nu, cudaMemcpyHostToDevice, c->gstream);
     cudaMemcpyAsync(c->d_maps, c->h_maps, sizeof(CUtensorMap) * std::max<size_t>(1, nmaps),
                     cudaMemcpyHostToDevice, c->gstream);
+    cudaError_t xe = cudaSuccess;
+    if (xbatch) {
+        cudaMemcpyAsync(c->d_xcubes, c->h_xcubes, sizeof(sf_xcube) * c->cubes.size(),
+                        cudaMemcpyHostToDevice, c->gstream);
+        sf_xbargs xa{};
+        xa.cubes = c->d_xcubes;
+        xa.n = (int)c->cubes.size();
+        void *xargs[] = {&xa, c->pxtaps.data()};
+        cudaLaunchConfig_t xl{};
+        xl.gridDim = c->xblaunch.grid;
+        xl.blockDim = c->xblaunch.block;
+        xl.dynamicSmemBytes = c->xblaunch.smem;
+        xl.stream = c->gstream;
+        xe = cudaLaunchKernelExC(&xl, (const void *)c->xblaunch.kernel, xargs);
+    }
     void *args[] = {&pa, c->ptaps.data(), c->pxtaps.data()};
     cudaLaunchConfig_t lc{};
     lc.gridDim = c->plaunch.grid;
@@ -912,6 +975,7 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
     cudaError_t le = cudaLaunchKernelExC(&lc, (const void *)c->plaunch.kernel, args);
     e = cudaStreamEndCapture(c->gstream, &graph);
     if (le != cudaSuccess) e = le;
+    if (xe != cudaSuccess) e = xe;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(c, e, "persistent graph");
@@ -957,6 +1021,16 @@ sf_status run_persist(sf_ctx *c, const void *const *cubes, uint32_t *const *mask
         for (int k = 0; k < SF_MAX_XOUT; ++k)
             h.xdst[k] = k < (int)c->xy_sigma.size() ? (void *)((char *)q.slots + (size_t)k * q.slot_bytes) : nullptr;
         c->h_units[u] = h;
+    }
+    if (c->h_xcubes) {
+        for (size_t i = 0; i < c->cubes.size(); ++i) {
+            const sf_ctx::Cube &q = c->cubes[i];
+            sf_xcube &xc = c->h_xcubes[i];
+            xc.src = cubes[i];
+            for (int k = 0; k < SF_MAX_XOUT; ++k)
+                xc.dst[k] = k < (int)c->xy_sigma.size() ? (void *)((char *)q.slots + (size_t)k * q.slot_bytes)
+                                                        : nullptr;
+        }
     }
     for (size_t i = 0; i < c->cubes.size(); ++i) {
         const sf_ctx::Cube &q = c->cubes[i];
@@ -1235,7 +1309,11 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
             q.slots = c->bscratch ? (char *)c->bscratch + off : nullptr;
             off += q.slot_bytes * c->xy_sigma.size();
         }
-        if (s == SF_OK) s = plan_persist(c, sf_ctx::PersistPlan{});
+        if (s == SF_OK) {
+            sf_ctx::PersistPlan dp;
+            dp.xbatch = true;   /* the default until sf_tune chooses */
+            s = plan_persist(c, dp);
+        }
         if (s != SF_OK) {
             {
                 std::lock_guard<std::mutex> lk(g_err_mu);
@@ -1538,6 +1616,12 @@ sf_status sf_tune(sf_ctx *c, const void *const *d_cubes, uint32_t *const *d_mask
     int best_kind = -1;   /* -1: two-kernel path, else index into cands */
     std::vector<sf_ctx::PersistPlan> cands;
     const long long maxnx = c->batch ? 0 : c->cfg.nx;
+    {
+        /* x pass as one batched launch, then the windows */
+        sf_ctx::PersistPlan q;
+        q.xbatch = true;
+        cands.push_back(q);
+    }
     for (int slab : {0, 128, 256}) {
         if (!c->batch && slab > 0 && slab >= maxnx) continue;
         for (int xl : {1024, 4096}) {
@@ -1575,8 +1659,12 @@ sf_status sf_tune(sf_ctx *c, const void *const *d_cubes, uint32_t *const *d_mask
         }, &s);
         if (s != SF_OK) break;
         if (rep.size() > 1) rep += ", ";
-        rep += "{\"path\": \"persistent\", \"slab\": " + std::to_string(cands[k].slab) +
-               ", \"x_lanes_per_item\": " + std::to_string(cands[k].xlanes) + ", \"ms\": " + std::to_string(ms) + "}";
+        if (cands[k].xbatch)
+            rep += "{\"path\": \"batched x pass + persistent windows\", \"ms\": " + std::to_string(ms) + "}";
+        else
+            rep += "{\"path\": \"persistent\", \"slab\": " + std::to_string(cands[k].slab) +
+                   ", \"x_lanes_per_item\": " + std::to_string(cands[k].xlanes) + ", \"ms\": " +
+                   std::to_string(ms) + "}";
         if (ms > 0.f && ms < best) {
             best = ms;
             best_kind = (int)k;

@@ -90,7 +90,7 @@ def test_tune_keeps_results(dev):
     with BatchSourceFinder(SHAPES, BANK6, 3.0, (32, 32, 64), device=dev) as bf:
         before = bf.detect(cubes)
         rep = json.loads(bf.tune(cubes))
-        assert all(r["path"] == "persistent" for r in rep)
+        assert {r["path"] for r in rep} == {"persistent", "batched x pass + persistent windows"}
         after = bf.detect(cubes)
         bf.synchronize()
         for x, y in zip(before, after):
