@@ -240,6 +240,7 @@ struct sf_ctx {
     void *host_cube = nullptr;
     unsigned int *host_mask = nullptr;
     cudaStream_t hcopy[2] = {nullptr, nullptr}, hback = nullptr;
+    cudaStream_t hcomp[2] = {nullptr, nullptr};   /* compute streams of the host pipeline */
     std::vector<cudaEvent_t> hev;
 
     /* stage timing: pairs of events per recorded stage instance */
@@ -1383,6 +1384,8 @@ sf_status sf_destroy(sf_ctx *c)
     cudaFree(c->host_cube);
     cudaFree(c->host_mask);
     cudaFree(c->err_flag);
+    for (cudaStream_t x : c->hcomp)
+        if (x) cudaStreamDestroy(x);
     for (cudaStream_t x : c->hcopy)
         if (x) cudaStreamDestroy(x);
     if (c->hback) cudaStreamDestroy(c->hback);
@@ -1759,32 +1762,39 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
         return sf_synchronize(c, stream);
     }
     /* Pipelined along x (Sec. 6: overlap input with processing): chunks of
-     * whole windows go host-to-device on two copy streams; chunk k's x pass
-     * starts once the chunks holding its planes and x halo have landed, its
-     * window kernel follows, and its mask rows go back on a third stream. */
+     * whole window slabs go host-to-device on two copy streams; chunk k's x
+     * pass starts once the chunks holding its planes and x halo have landed,
+     * its window kernel follows on the same compute stream, and its mask rows
+     * go back on a third stream.  Consecutive chunks alternate between two
+     * compute streams, so one chunk's kernels fill the tail of the other's. */
     const long long wx = c->cfg.wx;
     const long long nx = c->cfg.nx;
-    long long S = (nx + 7) / 8;
+    long long S = (nx + 15) / 16;
     S = std::max(wx, (S + wx - 1) / wx * wx);
     const int K = (int)((nx + S - 1) / S);
     int rxm = 0;
     for (int r : c->xy_radius) rxm = std::max(rxm, r);
     if (!c->hback) {
         for (int i = 0; i < 2; ++i)
-            if ((e = cudaStreamCreateWithFlags(&c->hcopy[i], cudaStreamNonBlocking)) != cudaSuccess)
-                return cuda_fail(c, e, "copy stream");
+            if ((e = cudaStreamCreateWithFlags(&c->hcopy[i], cudaStreamNonBlocking)) != cudaSuccess ||
+                (e = cudaStreamCreateWithFlags(&c->hcomp[i], cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(c, e, "pipeline stream");
         if ((e = cudaStreamCreateWithFlags(&c->hback, cudaStreamNonBlocking)) != cudaSuccess)
-            return cuda_fail(c, e, "copy stream");
+            return cuda_fail(c, e, "pipeline stream");
     }
-    while ((int)c->hev.size() < 2 * K + 1) {
+    while ((int)c->hev.size() < 2 * K + 3) {
         cudaEvent_t ev;
         if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(c, e, "pipeline events");
         c->hev.push_back(ev);
     }
-    /* the copies must not overtake earlier work on the caller's stream */
+    /* nothing may overtake earlier work on the caller's stream */
     cudaEventRecord(c->hev[2 * K], st);
-    for (int i = 0; i < 2; ++i) cudaStreamWaitEvent(c->hcopy[i], c->hev[2 * K], 0);
+    for (int i = 0; i < 2; ++i) {
+        cudaStreamWaitEvent(c->hcopy[i], c->hev[2 * K], 0);
+        cudaStreamWaitEvent(c->hcomp[i], c->hev[2 * K], 0);
+    }
+    cudaStreamWaitEvent(c->hback, c->hev[2 * K], 0);
     for (int k = 0; k < K; ++k) {
         const long long x0 = k * S, x1 = std::min(nx, x0 + S);
         cudaStream_t cs = c->hcopy[k & 1];
@@ -1793,24 +1803,27 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
             return cuda_fail(c, e, "host-to-device copy");
         cudaEventRecord(c->hev[k], cs);
     }
-    int waited = -1;
+    int waited[2] = {-1, -1};
     for (int k = 0; k < K; ++k) {
         const long long x0 = k * S, x1 = std::min(nx, x0 + S);
+        cudaStream_t ks = c->hcomp[k & 1];
         const int need = (int)(std::min(nx, x1 + rxm) - 1) / (int)S;
-        for (int j = waited + 1; j <= need; ++j) cudaStreamWaitEvent(st, c->hev[j], 0);
-        waited = std::max(waited, need);
+        for (int j = waited[k & 1] + 1; j <= need; ++j) cudaStreamWaitEvent(ks, c->hev[j], 0);
+        waited[k & 1] = std::max(waited[k & 1], need);
         for (size_t i = 0; i < c->xlaunch.size(); ++i)
-            if ((s = run_xpass(c, c->xlaunch[i], c->xgroups[i], c->host_cube, st, x0, x1)) != SF_OK) return s;
+            if ((s = run_xpass(c, c->xlaunch[i], c->xgroups[i], c->host_cube, ks, x0, x1)) != SF_OK) return s;
         const int w0 = (int)(x0 / wx) * c->nwy * c->nwz;
         const int w1 = (int)((x1 + wx - 1) / wx) * c->nwy * c->nwz;
-        if ((s = launch_windows(c, c->host_cube, c->host_mask, nullptr, nullptr, st, w0, w1)) != SF_OK) return s;
-        cudaEventRecord(c->hev[K + k], st);
+        if ((s = launch_windows(c, c->host_cube, c->host_mask, nullptr, nullptr, ks, w0, w1)) != SF_OK) return s;
+        cudaEventRecord(c->hev[K + k], ks);
         cudaStreamWaitEvent(c->hback, c->hev[K + k], 0);
         if ((e = cudaMemcpyAsync((char *)h_mask + (size_t)x0 * mplane, (const char *)c->host_mask + (size_t)x0 * mplane,
                                  (size_t)(x1 - x0) * mplane, cudaMemcpyDeviceToHost, c->hback)) != cudaSuccess)
             return cuda_fail(c, e, "device-to-host copy");
     }
-    if ((e = cudaStreamSynchronize(c->hback)) != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+    /* the caller's stream resumes after the last copy back */
+    cudaEventRecord(c->hev[2 * K + 1], c->hback);
+    cudaStreamWaitEvent(st, c->hev[2 * K + 1], 0);
     return sf_synchronize(c, stream);
 }
 
