@@ -99,6 +99,10 @@ def _load():
                                           ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
         lib.or_detect_windows.restype = ctypes.c_int
+        lib.or_local_stats.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _i64, _dp,
+                                       _dp, ctypes.c_int]
+        lib.or_local_stats.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -324,3 +328,75 @@ def unpack_bits(words, nz: int) -> np.ndarray:
     bits = (words[..., None] >> np.arange(32, dtype=np.uint32)) & 1
     nx, ny, nw = words.shape
     return bits.reshape(nx, ny, nw * 32)[:, :, :nz].astype(bool)
+
+
+# ------------------------------------------------- per-voxel local statistics
+def local_stats(c, half, idx=None, nthreads: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Mean and population std of the filtered cube c over the box of
+    half-widths half = (sx, sy, sz) around each voxel, clipped to the cube
+    (Sec. 3.3).  idx: flat voxel indices to evaluate (default: all voxels,
+    returned with c's shape)."""
+    c = np.ascontiguousarray(np.asarray(c), dtype=np.float64)
+    nx, ny, nz = c.shape
+    sx, sy, sz = (int(v) for v in half)
+    if min(sx, sy, sz) < 0:
+        raise ValueError("half-widths must be >= 0")
+    if idx is None:
+        mean = np.empty(c.shape, dtype=np.float64)
+        std = np.empty(c.shape, dtype=np.float64)
+        _load().or_local_stats(_ptr(c, _dp), nx, ny, nz, sx, sy, sz, None, 0,
+                               _ptr(mean, _dp), _ptr(std, _dp), int(nthreads))
+        return mean, std
+    idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).ravel())
+    mean = np.empty(idx.shape, dtype=np.float64)
+    std = np.empty(idx.shape, dtype=np.float64)
+    _load().or_local_stats(_ptr(c, _dp), nx, ny, nz, sx, sy, sz,
+                           _ptr(idx, ctypes.POINTER(ctypes.c_int64)), idx.size,
+                           _ptr(mean, _dp), _ptr(std, _dp), int(nthreads))
+    return mean, std
+
+
+def local_detect(d, bank, truncation, half, k, band_rel: float = 1e-4, voxels=None):
+    """The sliding-statistics form of the method (Sec. 3.3 read per voxel):
+    every filter of the bank (Eq. 2), the local mean/std of each filtered cube
+    over the box `half` around the voxel, c_f > mean_f + k std_f, OR over the
+    bank.  voxels: (x, y, z) triples to evaluate (default: the whole cube).
+
+    Returns (fire, sure, c, mean, std): fire / sure as uint8 per evaluated
+    voxel (sure = the OR cannot flip with rounding: no filter within
+    band_rel * std of its threshold unless another fires by more), and the
+    per-filter filtered values and statistics [nf][n]."""
+    d = _cube(d)
+    nx, ny, nz = d.shape
+    sx, sy, sz = (int(v) for v in half)
+    if voxels is None:
+        xs, ys, zs = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+        voxels = np.stack([xs.ravel(), ys.ravel(), zs.ravel()], axis=1)
+    voxels = np.asarray(voxels, dtype=np.int64).reshape(-1, 3)
+    nv = voxels.shape[0]
+    nf = len(bank)
+    cv = np.empty((nf, nv))
+    mv = np.empty((nf, nv))
+    sv = np.empty((nf, nv))
+    for f, (sxy, szz) in enumerate(bank):
+        if nv > 64:
+            c = filter_box(d, sxy, szz, truncation)
+            flat = (voxels[:, 0] * ny + voxels[:, 1]) * nz + voxels[:, 2]
+            mv[f], sv[f] = local_stats(c, (sx, sy, sz), flat)
+            cv[f] = c.ravel()[flat]
+        else:
+            for i, (x, y, z) in enumerate(voxels):
+                box = ((max(0, x - sx), min(nx, x + sx + 1)), (max(0, y - sy), min(ny, y + sy + 1)),
+                       (max(0, z - sz), min(nz, z + sz + 1)))
+                c = filter_box(d, sxy, szz, truncation, box)
+                lx, ly, lz = x - box[0][0], y - box[1][0], z - box[2][0]
+                m, s_ = local_stats(c, (sx, sy, sz), [(lx * c.shape[1] + ly) * c.shape[2] + lz])
+                mv[f, i], sv[f, i] = m[0], s_[0]
+                cv[f, i] = c[lx, ly, lz]
+    thr = mv + k * sv
+    fire_f = cv > thr
+    near = np.abs(cv - thr) < band_rel * sv
+    fire = fire_f.any(axis=0)
+    clear = (fire_f & ~near).any(axis=0)
+    sure = clear | ~near.any(axis=0)
+    return fire.astype(np.uint8), sure.astype(np.uint8), cv, mv, sv

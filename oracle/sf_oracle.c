@@ -396,3 +396,60 @@ int or_detect_windows(const float *d, int64_t nx, int64_t ny, int64_t nz,
     }
     return failed ? -1 : used;
 }
+
+/*
+ * Local statistics per voxel (Sec. 3.3: the mean and standard deviation of
+ * each voxel come from a user-specified range of the filtered data around it),
+ * read as the box [x-sx, x+sx] x [y-sy, y+sy] x [z-sz, z+sz] clipped to the
+ * cube, n = number of voxels in the clipped box, population statistics (two
+ * passes: the mean, then the mean squared deviation).
+ *
+ * c: filtered cube [x][y][z] (double).  The voxels evaluated are the n_idx
+ * flat indices in idx, or every voxel when idx is NULL; mean/stdv receive one
+ * value per evaluated voxel, in that order.  Returns the OpenMP threads used.
+ */
+int or_local_stats(const double *c, int64_t nx, int64_t ny, int64_t nz, int sx, int sy, int sz,
+                   const int64_t *idx, int64_t n_idx, double *mean, double *stdv, int nthreads)
+{
+    const int64_t nv = idx ? n_idx : nx * ny * nz;
+    int used = 1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+    }
+#else
+    (void)nthreads;
+#endif
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+    for (int64_t i = 0; i < nv; ++i) {
+        const int64_t v = idx ? idx[i] : i;
+        const int64_t x = v / (ny * nz), y = (v / nz) % ny, z = v % nz;
+        const int64_t x0 = x - sx < 0 ? 0 : x - sx, x1 = x + sx >= nx ? nx - 1 : x + sx;
+        const int64_t y0 = y - sy < 0 ? 0 : y - sy, y1 = y + sy >= ny ? ny - 1 : y + sy;
+        const int64_t z0 = z - sz < 0 ? 0 : z - sz, z1 = z + sz >= nz ? nz - 1 : z + sz;
+        double s = 0.0;
+        int64_t n = 0;
+        for (int64_t a = x0; a <= x1; ++a)
+            for (int64_t b = y0; b <= y1; ++b)
+                for (int64_t e = z0; e <= z1; ++e) {
+                    s += c[(a * ny + b) * nz + e];
+                    ++n;
+                }
+        const double m = s / (double)n;
+        double q = 0.0;
+        for (int64_t a = x0; a <= x1; ++a)
+            for (int64_t b = y0; b <= y1; ++b)
+                for (int64_t e = z0; e <= z1; ++e) {
+                    const double d = c[(a * ny + b) * nz + e] - m;
+                    q += d * d;
+                }
+        mean[i] = m;
+        stdv[i] = sqrt(q / (double)n);
+    }
+    return used;
+}

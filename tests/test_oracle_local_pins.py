@@ -1,0 +1,106 @@
+"""Pins of the oracle's per-voxel local statistics (Sec. 3.3 read as a box of
+half-widths (sx, sy, sz) around each voxel, clipped to the cube) against
+values fixed independently of it: numpy slices of the same box, closed forms
+(constant fields, a box covering the whole cube, linear ramps, zero
+half-widths, the clipped count at a corner), and the sampled path of
+local_detect against its whole-cube path."""
+import math
+
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def rng():
+    return np.random.default_rng(20260)
+
+
+@pytest.mark.parametrize("shape,half", [((6, 7, 9), (1, 2, 3)), ((5, 4, 11), (2, 0, 4)),
+                                        ((3, 8, 5), (0, 3, 1))])
+def test_brute_force_every_voxel(oracle, rng, shape, half):
+    c = rng.normal(size=shape) * 3.0 + 1.5
+    m, s = oracle.local_stats(c, half)
+    sx, sy, sz = half
+    nx, ny, nz = shape
+    for x in range(nx):
+        for y in range(ny):
+            for z in range(nz):
+                blk = c[max(0, x - sx):x + sx + 1, max(0, y - sy):y + sy + 1, max(0, z - sz):z + sz + 1]
+                assert m[x, y, z] == pytest.approx(blk.mean(), rel=1e-12, abs=1e-12)
+                assert s[x, y, z] == pytest.approx(blk.std(), rel=1e-12, abs=1e-12)
+
+
+def test_constant_field(oracle):
+    c = np.full((5, 6, 7), 2.25)
+    m, s = oracle.local_stats(c, (2, 1, 3))
+    assert np.all(m == 2.25)
+    assert np.allclose(s, 0.0, atol=1e-15)
+
+
+def test_box_covering_the_cube_gives_global_moments(oracle, rng):
+    c = rng.normal(size=(4, 5, 6))
+    m, s = oracle.local_stats(c, (4, 5, 6))
+    assert np.allclose(m, c.mean(), rtol=0, atol=1e-13)
+    assert np.allclose(s, c.std(), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_linear_ramp_interior(oracle, axis):
+    shape = (9, 10, 11)
+    half = [1, 2, 3]
+    idx = np.indices(shape)[axis].astype(np.float64)
+    c = 0.5 * idx - 1.0
+    m, s = oracle.local_stats(c, half)
+    h = half[axis]
+    # interior along the ramp axis: the box is centred, so mean = value and
+    # std = 0.5 * sqrt(h (h + 1) / 3) (uniform on 2h+1 equally spaced points)
+    sl = [slice(None)] * 3
+    sl[axis] = slice(h, shape[axis] - h)
+    sl = tuple(sl)
+    assert np.allclose(m[sl], c[sl], atol=1e-12)
+    assert np.allclose(s[sl], 0.5 * math.sqrt(h * (h + 1) / 3.0), atol=1e-12)
+
+
+def test_zero_half_width_is_the_voxel(oracle, rng):
+    c = rng.normal(size=(3, 4, 5))
+    m, s = oracle.local_stats(c, (0, 0, 0))
+    assert np.array_equal(m, c)
+    assert np.all(s == 0.0)
+
+
+def test_clipped_count_at_the_corners(oracle):
+    shape, half = (7, 8, 9), (2, 3, 1)
+    for corner in [(0, 0, 0), (6, 7, 8), (0, 7, 0), (6, 0, 8)]:
+        c = np.zeros(shape)
+        c[corner] = 1.0
+        m, _ = oracle.local_stats(c, half)
+        n = (half[0] + 1) * (half[1] + 1) * (half[2] + 1)
+        assert m[corner] == pytest.approx(1.0 / n, rel=1e-14)
+
+
+def test_indexed_voxels_match_the_full_cube(oracle, rng):
+    c = rng.normal(size=(6, 5, 8))
+    m, s = oracle.local_stats(c, (1, 2, 2))
+    flat = rng.choice(c.size, size=17, replace=False)
+    mi, si = oracle.local_stats(c, (1, 2, 2), flat)
+    assert np.array_equal(mi, m.ravel()[flat])
+    assert np.array_equal(si, s.ravel()[flat])
+
+
+def test_local_detect_sampled_path_matches_whole_cube(oracle, rng):
+    d = rng.normal(size=(20, 18, 40)).astype(np.float32)
+    d[8:12, 7:11, 15:25] += 4.0
+    bank = ((1.0, 2.0), (0.0, 3.0))
+    half = (3, 2, 6)
+    fire, sure, cv, mv, sv = oracle.local_detect(d, bank, 3.0, half, 3.0)
+    vox = np.stack([rng.integers(0, n, size=40) for n in d.shape], axis=1)
+    f2, s2, c2, m2, v2 = oracle.local_detect(d, bank, 3.0, half, 3.0, voxels=vox)
+    flat = (vox[:, 0] * d.shape[1] + vox[:, 1]) * d.shape[2] + vox[:, 2]
+    assert np.allclose(c2, cv[:, flat], rtol=0, atol=1e-12)
+    assert np.allclose(m2, mv[:, flat], rtol=0, atol=1e-12)
+    assert np.allclose(v2, sv[:, flat], rtol=0, atol=1e-12)
+    assert np.array_equal(f2, fire[flat])
+    # the selection is the stated comparison
+    thr = mv + 3.0 * sv
+    assert np.array_equal(fire.astype(bool), (cv > thr).any(axis=0))
+    assert fire.sum() > 0 and fire.sum() < fire.size

@@ -37,9 +37,22 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+# slips in the per-voxel local statistics, caught by tests/test_oracle_local_pins.py
+LOCAL_MUTANTS = {
+    "local_box_clipped_short": ("x1 = x + sx >= nx ? nx - 1 : x + sx;",
+                                "x1 = x + sx >= nx ? nx - 2 : x + sx;"),
+    "local_y_uses_z_half_width": ("y0 = y - sy < 0 ? 0 : y - sy, y1 = y + sy >= ny ? ny - 1 : y + sy;",
+                                  "y0 = y - sz < 0 ? 0 : y - sz, y1 = y + sz >= ny ? ny - 1 : y + sz;"),
+    "local_sample_std": ("stdv[i] = sqrt(q / (double)n);",
+                         "stdv[i] = sqrt(q / (double)(n > 1 ? n - 1 : 1));"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(LOCAL_MUTANTS))
 def test_pins_catch_planted_slip(tmp_path, name):
-    old, new = MUTANTS[name]
+    local = name in LOCAL_MUTANTS
+    old, new = LOCAL_MUTANTS[name] if local else MUTANTS[name]
+    pins = "test_oracle_local_pins.py" if local else "test_oracle_pins.py"
     dst = tmp_path / "oracle_mutant"
     shutil.copytree(os.path.join(ROOT, "oracle"), dst,
                     ignore=shutil.ignore_patterns("_build", "__pycache__"))
@@ -53,6 +66,6 @@ def test_pins_catch_planted_slip(tmp_path, name):
     assert cc.returncode == 0, cc.stderr
     env = dict(os.environ, SF_ORACLE_DIR=str(dst))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          os.path.join(ROOT, "tests", pins)],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"pins did not catch {name}:\n{res.stdout[-2000:]}"
