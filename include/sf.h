@@ -209,6 +209,28 @@ sf_status sf_filter_noalloc(const float *d_cube, int64_t nx, int64_t ny, int64_t
                             float sigma_xy, float sigma_z, float truncation, float *d_filtered,
                             void *stream);
 
+/* Per-voxel local statistics (Sec. 3.3: each voxel's mean and standard
+ * deviation come from a user-specified range of the filtered data around it),
+ * read as the box [x-sx, x+sx] x [y-sy, y+sy] x [z-sz, z+sz] clipped to the
+ * cube, with n the number of voxels of the clipped box; population
+ * statistics, float32 results.
+ *   d_filtered  float32 [nx][ny][nz] of the context's shape (device);
+ *   d_mean, d_std  float32 [nx][ny][nz] (device), written for every voxel.
+ * sx, sy, sz >= 0; sy <= 64 and sz <= 128 (the y-z tile of the box sums
+ * lives in shared memory); nx <= 65535.  The context keeps two float32
+ * scratch cubes for the partial sums, allocated on first use (SF_ENOMEM if
+ * that fails).  Not for batched contexts. */
+sf_status sf_local_stats(sf_ctx *ctx, const float *d_filtered, int32_t sx, int32_t sy, int32_t sz,
+                         float *d_mean, float *d_std, void *stream);
+
+/* The detect with per-voxel local statistics instead of windows: every
+ * filter of the bank (Eq. 2), the local mean / std of each filtered cube over
+ * the box above, c_f > mean_f + k std_f, OR over the bank, packed into d_mask
+ * like sf_detect's (every word written).  Same limits as sf_local_stats; the
+ * context keeps one more float32 scratch cube for the filtered values. */
+sf_status sf_local_detect(sf_ctx *ctx, const void *d_cube, int32_t sx, int32_t sy, int32_t sz,
+                          uint32_t *d_mask, void *stream);
+
 /* Wait for the work enqueued on `stream`, then report kernel-side failures:
  * SF_ETIMEOUT when a kernel's bounded wait on its own shared-memory loads
  * expired since the last call (the flag is cleared). */

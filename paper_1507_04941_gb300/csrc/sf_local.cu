@@ -1,0 +1,262 @@
+/*
+ * Per-voxel local statistics of a filtered cube (Sec. 3.3: the mean and
+ * standard deviation of each voxel come from a user-specified range of the
+ * filtered data around it), read as the box [x-sx, x+sx] x [y-sy, y+sy] x
+ * [z-sz, z+sz] clipped to the cube, with n the number of voxels of the clipped
+ * box; population statistics.  The box sums are separable, as in the paper's
+ * three directional sums:
+ *
+ *   sf_local_yz  one CTA per (x, 32-row, 64-column) tile: the tile with its y
+ *                and z halo is staged in shared memory, shifted by one of its
+ *                values s_t (entries outside the cube are 0: they are not in
+ *                any box); box sums of (c - s_t) and (c - s_t)^2 along z and
+ *                then along y are formed as running sums restarted every 16
+ *                outputs (direct sums per output for half-widths up to 16),
+ *                and each voxel's y-z box mean A and second central
+ *                moment M = sum (c - A)^2 are written as two float32 cubes;
+ *   sf_local_x   one thread per (y, z), marching along x with compensated
+ *                (Kahan) running sums over the x box of (A - s), (A - s)^2
+ *                and M, restarted every 32 planes from a direct sum with s
+ *                the segment's first A; the box statistics then
+ *                follow from the parallel-axis rule
+ *                  mean = s + sum(A - s)/X,
+ *                  M2   = sum M + n_yz (sum (A - s)^2 - (sum (A - s))^2 / X)
+ *                (X planes of n_yz voxels each), var = M2 / (X n_yz); either
+ *                the mean / std cubes are written or the selection
+ *                c > mean + k std is packed into the mask words by a warp
+ *                ballot (one warp = 32 consecutive z of one row), OR-ed into
+ *                the words already there when the mask accumulates a bank.
+ * Shifting by a value of the data keeps the second moments from cancelling
+ * when the local mean is large against the local spread.
+ */
+#include <cuda_runtime.h>
+
+namespace {
+
+typedef long long i64;
+
+constexpr int kYT = 32;          /* tile rows (y) */
+constexpr int kZT = 64;          /* tile columns (z) */
+constexpr int kSeg = 16;         /* outputs per running-sum segment */
+constexpr int kDirect = 16;      /* half-widths up to this: direct sums per output */
+constexpr int kYZThreads = 256;
+constexpr int kXThreads = 128;
+constexpr int kXSeg = 32;        /* x planes per re-anchored segment */
+
+__host__ __device__ inline int stage_cols(int sz) { return (kZT + 2 * sz) | 1; }   /* odd: fewer bank conflicts */
+
+__device__ __forceinline__ i64 clipped(i64 v, int h, i64 n)
+{
+    const i64 lo = v - h < 0 ? 0 : v - h, hi = v + h >= n ? n - 1 : v + h;
+    return hi - lo + 1;
+}
+
+__global__ void __launch_bounds__(kYZThreads) sf_local_yz(const float *__restrict__ c, float *__restrict__ A,
+                                                        float *__restrict__ M, i64 nx, i64 ny, i64 nz, int sy,
+                                                        int sz)
+{
+    extern __shared__ float sm[];
+    const int rows = kYT + 2 * sy, cols = stage_cols(sz);
+    float *T = sm;                       /* [rows][cols] staged c - s_t */
+    float *Pz = T + rows * cols;         /* [rows][kZT] z box sums of c - s_t */
+    float *Qz = Pz + rows * kZT;         /* [rows][kZT] z box sums of (c - s_t)^2 */
+    const i64 x = blockIdx.z, y0 = (i64)blockIdx.y * kYT, z0 = (i64)blockIdx.x * kZT;
+    (void)nx;
+    /* the tile's shift: the value nearest its centre inside the cube */
+    const i64 yc = min(ny - 1, y0 + kYT / 2), zc = min(nz - 1, z0 + kZT / 2);
+    const float st = c[(x * ny + yc) * nz + zc];
+    for (int i = threadIdx.x; i < rows * cols; i += kYZThreads) {
+        const int r = i / cols, q = i - r * cols;
+        const i64 y = y0 - sy + r, z = z0 - sz + q;
+        T[i] = (y >= 0 && y < ny && z >= 0 && z < nz && q < kZT + 2 * sz) ? c[(x * ny + y) * nz + z] - st : 0.f;
+    }
+    __syncthreads();
+    /* z: output column j of staged row r sums staged columns j .. j + 2 sz */
+    constexpr int nseg_z = kZT / kSeg;
+    for (int task = threadIdx.x; task < rows * nseg_z; task += kYZThreads) {
+        const int r = task / nseg_z, j0 = (task - r * nseg_z) * kSeg;
+        const float *row = T + r * cols;
+        float p = 0.f, q = 0.f;
+        for (int o = 0; o <= 2 * sz; ++o) {
+            const float v = row[j0 + o];
+            p += v;
+            q = fmaf(v, v, q);
+        }
+        Pz[r * kZT + j0] = p;
+        Qz[r * kZT + j0] = q;
+        for (int j = j0 + 1; j < j0 + kSeg; ++j) {
+            if (sz <= kDirect) {
+                /* short boxes: a direct sum per output (exact for one voxel) */
+                p = 0.f;
+                q = 0.f;
+                for (int o = 0; o <= 2 * sz; ++o) {
+                    const float v = row[j + o];
+                    p += v;
+                    q = fmaf(v, v, q);
+                }
+            } else {
+                const float vin = row[j + 2 * sz], vout = row[j - 1];
+                p += vin - vout;
+                q = fmaf(-vout, vout, fmaf(vin, vin, q));
+            }
+            Pz[r * kZT + j] = p;
+            Qz[r * kZT + j] = q;
+        }
+    }
+    __syncthreads();
+    /* y: output row i sums staged rows i .. i + 2 sy */
+    constexpr int nseg_y = kYT / kSeg;
+    for (int task = threadIdx.x; task < kZT * nseg_y; task += kYZThreads) {
+        const int j = task % kZT, i0 = (task / kZT) * kSeg;
+        const i64 z = z0 + j;
+        float p = 0.f, q = 0.f;
+        for (int o = 0; o <= 2 * sy; ++o) {
+            p += Pz[(i0 + o) * kZT + j];
+            q += Qz[(i0 + o) * kZT + j];
+        }
+        for (int i = i0; i < i0 + kSeg; ++i) {
+            if (i > i0 && sy <= kDirect) {
+                p = 0.f;
+                q = 0.f;
+                for (int o = 0; o <= 2 * sy; ++o) {
+                    p += Pz[(i + o) * kZT + j];
+                    q += Qz[(i + o) * kZT + j];
+                }
+            } else if (i > i0) {
+                p += Pz[(i + 2 * sy) * kZT + j] - Pz[(i - 1) * kZT + j];
+                q += Qz[(i + 2 * sy) * kZT + j] - Qz[(i - 1) * kZT + j];
+            }
+            const i64 y = y0 + i;
+            if (y < ny && z < nz) {
+                const float n = (float)(clipped(y, sy, ny) * clipped(z, sz, nz));
+                A[(x * ny + y) * nz + z] = st + p / n;
+                /* a rounded product (no contraction into an fma): for a
+                 * one-voxel box q and p*p round alike and M is exactly 0 */
+                M[(x * ny + y) * nz + z] = fmaxf(q - __fmul_rn(p, p / n), 0.f);
+            }
+        }
+    }
+}
+
+/* compensated running sum */
+struct Kahan {
+    float s = 0.f, comp = 0.f;
+    __device__ __forceinline__ void add(float v)
+    {
+        const float y = v - comp;
+        const float t = s + y;
+        comp = (t - s) - y;
+        s = t;
+    }
+};
+
+/* mode 0: mean / std cubes; 1: mask words set; 2: mask words OR-ed */
+__global__ void __launch_bounds__(kXThreads) sf_local_x(const float *__restrict__ c, const float *__restrict__ A,
+                                                      const float *__restrict__ M, i64 nx, i64 ny, i64 nz, i64 nw32,
+                                                      int sx, int sy, int sz, float k, float *__restrict__ mean,
+                                                      float *__restrict__ stdv, unsigned int *__restrict__ mask,
+                                                      int mode)
+{
+    const i64 lane = (i64)blockIdx.x * kXThreads + threadIdx.x;
+    const i64 per_row = nw32 * 32;
+    const i64 y = lane / per_row;
+    if (y >= ny) return;   /* whole warps: a row holds a multiple of 32 lanes */
+    const i64 zw = (lane - y * per_row) >> 5;
+    const int bit = (int)(lane & 31);
+    const i64 z = zw * 32 + bit;
+    const bool valid = z < nz;
+    const i64 plane = ny * nz, off = y * nz + (valid ? z : 0);
+    const float nyz = (float)(clipped(y, sy, ny) * clipped(z, sz, nz));
+    /* box statistics of plane x -> selection or stats output */
+    auto emit = [&](i64 x, float mu, float m2, float X) {
+        const float sd = sqrtf(m2 / (X * nyz));
+        if (mode == 0) {
+            if (valid) {
+                mean[x * plane + off] = mu;
+                stdv[x * plane + off] = sd;
+            }
+        } else {
+            const bool fire = valid && c[x * plane + off] > fmaf(k, sd, mu);
+            const unsigned int bits = __ballot_sync(0xffffffffu, fire);
+            if (bit == 0) {
+                unsigned int *w = mask + (x * ny + y) * nw32 + zw;
+                *w = mode == 2 ? (*w | bits) : bits;
+            }
+        }
+    };
+    if (sx == 0) {
+        /* the x box is the plane itself */
+        for (i64 x = 0; x < nx; ++x) {
+            const float a = valid ? A[x * plane + off] : 0.f, m = valid ? M[x * plane + off] : 0.f;
+            emit(x, a, m, 1.f);
+        }
+        return;
+    }
+    /* segments of kXSeg planes: the sums restart from a direct sum over the
+     * box of the segment's first plane, shifted by that plane's A, so the
+     * running updates neither drift nor cancel */
+    for (i64 x0 = 0; x0 < nx; x0 += kXSeg) {
+        const float s = valid ? A[x0 * plane + off] : 0.f;
+        Kahan sa, sb, sm;   /* sums over the x box of A - s, (A - s)^2, M */
+        if (valid) {
+            const i64 lo = x0 - sx < 0 ? 0 : x0 - sx, hi = x0 + sx >= nx ? nx - 1 : x0 + sx;
+            for (i64 xi = lo; xi <= hi; ++xi) {
+                const float d = A[xi * plane + off] - s;
+                sa.add(d);
+                sb.add(d * d);
+                sm.add(M[xi * plane + off]);
+            }
+        }
+        const i64 x1 = x0 + kXSeg < nx ? x0 + kXSeg : nx;
+        for (i64 x = x0; x < x1; ++x) {
+            if (valid && x > x0) {
+                const i64 xin = x + sx, xout = x - sx - 1;
+                if (xin < nx) {
+                    const float d = A[xin * plane + off] - s;
+                    sa.add(d);
+                    sb.add(d * d);
+                    sm.add(M[xin * plane + off]);
+                }
+                if (xout >= 0) {
+                    const float d = A[xout * plane + off] - s;
+                    sa.add(-d);
+                    sb.add(-(d * d));
+                    sm.add(-M[xout * plane + off]);
+                }
+            }
+            const float X = (float)clipped(x, sx, nx);
+            const float da = sa.s / X;
+            emit(x, s + da, sm.s + nyz * fmaxf(sb.s - __fmul_rn(sa.s, da), 0.f), X);
+        }
+    }
+}
+
+}  // namespace
+
+/* shared memory of sf_local_yz for half-widths (sy, sz) */
+size_t sf_local_yz_smem(int sy, int sz)
+{
+    const size_t rows = (size_t)kYT + 2 * (size_t)sy;
+    return sizeof(float) * rows * ((size_t)stage_cols(sz) + 2 * kZT);
+}
+
+cudaError_t sf_launch_local_yz(const float *c, float *A, float *M, long long nx, long long ny, long long nz, int sy,
+                               int sz, cudaStream_t st)
+{
+    const size_t smem = sf_local_yz_smem(sy, sz);
+    cudaError_t e = cudaFuncSetAttribute(sf_local_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)((nz + kZT - 1) / kZT), (unsigned)((ny + kYT - 1) / kYT), (unsigned)nx);
+    sf_local_yz<<<grid, kYZThreads, smem, st>>>(c, A, M, nx, ny, nz, sy, sz);
+    return cudaGetLastError();
+}
+
+cudaError_t sf_launch_local_x(const float *c, const float *A, const float *M, long long nx, long long ny,
+                              long long nz, long long nw32, int sx, int sy, int sz, float k, float *mean,
+                              float *stdv, unsigned int *mask, int mode, cudaStream_t st)
+{
+    const long long lanes = ny * nw32 * 32;
+    const unsigned grid = (unsigned)((lanes + kXThreads - 1) / kXThreads);
+    sf_local_x<<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask, mode);
+    return cudaGetLastError();
+}

@@ -43,6 +43,12 @@ extern "C" const char *sf_embedded_abi_source;      /* sf_kernel_abi.h (generate
 cudaError_t sf_launch_stats(const float *c, long long nx, long long ny, long long nz, int wx, int wy,
                             int wz, int nwx, int nwy, int nwz, float *mean, float *stdv,
                             cudaStream_t st);
+size_t sf_local_yz_smem(int sy, int sz);
+cudaError_t sf_launch_local_yz(const float *c, float *P, float *Q, long long nx, long long ny, long long nz, int sy,
+                               int sz, cudaStream_t st);
+cudaError_t sf_launch_local_x(const float *c, const float *P, const float *Q, long long nx, long long ny,
+                              long long nz, long long nw32, int sx, int sy, int sz, float k, float *mean,
+                              float *stdv, unsigned int *mask, int mode, cudaStream_t st);
 cudaError_t sf_launch_threshold(const float *c, long long nx, long long ny, long long nz, int wx,
                                 int wy, int wz, int nwy, int nwz, const float *mean,
                                 const float *stdv, float k, unsigned int *mask, int accumulate,
@@ -241,6 +247,7 @@ struct sf_ctx {
     unsigned int *host_mask = nullptr;
     cudaStream_t hcopy[2] = {nullptr, nullptr}, hback = nullptr;
     cudaStream_t hcomp[2] = {nullptr, nullptr};   /* compute streams of the host pipeline */
+    float *lscratch = nullptr;        /* local statistics: filtered cube, P, Q */
     std::vector<cudaEvent_t> hev;
 
     /* stage timing: pairs of events per recorded stage instance */
@@ -1386,6 +1393,7 @@ sf_status sf_destroy(sf_ctx *c)
     cudaFree(c->err_flag);
     for (cudaStream_t x : c->hcomp)
         if (x) cudaStreamDestroy(x);
+    cudaFree(c->lscratch);
     for (cudaStream_t x : c->hcopy)
         if (x) cudaStreamDestroy(x);
     if (c->hback) cudaStreamDestroy(c->hback);
@@ -1825,6 +1833,75 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
     cudaEventRecord(c->hev[2 * K + 1], c->hback);
     cudaStreamWaitEvent(st, c->hev[2 * K + 1], 0);
     return sf_synchronize(c, stream);
+}
+
+namespace {
+sf_status local_check(sf_ctx *c, int sx, int sy, int sz)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (c->batch) return fail(c, SF_EINVAL, "batched context: local statistics take one cube");
+    if (sx < 0 || sy < 0 || sz < 0) return fail(c, SF_EINVAL, "box half-widths must be >= 0");
+    if (sy > 64 || sz > 128) return fail(c, SF_EINVAL, "box half-widths sy <= 64 and sz <= 128");
+    if (c->cfg.nx > 65535) return fail(c, SF_EINVAL, "local statistics take nx <= 65535");
+    return SF_OK;
+}
+
+/* filtered cube (if `filtered`), P and Q scratch of the local statistics */
+sf_status local_scratch(sf_ctx *c)
+{
+    if (c->lscratch) return SF_OK;
+    const size_t cube = align_up((size_t)c->nvox * sizeof(float), 256);
+    const cudaError_t e = cudaMalloc((void **)&c->lscratch, 3 * cube);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->lscratch = nullptr;
+        return fail(c, SF_ENOMEM, "local-statistics scratch (%zu bytes)", 3 * cube);
+    }
+    return SF_OK;
+}
+}  // namespace
+
+sf_status sf_local_stats(sf_ctx *c, const float *d_filtered, int32_t sx, int32_t sy, int32_t sz, float *d_mean,
+                         float *d_std, void *stream)
+{
+    sf_status s = local_check(c, sx, sy, sz);
+    if (s != SF_OK) return s;
+    if (!d_filtered || !d_mean || !d_std) return fail(c, SF_EINVAL, "NULL buffer");
+    DeviceGuard dg(c->device);
+    if ((s = local_scratch(c)) != SF_OK) return s;
+    const sf_config &g = c->cfg;
+    const size_t cube = align_up((size_t)c->nvox * sizeof(float), 256) / sizeof(float);
+    float *P = c->lscratch + cube, *Q = c->lscratch + 2 * cube;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = sf_launch_local_yz(d_filtered, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
+    if (e == cudaSuccess)
+        e = sf_launch_local_x(d_filtered, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_mean, d_std,
+                              nullptr, 0, st);
+    return e == cudaSuccess ? SF_OK : cuda_fail(c, e, "local statistics launch");
+}
+
+sf_status sf_local_detect(sf_ctx *c, const void *d_cube, int32_t sx, int32_t sy, int32_t sz, uint32_t *d_mask,
+                          void *stream)
+{
+    sf_status s = local_check(c, sx, sy, sz);
+    if (s != SF_OK) return s;
+    if (!d_cube || !d_mask) return fail(c, SF_EINVAL, "NULL buffer");
+    DeviceGuard dg(c->device);
+    if ((s = local_scratch(c)) != SF_OK) return s;
+    const sf_config &g = c->cfg;
+    const size_t cube = align_up((size_t)c->nvox * sizeof(float), 256) / sizeof(float);
+    float *F = c->lscratch, *P = c->lscratch + cube, *Q = c->lscratch + 2 * cube;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int f = 0; f < (int)c->filt.size(); ++f) {
+        if ((s = sf_filter(c, d_cube, f, F, stream)) != SF_OK) return s;
+        cudaError_t e = sf_launch_local_yz(F, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
+        if (e == cudaSuccess)
+            e = sf_launch_local_x(F, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, nullptr, nullptr, d_mask,
+                                  f == 0 ? 1 : 2, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "local detect launch");
+    }
+    return SF_OK;
 }
 
 sf_status sf_synchronize(sf_ctx *c, void *stream)

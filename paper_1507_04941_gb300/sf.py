@@ -75,6 +75,8 @@ SIGNATURES = {
     "sf_server_destroy": (_i32, [_vp]),
     "sf_filter_noalloc": (_i32, [_vp, _i64, _i64, _i64, ctypes.c_float, ctypes.c_float,
                                  ctypes.c_float, _vp, _vp]),
+    "sf_local_stats": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
+    "sf_local_detect": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "sf_profile_enable": (_i32, [_vp, _i32]),
     "sf_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
 }
@@ -243,6 +245,35 @@ class SourceFinder:
         _check(lib().sf_detect(self._h, _ptr(cube), _ptr(mask), _ptr(mean), _ptr(std),
                                _stream(self.device)), self._h)
         return (mask, mean, std) if stats else mask
+
+    def local_stats(self, filtered, half, mean=None, std=None):
+        """Per-voxel mean and std of a filtered cube over the box of
+        half-widths half = (sx, sy, sz) clipped to the cube (float32, the
+        cube's shape)."""
+        import torch
+        self._check_f32(filtered, self.shape, "filtered")
+        if mean is None:
+            mean = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        if std is None:
+            std = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        self._check_f32(mean, self.shape, "mean")
+        self._check_f32(std, self.shape, "std")
+        sx, sy, sz = (int(v) for v in half)
+        _check(lib().sf_local_stats(self._h, _ptr(filtered), sx, sy, sz, _ptr(mean), _ptr(std),
+                                    _stream(self.device)), self._h)
+        return mean, std
+
+    def local_detect(self, cube, half, mask=None):
+        """Packed mask of the detect with per-voxel local statistics over the
+        box of half-widths half = (sx, sy, sz)."""
+        import torch
+        self._check_cube(cube)
+        if mask is None:
+            mask = torch.empty(self.mask_shape, dtype=torch.int32, device=self.device)
+        sx, sy, sz = (int(v) for v in half)
+        _check(lib().sf_local_detect(self._h, _ptr(cube), sx, sy, sz, _ptr(mask),
+                                     _stream(self.device)), self._h)
+        return mask
 
     def detect_host(self, cube_host, mask_host=None):
         """Host tensors in and out (pinned memory makes the copies DMA)."""

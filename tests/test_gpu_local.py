@@ -1,0 +1,137 @@
+"""GPU parity of the per-voxel local statistics form (Sec. 3.3 read per voxel:
+the box [x-sx, x+sx] x [y-sy, y+sy] x [z-sz, z+sz] clipped to the cube)
+against the FP64 oracle.
+
+Tolerances as for the window path:
+  local stats  |d mean|, |d std| <= 1e-5 * max(std, |mean|);
+  masks        bit-exact outside the guard band |c_f - T_f| < 1e-4 * std_f.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+BANK3 = ((0.0, 2.0), (1.5, 6.0), (3.0, 2.0))
+
+
+@pytest.fixture(scope="module")
+def dev():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1507_04941_gb300 import build
+    build.build()
+    return torch.device("cuda", 0)
+
+
+def _cube(shape, seed, n_sources=8, peak=(1.0, 5.0)):
+    from paper_1507_04941_gb300 import synth
+    return synth.make_cube(shape, seed, n_sources, peak, None)
+
+
+def _assert_stats(gm, gs, rm, rs, rel=1e-5, what=""):
+    scale = np.maximum(rs, np.abs(rm))
+    dm = np.abs(gm.astype(np.float64) - rm)
+    ds = np.abs(gs.astype(np.float64) - rs)
+    assert (dm <= rel * scale).all(), f"{what}: mean off by {float((dm / scale).max()):.3g} x scale"
+    assert (ds <= rel * scale).all(), f"{what}: std off by {float((ds / scale).max()):.3g} x scale"
+
+
+@pytest.mark.parametrize("shape,half", [((70, 45, 150), (4, 3, 9)),     # several tiles, ragged
+                                        ((9, 7, 5), (2, 3, 1)),          # smaller than one tile
+                                        ((20, 80, 200), (3, 40, 100)),   # big y/z box: deep halo
+                                        ((12, 33, 65), (0, 0, 0)),       # the voxel itself
+                                        ((6, 40, 70), (9, 50, 90))])     # box wider than the cube
+def test_local_stats_parity(dev, oracle, shape, half):
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder
+    cube = _cube(shape, seed=41)
+    with SourceFinder(shape, ((1.5, 2.0),), 3.0, (16, 16, 32), device=dev) as sf:
+        c = sf.filter(cube.to(dev), 0)
+        c += 3.0   # an offset makes the variance cancellation visible
+        mean, std = sf.local_stats(c, half)
+        torch.cuda.synchronize(dev)
+        rm, rs = oracle.local_stats(c.cpu().numpy().astype(np.float64), half)
+    _assert_stats(mean.cpu().numpy(), std.cpu().numpy(), rm, rs, what=f"{shape} {half}")
+
+
+@pytest.mark.parametrize("shape,half,k", [((40, 36, 100), (4, 4, 8), 3.0),
+                                          ((17, 50, 31), (2, 6, 3), 2.5),   # nz < 32, ragged
+                                          ((33, 20, 96), (5, 2, 12), 3.0)])
+def test_local_detect_parity(dev, oracle, shape, half, k):
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder, words_to_bits
+    cube = _cube(shape, seed=42, n_sources=10, peak=(1.0, 6.0))
+    with SourceFinder(shape, BANK3, 3.0, (16, 16, 32), k=k, device=dev) as sf:
+        mask = sf.local_detect(cube.to(dev), half)
+        torch.cuda.synchronize(dev)
+        got = words_to_bits(mask.cpu().numpy(), shape[2])
+        words = mask.cpu().numpy().view(np.uint32)
+    fire, sure, *_ = oracle.local_detect(cube.numpy(), BANK3, 3.0, half, k)
+    want = fire.reshape(shape).astype(bool)
+    sure = sure.reshape(shape).astype(bool)
+    assert want.sum() > 0
+    diff = (got != want) & sure
+    assert not diff.any(), f"{int(diff.sum())} certain mask bits differ"
+    nz = shape[2]
+    if nz % 32:
+        assert not (words[:, :, -1] >> np.uint32(nz % 32)).any(), "tail bits must be zero"
+
+
+def test_local_detect_repeat_is_identical(dev):
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder
+    shape = (30, 40, 64)
+    cube = _cube(shape, seed=43).to(dev)
+    with SourceFinder(shape, BANK3, 3.0, (16, 16, 32), k=3.0, device=dev) as sf:
+        a = sf.local_detect(cube, (3, 3, 6)).clone()
+        b = sf.local_detect(cube, (3, 3, 6))
+        torch.cuda.synchronize(dev)
+    assert torch.equal(a, b)
+
+
+def test_local_stats_full_tile_sampled(dev, oracle):
+    """The tile workload's cube and bank at full size with the box half-widths
+    of its windows (16, 16, 32): sampled voxels against the oracle."""
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder, synth
+    w = synth.TILE
+    cube = synth.make(w, device=dev)
+    half = (16, 16, 32)
+    with SourceFinder(w.shape, w.bank, w.truncation, w.window, w.k, device=dev) as sf:
+        c = sf.filter(cube, 3)
+        mean, std = sf.local_stats(c, half)
+        torch.cuda.synchronize(dev)
+        rng = np.random.default_rng(44)
+        n = int(np.prod(w.shape))
+        idx = np.concatenate([rng.integers(0, n, size=300),
+                              np.array([0, n - 1, w.shape[2] - 1, (w.shape[0] - 1) * w.shape[1] * w.shape[2]])])
+        cn = c.cpu().numpy().astype(np.float64)
+        rm, rs = oracle.local_stats(cn, half, idx)
+        gm = mean.cpu().numpy().ravel()[idx]
+        gs = std.cpu().numpy().ravel()[idx]
+    _assert_stats(gm, gs, rm, rs, what="tile sampled")
+
+
+def test_local_detect_full_tile_sampled(dev, oracle):
+    """sf_local_detect on the full tile workload: mask bits at sampled voxels
+    (half near the brightest voxels) against the oracle's per-voxel decision."""
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder, synth, words_to_bits
+    w = synth.TILE
+    cube = synth.make(w, device=dev)
+    half = (16, 16, 32)
+    with SourceFinder(w.shape, w.bank, w.truncation, w.window, w.k, device=dev) as sf:
+        mask = sf.local_detect(cube, half)
+        torch.cuda.synchronize(dev)
+        bits = words_to_bits(mask.cpu().numpy(), w.shape[2])
+    d = cube.cpu().numpy()
+    rng = np.random.default_rng(45)
+    bright = np.argsort(d.ravel())[-2000:]
+    pick = np.concatenate([rng.choice(bright, 24, replace=False),
+                           rng.integers(0, d.size, size=24)])
+    vox = np.stack(np.unravel_index(pick, w.shape), axis=1)
+    fire, sure, *_ = oracle.local_detect(d, w.bank, w.truncation, half, w.k, voxels=vox)
+    got = bits.ravel()[pick]
+    diff = (got != fire.astype(bool)) & sure.astype(bool)
+    assert not diff.any(), f"{int(diff.sum())} of {len(pick)} sampled certain bits differ"
