@@ -309,6 +309,37 @@ def run_ours(args):
             sq.close()
             del cq
 
+    # sliding-statistics form: per-voxel local mean/std over the box of the
+    # window's half extents (Sec. 3.3 read per voxel), same cube and bank
+    local = None
+    if not args.no_local and storage == "f32":
+        half = tuple(int(v) // 2 for v in w.window)
+        lmask = torch.empty(sf.mask_shape, dtype=torch.int32, device=dev)
+        for _ in range(3):
+            sf.local_detect(cube, half, lmask)
+        torch.cuda.synchronize(dev)
+        n_l = max(5, min(args.steps // 10, 30))
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for _ in range(n_l):
+            sf.local_detect(cube, half, lmask)
+        l1.record(stream)
+        torch.cuda.synchronize(dev)
+        msl = l0.elapsed_time(l1) / n_l
+        nf = len(w.bank)
+        n_xy = sum(1 for b in w.bank if b[0] > 0)
+        # composed traffic per voxel: filter (x pass 8 B where sigma_xy > 0, y/z
+        # pass 8 B), y-z box sums (4 B in, 8 B out), x box + selection (8 + 4 B
+        # in, mask words: written by the first filter, read and written after)
+        lbytes = nvox * (8 * n_xy + 8 * nf + 12 * nf + 12 * nf + 0.125 + 0.25 * (nf - 1))
+        local = {"value": units / (msl * 1e-3), "unit": UNIT, "ms_per_step": msl, "steps": n_l,
+                 "box_half_widths": list(half),
+                 "path": "per filter: filter (x pass + y/z pass), y-z box sums, x box + selection",
+                 "hbm_view": {"bytes_per_step": lbytes, "achieved_gbs": lbytes / (msl * 1e-3) / 1e9,
+                              "peak_gbs": hbm_peak,
+                              "frac": lbytes / (msl * 1e-3) / 1e9 / hbm_peak}}
+
     # batched form: 64 uneven subcubes in one persistent launch (CUDA graph)
     batch = None
     if not args.no_batch and world == 1 and storage == "f32":
@@ -358,6 +389,7 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({nvox * sbytes / 2**20:.0f} MiB cube, "
                              "129 MB L2)"},
             "roofline": roof, "kernels": other, "clocks": clocks, "storage_forms": forms,
+            "local_stats_form": local,
             "serving": serving,
             "path": "persistent (x-pass + windows in one launch)" if persistent else
                     "x pass + window kernel", "autotune": tune_rep, "batched_form": batch,
@@ -593,6 +625,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-subcube form")
+    ap.add_argument("--no-local", action="store_true", help="skip the sliding-statistics form")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving form")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per offered-load level of the serving form")

@@ -14,9 +14,9 @@
  *                outputs (direct sums per output for half-widths up to 16),
  *                and each voxel's y-z box mean A and second central
  *                moment M = sum (c - A)^2 are written as two float32 cubes;
- *   sf_local_x   one thread per (y, z), marching along x with compensated
- *                (Kahan) running sums over the x box of (A - s), (A - s)^2
- *                and M, restarted every 32 planes from a direct sum with s
+ *   sf_local_x   one thread per (y, z) and 32-plane x segment, marching along
+ *                x with compensated (Kahan) running sums over the x box of
+ *                (A - s), (A - s)^2 and M, started from a direct sum with s
  *                the segment's first A; the box statistics then
  *                follow from the parallel-axis rule
  *                  mean = s + sum(A - s)/X,
@@ -37,8 +37,10 @@ typedef long long i64;
 
 constexpr int kYT = 32;          /* tile rows (y) */
 constexpr int kZT = 64;          /* tile columns (z) */
+constexpr int kPZ = kZT + 1;     /* row stride of the z sums (odd: conflict-free) */
 constexpr int kSeg = 16;         /* outputs per running-sum segment */
-constexpr int kDirect = 16;      /* half-widths up to this: direct sums per output */
+constexpr int kDirect = 2;       /* half-widths up to this: direct sums per output */
+constexpr int kYSeg = 8;         /* rows per y running-sum segment */
 constexpr int kYZThreads = 256;
 constexpr int kXThreads = 128;
 constexpr int kXSeg = 32;        /* x planes per re-anchored segment */
@@ -58,32 +60,54 @@ __global__ void __launch_bounds__(kYZThreads) sf_local_yz(const float *__restric
     extern __shared__ float sm[];
     const int rows = kYT + 2 * sy, cols = stage_cols(sz);
     float *T = sm;                       /* [rows][cols] staged c - s_t */
-    float *Pz = T + rows * cols;         /* [rows][kZT] z box sums of c - s_t */
-    float *Qz = Pz + rows * kZT;         /* [rows][kZT] z box sums of (c - s_t)^2 */
+    float *Pz = T + rows * cols;         /* [rows][kPZ] z box sums of c - s_t */
+    float *Qz = Pz + rows * kPZ;         /* [rows][kPZ] z box sums of (c - s_t)^2 */
     const i64 x = blockIdx.z, y0 = (i64)blockIdx.y * kYT, z0 = (i64)blockIdx.x * kZT;
     (void)nx;
     /* the tile's shift: the value nearest its centre inside the cube */
     const i64 yc = min(ny - 1, y0 + kYT / 2), zc = min(nz - 1, z0 + kZT / 2);
     const float st = c[(x * ny + yc) * nz + zc];
-    for (int i = threadIdx.x; i < rows * cols; i += kYZThreads) {
-        const int r = i / cols, q = i - r * cols;
-        const i64 y = y0 - sy + r, z = z0 - sz + q;
-        T[i] = (y >= 0 && y < ny && z >= 0 && z < nz && q < kZT + 2 * sz) ? c[(x * ny + y) * nz + z] - st : 0.f;
+    /* staging by cp.async (4 bytes, zero fill outside the cube), then each
+     * thread shifts the elements its own copies wrote */
+    const unsigned int tbase = (unsigned int)__cvta_generic_to_shared(T);
+    for (int r = threadIdx.x >> 5; r < rows; r += kYZThreads / 32) {
+        const i64 y = y0 - sy + r;
+        const bool yin = y >= 0 && y < ny;
+        const float *src = c + (x * ny + (yin ? y : 0)) * nz;
+        for (int q = threadIdx.x & 31; q < cols; q += 32) {
+            const i64 z = z0 - sz + q;
+            const bool in = yin && z >= 0 && z < nz && q < kZT + 2 * sz;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(tbase + 4u * (unsigned)(r * cols + q)),
+                         "l"(in ? src + z : c), "r"(in ? 4 : 0)
+                         : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+    for (int r = threadIdx.x >> 5; r < rows; r += kYZThreads / 32) {
+        const i64 y = y0 - sy + r;
+        const bool yin = y >= 0 && y < ny;
+        for (int q = threadIdx.x & 31; q < cols; q += 32) {
+            const i64 z = z0 - sz + q;
+            if (yin && z >= 0 && z < nz && q < kZT + 2 * sz) T[r * cols + q] -= st;
+        }
     }
     __syncthreads();
     /* z: output column j of staged row r sums staged columns j .. j + 2 sz */
     constexpr int nseg_z = kZT / kSeg;
     for (int task = threadIdx.x; task < rows * nseg_z; task += kYZThreads) {
-        const int r = task / nseg_z, j0 = (task - r * nseg_z) * kSeg;
+        /* consecutive lanes take consecutive rows: with an odd row stride the
+         * shared loads of a warp hit 32 different banks */
+        const int seg = task / rows, r = task - seg * rows, j0 = seg * kSeg;
         const float *row = T + r * cols;
         float p = 0.f, q = 0.f;
+#pragma unroll 4
         for (int o = 0; o <= 2 * sz; ++o) {
             const float v = row[j0 + o];
             p += v;
             q = fmaf(v, v, q);
         }
-        Pz[r * kZT + j0] = p;
-        Qz[r * kZT + j0] = q;
+        Pz[r * kPZ + j0] = p;
+        Qz[r * kPZ + j0] = q;
         for (int j = j0 + 1; j < j0 + kSeg; ++j) {
             if (sz <= kDirect) {
                 /* short boxes: a direct sum per output (exact for one voxel) */
@@ -99,32 +123,33 @@ __global__ void __launch_bounds__(kYZThreads) sf_local_yz(const float *__restric
                 p += vin - vout;
                 q = fmaf(-vout, vout, fmaf(vin, vin, q));
             }
-            Pz[r * kZT + j] = p;
-            Qz[r * kZT + j] = q;
+            Pz[r * kPZ + j] = p;
+            Qz[r * kPZ + j] = q;
         }
     }
     __syncthreads();
     /* y: output row i sums staged rows i .. i + 2 sy */
-    constexpr int nseg_y = kYT / kSeg;
+    constexpr int nseg_y = kYT / kYSeg;
     for (int task = threadIdx.x; task < kZT * nseg_y; task += kYZThreads) {
-        const int j = task % kZT, i0 = (task / kZT) * kSeg;
+        const int j = task % kZT, i0 = (task / kZT) * kYSeg;
         const i64 z = z0 + j;
         float p = 0.f, q = 0.f;
+#pragma unroll 4
         for (int o = 0; o <= 2 * sy; ++o) {
-            p += Pz[(i0 + o) * kZT + j];
-            q += Qz[(i0 + o) * kZT + j];
+            p += Pz[(i0 + o) * kPZ + j];
+            q += Qz[(i0 + o) * kPZ + j];
         }
-        for (int i = i0; i < i0 + kSeg; ++i) {
+        for (int i = i0; i < i0 + kYSeg; ++i) {
             if (i > i0 && sy <= kDirect) {
                 p = 0.f;
                 q = 0.f;
                 for (int o = 0; o <= 2 * sy; ++o) {
-                    p += Pz[(i + o) * kZT + j];
-                    q += Qz[(i + o) * kZT + j];
+                    p += Pz[(i + o) * kPZ + j];
+                    q += Qz[(i + o) * kPZ + j];
                 }
             } else if (i > i0) {
-                p += Pz[(i + 2 * sy) * kZT + j] - Pz[(i - 1) * kZT + j];
-                q += Qz[(i + 2 * sy) * kZT + j] - Qz[(i - 1) * kZT + j];
+                p += Pz[(i + 2 * sy) * kPZ + j] - Pz[(i - 1) * kPZ + j];
+                q += Qz[(i + 2 * sy) * kPZ + j] - Qz[(i - 1) * kPZ + j];
             }
             const i64 y = y0 + i;
             if (y < ny && z < nz) {
@@ -150,83 +175,91 @@ struct Kahan {
     }
 };
 
-/* mode 0: mean / std cubes; 1: mask words set; 2: mask words OR-ed */
-__global__ void __launch_bounds__(kXThreads) sf_local_x(const float *__restrict__ c, const float *__restrict__ A,
-                                                      const float *__restrict__ M, i64 nx, i64 ny, i64 nz, i64 nw32,
-                                                      int sx, int sy, int sz, float k, float *__restrict__ mean,
-                                                      float *__restrict__ stdv, unsigned int *__restrict__ mask,
-                                                      int mode)
+/* MODE 0: mean / std cubes; 1: mask words set; 2: mask words OR-ed */
+template <int MODE>
+__global__ void __launch_bounds__(kXThreads, 12)
+    sf_local_x(const float *__restrict__ c, const float *__restrict__ A, const float *__restrict__ M, i64 nx,
+               i64 ny, i64 nz, i64 nw32, int sx, int sy, int sz, float k, float *__restrict__ mean,
+               float *__restrict__ stdv, unsigned int *__restrict__ mask)
 {
     const i64 lane = (i64)blockIdx.x * kXThreads + threadIdx.x;
     const i64 per_row = nw32 * 32;
     const i64 y = lane / per_row;
     if (y >= ny) return;   /* whole warps: a row holds a multiple of 32 lanes */
-    const i64 zw = (lane - y * per_row) >> 5;
+    const int zw = (int)((lane - y * per_row) >> 5);
     const int bit = (int)(lane & 31);
-    const i64 z = zw * 32 + bit;
+    const i64 z = (i64)zw * 32 + bit;
     const bool valid = z < nz;
-    const i64 plane = ny * nz, off = y * nz + (valid ? z : 0);
+    const i64 plane = ny * nz;
+    const i64 off = y * nz + (valid ? z : 0);
+    const float *pa = A + off, *pm = M + off, *pc = c + off;
     const float nyz = (float)(clipped(y, sy, ny) * clipped(z, sz, nz));
-    /* box statistics of plane x -> selection or stats output */
-    auto emit = [&](i64 x, float mu, float m2, float X) {
+    const i64 x0 = (i64)blockIdx.y * kXSeg;
+    const i64 x1 = x0 + kXSeg < nx ? x0 + kXSeg : nx;
+    /* segment blockIdx.y of kXSeg planes: the sums start from a direct sum
+     * over the box of the segment's first plane, shifted by that plane's A,
+     * so the running updates neither drift nor cancel */
+    const float s = pa[x0 * plane];
+    Kahan sa, sb, sm;   /* sums over the x box of A - s, (A - s)^2, M */
+    {
+        const i64 lo = x0 - sx < 0 ? 0 : x0 - sx, hi = x0 + sx >= nx ? nx - 1 : x0 + sx;
+        for (i64 xi = lo; xi <= hi; ++xi) {
+            const float d = pa[xi * plane] - s;
+            sa.add(d);
+            sb.add(d * d);
+            sm.add(pm[xi * plane]);
+        }
+    }
+#pragma unroll 4
+    for (i64 x = x0; x < x1; ++x) {
+        /* the step's loads, unconditional (unused ones read plane 0) so they
+         * issue together */
+        const i64 xin = x + sx, xout = x - sx - 1;
+        const bool hin = x > x0 && xin < nx, hout = x > x0 && xout >= 0;
+        const i64 oin = (hin ? xin : 0) * plane, oout = (hout ? xout : 0) * plane;
+        const float ain = pa[oin], min_ = pm[oin], aout = pa[oout], mout = pm[oout];
+        const float cv = MODE != 0 ? pc[x * plane] : 0.f;
+        if (hin) {
+            const float d = ain - s;
+            sa.add(d);
+            sb.add(d * d);
+            sm.add(min_);
+        }
+        if (hout) {
+            const float d = aout - s;
+            sa.add(-d);
+            sb.add(-(d * d));
+            sm.add(-mout);
+        }
+        float X, mu, m2;
+        if (sx == 0) {
+            /* the x box is the plane itself */
+            X = 1.f;
+            mu = pa[x * plane];
+            m2 = pm[x * plane];
+        } else {
+            X = (float)clipped(x, sx, nx);
+            const float da = sa.s / X;
+            mu = s + da;
+            /* a rounded product (no contraction into an fma) */
+            m2 = sm.s + nyz * fmaxf(sb.s - __fmul_rn(sa.s, da), 0.f);
+        }
         const float sd = sqrtf(m2 / (X * nyz));
-        if (mode == 0) {
+        if (MODE == 0) {
             if (valid) {
                 mean[x * plane + off] = mu;
                 stdv[x * plane + off] = sd;
             }
         } else {
-            const bool fire = valid && c[x * plane + off] > fmaf(k, sd, mu);
-            const unsigned int bits = __ballot_sync(0xffffffffu, fire);
+            const unsigned int bits = __ballot_sync(0xffffffffu, valid && cv > fmaf(k, sd, mu));
             if (bit == 0) {
                 unsigned int *w = mask + (x * ny + y) * nw32 + zw;
-                *w = mode == 2 ? (*w | bits) : bits;
-            }
-        }
-    };
-    if (sx == 0) {
-        /* the x box is the plane itself */
-        for (i64 x = 0; x < nx; ++x) {
-            const float a = valid ? A[x * plane + off] : 0.f, m = valid ? M[x * plane + off] : 0.f;
-            emit(x, a, m, 1.f);
-        }
-        return;
-    }
-    /* segments of kXSeg planes: the sums restart from a direct sum over the
-     * box of the segment's first plane, shifted by that plane's A, so the
-     * running updates neither drift nor cancel */
-    for (i64 x0 = 0; x0 < nx; x0 += kXSeg) {
-        const float s = valid ? A[x0 * plane + off] : 0.f;
-        Kahan sa, sb, sm;   /* sums over the x box of A - s, (A - s)^2, M */
-        if (valid) {
-            const i64 lo = x0 - sx < 0 ? 0 : x0 - sx, hi = x0 + sx >= nx ? nx - 1 : x0 + sx;
-            for (i64 xi = lo; xi <= hi; ++xi) {
-                const float d = A[xi * plane + off] - s;
-                sa.add(d);
-                sb.add(d * d);
-                sm.add(M[xi * plane + off]);
-            }
-        }
-        const i64 x1 = x0 + kXSeg < nx ? x0 + kXSeg : nx;
-        for (i64 x = x0; x < x1; ++x) {
-            if (valid && x > x0) {
-                const i64 xin = x + sx, xout = x - sx - 1;
-                if (xin < nx) {
-                    const float d = A[xin * plane + off] - s;
-                    sa.add(d);
-                    sb.add(d * d);
-                    sm.add(M[xin * plane + off]);
-                }
-                if (xout >= 0) {
-                    const float d = A[xout * plane + off] - s;
-                    sa.add(-d);
-                    sb.add(-(d * d));
-                    sm.add(-M[xout * plane + off]);
+                if (MODE == 2) {
+                    if (bits) atomicOr(w, bits);   /* nothing waits on it */
+                } else {
+                    *w = bits;
                 }
             }
-            const float X = (float)clipped(x, sx, nx);
-            const float da = sa.s / X;
-            emit(x, s + da, sm.s + nyz * fmaxf(sb.s - __fmul_rn(sa.s, da), 0.f), X);
         }
     }
 }
@@ -237,7 +270,7 @@ __global__ void __launch_bounds__(kXThreads) sf_local_x(const float *__restrict_
 size_t sf_local_yz_smem(int sy, int sz)
 {
     const size_t rows = (size_t)kYT + 2 * (size_t)sy;
-    return sizeof(float) * rows * ((size_t)stage_cols(sz) + 2 * kZT);
+    return sizeof(float) * rows * ((size_t)stage_cols(sz) + 2 * kPZ);
 }
 
 cudaError_t sf_launch_local_yz(const float *c, float *A, float *M, long long nx, long long ny, long long nz, int sy,
@@ -256,7 +289,9 @@ cudaError_t sf_launch_local_x(const float *c, const float *A, const float *M, lo
                               float *stdv, unsigned int *mask, int mode, cudaStream_t st)
 {
     const long long lanes = ny * nw32 * 32;
-    const unsigned grid = (unsigned)((lanes + kXThreads - 1) / kXThreads);
-    sf_local_x<<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask, mode);
+    const dim3 grid((unsigned)((lanes + kXThreads - 1) / kXThreads), (unsigned)((nx + kXSeg - 1) / kXSeg));
+    if (mode == 0) sf_local_x<0><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask);
+    else if (mode == 1) sf_local_x<1><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask);
+    else sf_local_x<2><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask);
     return cudaGetLastError();
 }
