@@ -103,6 +103,14 @@ def _load():
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _i64, _dp,
                                        _dp, ctypes.c_int]
         lib.or_local_stats.restype = ctypes.c_int
+        lib.or_weighted_filter_box.argtypes = [_fp, _fp, _i64, _i64, _i64, _dp, ctypes.c_int, _dp,
+                                               ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _i64,
+                                               _i64, _i64, _i64, _i64, _i64, _dp]
+        lib.or_weighted_filter_box.restype = ctypes.c_int
+        lib.or_weighted_direct_voxel.argtypes = [_fp, _fp, _i64, _i64, _i64, _dp, ctypes.c_int, _dp,
+                                                 ctypes.c_int, _dp, ctypes.c_int, ctypes.c_int, _i64,
+                                                 _i64, _i64]
+        lib.or_weighted_direct_voxel.restype = ctypes.c_double
         _lib = lib
         return lib
 
@@ -400,3 +408,76 @@ def local_detect(d, bank, truncation, half, k, band_rel: float = 1e-4, voxels=No
     clear = (fire_f & ~near).any(axis=0)
     sure = clear | ~near.any(axis=0)
     return fire.astype(np.uint8), sure.astype(np.uint8), cv, mv, sv
+
+
+# ------------------------------------------------- weighted convolution (Eq. 1)
+DEN_MODES = {"fw": 0, "w": 1}
+
+
+def weighted_filter_box(d, w, sigma_xy: float, sigma_z: float, truncation: float, den: str = "fw",
+                        box=None) -> np.ndarray:
+    """Eq. 1 on box ((x0,x1),(y0,y1),(z0,z1)) (float64): sum d f w / D with
+    D = sum f w (den="fw", normalised convolution) or D = sum w (den="w", as
+    printed); 0 where D = 0."""
+    d = _cube(d)
+    w = _cube(w)
+    if d.shape != w.shape:
+        raise ValueError("cube and weights must have the same shape")
+    nx, ny, nz = d.shape
+    if box is None:
+        box = ((0, nx), (0, ny), (0, nz))
+    (x0, x1), (y0, y1), (z0, z1) = box
+    gxy = taps(sigma_xy, truncation)
+    gz = taps(sigma_z, truncation)
+    rxy, rz = (len(gxy) - 1) // 2, (len(gz) - 1) // 2
+    out = np.empty((x1 - x0, y1 - y0, z1 - z0), dtype=np.float64)
+    rc = _load().or_weighted_filter_box(_ptr(d, _fp), _ptr(w, _fp), nx, ny, nz, _ptr(gxy, _dp), rxy,
+                                        _ptr(gxy, _dp), rxy, _ptr(gz, _dp), rz, DEN_MODES[den],
+                                        x0, x1, y0, y1, z0, z1, _ptr(out, _dp))
+    if rc != 0:
+        raise MemoryError("oracle weighted_filter_box: out of memory")
+    return out
+
+
+def weighted_direct_voxel(d, w, sigma_xy: float, sigma_z: float, truncation: float, x: int, y: int,
+                          z: int, den: str = "fw") -> float:
+    """Eq. 1 as the literal triple sums at one voxel."""
+    d = _cube(d)
+    w = _cube(w)
+    nx, ny, nz = d.shape
+    gxy = taps(sigma_xy, truncation)
+    gz = taps(sigma_z, truncation)
+    rxy, rz = (len(gxy) - 1) // 2, (len(gz) - 1) // 2
+    return float(_load().or_weighted_direct_voxel(_ptr(d, _fp), _ptr(w, _fp), nx, ny, nz,
+                                                  _ptr(gxy, _dp), rxy, _ptr(gxy, _dp), rxy,
+                                                  _ptr(gz, _dp), rz, DEN_MODES[den], x, y, z))
+
+
+def weighted_detect(d, w, bank, truncation, window, k, den: str = "fw", band_rel: float = 1e-4):
+    """The method with Eq. 1 filtering: every filter of the bank weighted by w,
+    window statistics (Sec. 3.3), c > mean + k std, OR over the bank.
+    Returns dict(mask, sure (packed words), mean, std [nf][nwx][nwy][nwz])."""
+    d = _cube(d)
+    nf = len(bank)
+    grid = window_grid(d.shape, window)
+    mask = np.zeros(mask_words_shape(d.shape), dtype=np.uint32)
+    means = np.empty((nf,) + grid)
+    stds = np.empty((nf,) + grid)
+    fire = np.zeros(d.shape, dtype=bool)
+    clear = np.zeros(d.shape, dtype=bool)
+    near_any = np.zeros(d.shape, dtype=bool)
+    for f, (sxy, sz) in enumerate(bank):
+        c = weighted_filter_box(d, w, sxy, sz, truncation, den)
+        m, s = window_stats(c, window)
+        means[f], stds[f] = m, s
+        wi = [np.arange(n) // wn for n, wn in zip(d.shape, window)]
+        mb = m[np.ix_(*wi)]
+        sb = s[np.ix_(*wi)]
+        thr = mb + k * sb
+        ff = c > thr
+        near = np.abs(c - thr) < band_rel * sb
+        fire |= ff
+        clear |= ff & ~near
+        near_any |= near
+    sure = clear | ~near_any
+    return {"mask": pack_bits(fire), "sure": pack_bits(sure), "mean": means, "std": stds}

@@ -453,3 +453,112 @@ int or_local_stats(const double *c, int64_t nx, int64_t ny, int64_t nz, int sx, 
     }
     return used;
 }
+
+/*
+ * Eq. 1 (weighted convolution) on the box [x0,x1) x [y0,y1) x [z0,z1):
+ *   c_w = sum_o d[i] f[o] w[i] / D,  i = v + o over the filter offsets,
+ * with d and w zero outside the cube.  The denominator is read two ways (the
+ * printed form sums w alone, which does not reduce to Eq. 2 for unit
+ * weights):
+ *   den_mode 0  D = sum_o f[o] w[i]   (normalised convolution; w = 1 gives
+ *                                      Eq. 2 wherever the support is inside);
+ *   den_mode 1  D = sum_o w[i]        (as printed).
+ * Where D = 0 (no weight in the support) c_w = 0.  Both sums use the same
+ * three 1D passes as or_filter_box (x, then y, then z), on the product d*w
+ * and on w, in double precision.  out is [x1-x0][y1-y0][z1-z0].
+ * Returns 0, or -1 when memory runs out.
+ */
+static void passes3(const double *src, int64_t ex, int64_t ey, int64_t ez, const double *gx, int rx,
+                    const double *gy, int ry, const double *gz, int rz, double *t1, double *t2,
+                    double *out)
+{
+    /* src covers [x0-rx, x1+rx) x [y0-ry, y1+ry) x [z0-rz, z1+rz) */
+    const int64_t exh = ex + 2 * rx, eyh = ey + 2 * ry, ezh = ez + 2 * rz;
+    for (int64_t i = 0; i < ex; ++i)
+        for (int64_t j = 0; j < eyh; ++j)
+            for (int64_t k = 0; k < ezh; ++k) {
+                double s = 0.0;
+                for (int o = -rx; o <= rx; ++o)
+                    s += gx[o + rx] * src[((i + rx + o) * eyh + j) * ezh + k];
+                t1[(i * eyh + j) * ezh + k] = s;
+            }
+    (void)exh;
+    for (int64_t i = 0; i < ex; ++i)
+        for (int64_t j = 0; j < ey; ++j)
+            for (int64_t k = 0; k < ezh; ++k) {
+                double s = 0.0;
+                for (int o = -ry; o <= ry; ++o)
+                    s += gy[o + ry] * t1[(i * eyh + (j + ry + o)) * ezh + k];
+                t2[(i * ey + j) * ezh + k] = s;
+            }
+    for (int64_t i = 0; i < ex; ++i)
+        for (int64_t j = 0; j < ey; ++j)
+            for (int64_t k = 0; k < ez; ++k) {
+                double s = 0.0;
+                for (int o = -rz; o <= rz; ++o)
+                    s += gz[o + rz] * t2[(i * ey + j) * ezh + (k + rz + o)];
+                out[(i * ey + j) * ez + k] = s;
+            }
+}
+
+int or_weighted_filter_box(const float *d, const float *w, int64_t nx, int64_t ny, int64_t nz,
+                           const double *gx, int rx, const double *gy, int ry, const double *gz, int rz,
+                           int den_mode, int64_t x0, int64_t x1, int64_t y0, int64_t y1, int64_t z0,
+                           int64_t z1, double *out)
+{
+    const int64_t ex = x1 - x0, ey = y1 - y0, ez = z1 - z0;
+    const int64_t exh = ex + 2 * rx, eyh = ey + 2 * ry, ezh = ez + 2 * rz;
+    const size_t nh = (size_t)(exh * eyh * ezh), nb = (size_t)(ex * ey * ez);
+    double *pw = (double *)malloc(sizeof(double) * nh), *ww = (double *)malloc(sizeof(double) * nh);
+    double *t1 = (double *)malloc(sizeof(double) * (size_t)(ex * eyh * ezh));
+    double *t2 = (double *)malloc(sizeof(double) * (size_t)(ex * ey * ezh));
+    double *num = (double *)malloc(sizeof(double) * nb), *den = (double *)malloc(sizeof(double) * nb);
+    double *ones = (double *)malloc(sizeof(double) * (size_t)(2 * (rx > ry ? (rx > rz ? rx : rz) : (ry > rz ? ry : rz)) + 1));
+    if (!pw || !ww || !t1 || !t2 || !num || !den || !ones) {
+        free(pw); free(ww); free(t1); free(t2); free(num); free(den); free(ones);
+        return -1;
+    }
+    for (int64_t i = 0; i < exh; ++i)
+        for (int64_t j = 0; j < eyh; ++j)
+            for (int64_t k = 0; k < ezh; ++k) {
+                const int64_t x = x0 - rx + i, y = y0 - ry + j, z = z0 - rz + k;
+                const size_t q = (size_t)((i * eyh + j) * ezh + k);
+                if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz) {
+                    pw[q] = 0.0;
+                    ww[q] = 0.0;
+                } else {
+                    const size_t v = (size_t)((x * ny + y) * nz + z);
+                    pw[q] = (double)d[v] * (double)w[v];
+                    ww[q] = (double)w[v];
+                }
+            }
+    passes3(pw, ex, ey, ez, gx, rx, gy, ry, gz, rz, t1, t2, num);
+    if (den_mode == 0) {
+        passes3(ww, ex, ey, ez, gx, rx, gy, ry, gz, rz, t1, t2, den);
+    } else {
+        const int rm = rx > ry ? (rx > rz ? rx : rz) : (ry > rz ? ry : rz);
+        for (int o = 0; o <= 2 * rm; ++o) ones[o] = 1.0;
+        passes3(ww, ex, ey, ez, ones, rx, ones, ry, ones, rz, t1, t2, den);
+    }
+    for (size_t v = 0; v < nb; ++v) out[v] = den[v] != 0.0 ? num[v] / den[v] : 0.0;
+    free(pw); free(ww); free(t1); free(t2); free(num); free(den); free(ones);
+    return 0;
+}
+
+/* Eq. 1 written out literally for one voxel: the triple sums of the
+ * numerator and of the denominator (den_mode as above). */
+double or_weighted_direct_voxel(const float *d, const float *w, int64_t nx, int64_t ny, int64_t nz,
+                                const double *gx, int rx, const double *gy, int ry, const double *gz,
+                                int rz, int den_mode, int64_t x, int64_t y, int64_t z)
+{
+    double num = 0.0, den = 0.0;
+    for (int ox = -rx; ox <= rx; ++ox)
+        for (int oy = -ry; oy <= ry; ++oy)
+            for (int oz = -rz; oz <= rz; ++oz) {
+                const double f = gx[ox + rx] * gy[oy + ry] * gz[oz + rz];
+                const double wv = at(w, nx, ny, nz, x + ox, y + oy, z + oz, 0);
+                num += at(d, nx, ny, nz, x + ox, y + oy, z + oz, 0) * f * wv;
+                den += den_mode == 0 ? f * wv : wv;
+            }
+    return den != 0.0 ? num / den : 0.0;
+}

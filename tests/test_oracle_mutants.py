@@ -48,11 +48,24 @@ LOCAL_MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(LOCAL_MUTANTS))
+# slips in the weighted convolution, caught by tests/test_oracle_weighted_pins.py
+WEIGHTED_MUTANTS = {
+    "weighted_product_drops_w": ("pw[q] = (double)d[v] * (double)w[v];", "pw[q] = (double)d[v];"),
+    "weighted_den_modes_swapped": ("if (den_mode == 0) {\n        passes3(ww,",
+                                   "if (den_mode != 0) {\n        passes3(ww,"),
+    "weighted_zero_den_gives_one": ("out[v] = den[v] != 0.0 ? num[v] / den[v] : 0.0;",
+                                    "out[v] = den[v] != 0.0 ? num[v] / den[v] : 1.0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(LOCAL_MUTANTS) + sorted(WEIGHTED_MUTANTS))
 def test_pins_catch_planted_slip(tmp_path, name):
     local = name in LOCAL_MUTANTS
-    old, new = LOCAL_MUTANTS[name] if local else MUTANTS[name]
-    pins = "test_oracle_local_pins.py" if local else "test_oracle_pins.py"
+    weighted = name in WEIGHTED_MUTANTS
+    old, new = (LOCAL_MUTANTS[name] if local else WEIGHTED_MUTANTS[name] if weighted
+                else MUTANTS[name])
+    pins = ("test_oracle_local_pins.py" if local else
+            "test_oracle_weighted_pins.py" if weighted else "test_oracle_pins.py")
     dst = tmp_path / "oracle_mutant"
     shutil.copytree(os.path.join(ROOT, "oracle"), dst,
                     ignore=shutil.ignore_patterns("_build", "__pycache__"))
