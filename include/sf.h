@@ -231,6 +231,26 @@ sf_status sf_local_stats(sf_ctx *ctx, const float *d_filtered, int32_t sx, int32
 sf_status sf_local_detect(sf_ctx *ctx, const void *d_cube, int32_t sx, int32_t sy, int32_t sz,
                           uint32_t *d_mask, void *stream);
 
+/* Weighted convolution (Eq. 1): c_w = sum_o d[i] f[o] w[i] / D over the
+ * filter's offsets, d and w zero outside the cube, with
+ *   den = 0  D = sum_o f[o] w[i]  (normalised convolution: unit weights give
+ *            Eq. 2 wherever the support lies inside the cube),
+ *   den = 1  D = sum_o w[i]       (the denominator as the paper prints it);
+ * c_w = 0 where D = 0.  d_cube and d_weights: float32 [nx][ny][nz] (device,
+ * 16-byte aligned); float32 storage contexts only, not batched.  The context
+ * keeps three float32 scratch cubes (product, numerator, denominator), and
+ * for den = 1 a second plan with the bank's radii and unit taps, both created
+ * on first use (SF_ENOMEM if that fails). */
+sf_status sf_weighted_filter(sf_ctx *ctx, const float *d_cube, const float *d_weights, int32_t filter,
+                             int32_t den, float *d_out, void *stream);
+
+/* The detect with Eq. 1 filtering: every filter of the bank weighted by w,
+ * window statistics, c > mean + k*std, OR over the bank into d_mask (every
+ * word written).  d_mean / d_std: NULL, or float32 [n_filters][nwx*nwy*nwz]
+ * like sf_detect's. */
+sf_status sf_weighted_detect(sf_ctx *ctx, const float *d_cube, const float *d_weights, int32_t den,
+                             uint32_t *d_mask, float *d_mean, float *d_std, void *stream);
+
 /* Wait for the work enqueued on `stream`, then report kernel-side failures:
  * SF_ETIMEOUT when a kernel's bounded wait on its own shared-memory loads
  * expired since the last call (the flag is cleared). */

@@ -48,13 +48,14 @@ def _embed(out_path: str) -> None:
 def _sources() -> list[str]:
     return [os.path.join(CSRC, "sf_runtime.cpp"), os.path.join(CSRC, "sf_aot.cu"),
             os.path.join(CSRC, "sf_noalloc.cu"), os.path.join(CSRC, "sf_server.cpp"),
-            os.path.join(CSRC, "sf_local.cu"), os.path.join(BUILD, "sf_embedded.cpp")]
+            os.path.join(CSRC, "sf_local.cu"), os.path.join(CSRC, "sf_weighted.cu"),
+            os.path.join(BUILD, "sf_embedded.cpp")]
 
 
 def _inputs() -> list[str]:
     files = [os.path.join(CSRC, "sf_runtime.cpp"), os.path.join(CSRC, "sf_aot.cu"),
              os.path.join(CSRC, "sf_noalloc.cu"), os.path.join(CSRC, "sf_server.cpp"),
-             os.path.join(CSRC, "sf_local.cu"),
+             os.path.join(CSRC, "sf_local.cu"), os.path.join(CSRC, "sf_weighted.cu"),
              os.path.join(CSRC, "sf_kernel_abi.h"), os.path.join(CSRC, "kernels", "sf_kernels.cuh"),
              os.path.join(ROOT, "include", "sf.h"), os.path.abspath(__file__)]
     return files

@@ -44,6 +44,8 @@ cudaError_t sf_launch_stats(const float *c, long long nx, long long ny, long lon
                             int wz, int nwx, int nwy, int nwz, float *mean, float *stdv,
                             cudaStream_t st);
 size_t sf_local_yz_smem(int sy, int sz);
+cudaError_t sf_launch_w_product(const float *d, const float *w, float *p, long long n, cudaStream_t st);
+cudaError_t sf_launch_w_ratio(const float *num, const float *den, float *out, long long n, cudaStream_t st);
 cudaError_t sf_launch_local_yz(const float *c, float *P, float *Q, long long nx, long long ny, long long nz, int sy,
                                int sz, cudaStream_t st);
 cudaError_t sf_launch_local_x(const float *c, const float *P, const float *Q, long long nx, long long ny,
@@ -248,6 +250,9 @@ struct sf_ctx {
     cudaStream_t hcopy[2] = {nullptr, nullptr}, hback = nullptr;
     cudaStream_t hcomp[2] = {nullptr, nullptr};   /* compute streams of the host pipeline */
     float *lscratch = nullptr;        /* local statistics: filtered cube, P, Q */
+    float *wscratch = nullptr;        /* weighted form: product, numerator, denominator */
+    float *wstats = nullptr;          /* weighted form: window mean / std of one filter */
+    sf_ctx *boxtwin = nullptr;        /* the bank's radii with unit taps (printed Eq. 1 denominator) */
     std::vector<cudaEvent_t> hev;
 
     /* stage timing: pairs of events per recorded stage instance */
@@ -1394,6 +1399,9 @@ sf_status sf_destroy(sf_ctx *c)
     for (cudaStream_t x : c->hcomp)
         if (x) cudaStreamDestroy(x);
     cudaFree(c->lscratch);
+    cudaFree(c->wscratch);
+    cudaFree(c->wstats);
+    if (c->boxtwin) sf_destroy(c->boxtwin);
     for (cudaStream_t x : c->hcopy)
         if (x) cudaStreamDestroy(x);
     if (c->hback) cudaStreamDestroy(c->hback);
@@ -1900,6 +1908,107 @@ sf_status sf_local_detect(sf_ctx *c, const void *d_cube, int32_t sx, int32_t sy,
             e = sf_launch_local_x(F, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, nullptr, nullptr, d_mask,
                                   f == 0 ? 1 : 2, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "local detect launch");
+    }
+    return SF_OK;
+}
+
+namespace {
+sf_status weighted_check(sf_ctx *c, const float *d_cube, const float *d_w, int den)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (c->batch) return fail(c, SF_EINVAL, "batched context: the weighted form takes one cube");
+    if (c->cfg.storage != SF_F32) return fail(c, SF_EINVAL, "the weighted form takes float32 storage");
+    if (den != 0 && den != 1) return fail(c, SF_EINVAL, "den must be 0 (sum f w) or 1 (sum w)");
+    if (!d_cube || !d_w) return fail(c, SF_EINVAL, "NULL buffer");
+    if (!aligned16(d_cube) || !aligned16(d_w)) return fail(c, SF_EINVAL, "buffers must be 16-byte aligned");
+    return SF_OK;
+}
+
+sf_status weighted_scratch(sf_ctx *c, int den)
+{
+    if (!c->wscratch) {
+        const size_t cube = align_up((size_t)c->nvox * sizeof(float), 256);
+        cudaError_t e = cudaMalloc((void **)&c->wscratch, 3 * cube);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&c->wstats, 2 * sizeof(float) * (size_t)c->nwin);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->wscratch);
+            c->wscratch = nullptr;
+            return fail(c, SF_ENOMEM, "weighted-form scratch (%zu bytes)", 3 * cube);
+        }
+    }
+    if (den == 1 && !c->boxtwin) {
+        /* same shape, bank radii and window; every tap 1 (a box sum) */
+        sf_config cfg = c->cfg;
+        std::vector<sf_filter_spec> specs;
+        for (const Filt &f : c->filt) specs.push_back(sf_filter_spec{f.sxy, f.sz});
+        cfg.filters = specs.data();
+        cfg.device = c->device;
+        sf_ctx *t = nullptr;
+        sf_status s = create_impl(&cfg, 0, nullptr, &t);
+        if (s != SF_OK) return fail(c, s, "box-tap twin context");
+        for (Filt &f : t->filt) {
+            std::fill(f.gxy.begin(), f.gxy.end(), 1.f);
+            std::fill(f.gz.begin(), f.gz.end(), 1.f);
+        }
+        c->boxtwin = t;
+    }
+    return SF_OK;
+}
+
+/* c = Eq. 1 for filter f of the bank, into out; p = d * w already formed */
+sf_status weighted_one(sf_ctx *c, const float *p, const float *d_w, int f, int den, float *out, cudaStream_t st)
+{
+    const size_t cube = align_up((size_t)c->nvox * sizeof(float), 256) / sizeof(float);
+    float *num = c->wscratch + cube, *dn = c->wscratch + 2 * cube;
+    sf_status s = sf_filter(c, p, f, num, st);
+    if (s != SF_OK) return s;
+    sf_ctx *dc = den == 1 ? c->boxtwin : c;
+    if ((s = sf_filter(dc, d_w, f, dn, st)) != SF_OK) return dc == c ? s : fail(c, s, "%s", dc->err.c_str());
+    const cudaError_t e = sf_launch_w_ratio(num, dn, out, c->nvox, st);
+    return e == cudaSuccess ? SF_OK : cuda_fail(c, e, "ratio launch");
+}
+}  // namespace
+
+sf_status sf_weighted_filter(sf_ctx *c, const float *d_cube, const float *d_weights, int32_t filter, int32_t den,
+                             float *d_out, void *stream)
+{
+    sf_status s = weighted_check(c, d_cube, d_weights, den);
+    if (s != SF_OK) return s;
+    if (filter < 0 || filter >= (int)c->filt.size()) return fail(c, SF_EINVAL, "filter index %d", filter);
+    if (!d_out || !aligned16(d_out)) return fail(c, SF_EINVAL, "d_out must be a 16-byte aligned buffer");
+    DeviceGuard dg(c->device);
+    if ((s = weighted_scratch(c, den)) != SF_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *p = c->wscratch;
+    const cudaError_t e = sf_launch_w_product(d_cube, d_weights, p, c->nvox, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "product launch");
+    return weighted_one(c, p, d_weights, filter, den, d_out, st);
+}
+
+sf_status sf_weighted_detect(sf_ctx *c, const float *d_cube, const float *d_weights, int32_t den, uint32_t *d_mask,
+                             float *d_mean, float *d_std, void *stream)
+{
+    sf_status s = weighted_check(c, d_cube, d_weights, den);
+    if (s != SF_OK) return s;
+    if (!d_mask) return fail(c, SF_EINVAL, "NULL mask");
+    if ((d_mean == nullptr) != (d_std == nullptr))
+        return fail(c, SF_EINVAL, "d_mean and d_std must both be NULL or both be set");
+    DeviceGuard dg(c->device);
+    if ((s = weighted_scratch(c, den)) != SF_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t cube = align_up((size_t)c->nvox * sizeof(float), 256) / sizeof(float);
+    float *p = c->wscratch, *num = c->wscratch + cube;
+    cudaError_t e = sf_launch_w_product(d_cube, d_weights, p, c->nvox, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "product launch");
+    for (int f = 0; f < (int)c->filt.size(); ++f) {
+        /* the ratio overwrites the numerator in place */
+        if ((s = weighted_one(c, p, d_weights, f, den, num, st)) != SF_OK) return s;
+        float *m = d_mean ? d_mean + (size_t)f * c->nwin : c->wstats;
+        float *sd = d_std ? d_std + (size_t)f * c->nwin : c->wstats + c->nwin;
+        if ((s = sf_stats(c, num, m, sd, stream)) != SF_OK) return s;
+        if ((s = sf_threshold(c, num, m, sd, d_mask, f > 0 ? 1 : 0, stream)) != SF_OK) return s;
     }
     return SF_OK;
 }

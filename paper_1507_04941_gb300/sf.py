@@ -77,6 +77,8 @@ SIGNATURES = {
                                  ctypes.c_float, _vp, _vp]),
     "sf_local_stats": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "sf_local_detect": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "sf_weighted_filter": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
+    "sf_weighted_detect": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "sf_profile_enable": (_i32, [_vp, _i32]),
     "sf_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
 }
@@ -274,6 +276,38 @@ class SourceFinder:
         _check(lib().sf_local_detect(self._h, _ptr(cube), sx, sy, sz, _ptr(mask),
                                      _stream(self.device)), self._h)
         return mask
+
+    DEN = {"fw": 0, "w": 1}
+
+    def weighted_filter(self, cube, weights, filter_index: int, den: str = "fw", out=None):
+        """Eq. 1 for one filter: sum d f w / D, D = sum f w (den="fw") or
+        sum w (den="w", as printed); float32 cube of the context's shape."""
+        import torch
+        self._check_f32(cube, self.shape, "cube")
+        self._check_f32(weights, self.shape, "weights")
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        self._check_f32(out, self.shape, "out")
+        _check(lib().sf_weighted_filter(self._h, _ptr(cube), _ptr(weights), int(filter_index),
+                                        self.DEN[den], _ptr(out), _stream(self.device)), self._h)
+        return out
+
+    def weighted_detect(self, cube, weights, den: str = "fw", mask=None, stats: bool = False):
+        """Packed mask of the method with Eq. 1 filtering; with stats=True also
+        (mean, std) as float32 [n_filters][nwx][nwy][nwz]."""
+        import torch
+        self._check_f32(cube, self.shape, "cube")
+        self._check_f32(weights, self.shape, "weights")
+        if mask is None:
+            mask = torch.empty(self.mask_shape, dtype=torch.int32, device=self.device)
+        mean = std = None
+        if stats:
+            shp = (len(self.bank),) + self.grid
+            mean = torch.empty(shp, dtype=torch.float32, device=self.device)
+            std = torch.empty(shp, dtype=torch.float32, device=self.device)
+        _check(lib().sf_weighted_detect(self._h, _ptr(cube), _ptr(weights), self.DEN[den], _ptr(mask),
+                                        _ptr(mean), _ptr(std), _stream(self.device)), self._h)
+        return (mask, mean, std) if stats else mask
 
     def detect_host(self, cube_host, mask_host=None):
         """Host tensors in and out (pinned memory makes the copies DMA)."""

@@ -150,3 +150,27 @@ def make_subcube(spec: dict, device="cpu") -> torch.Tensor:
     """One subcube of the batched workload (noise model of the tile workload)."""
     return make_cube(spec["shape"], spec["seed"], spec["n_sources"], (0.3, 5.0), 1.5,
                      device=device)
+
+
+def make_weights(shape, seed: int, noise_sigma=(0.8, 1.5), n_flagged: int = 3, flag_width=(4, 24),
+                 device="cpu") -> torch.Tensor:
+    """Seeded float32 weights cube [x][y][z] for the weighted convolution
+    (Eq. 1): inverse noise variance, w = 1 / sigma(z)^2 with sigma rising
+    linearly over the channels from noise_sigma[0] to noise_sigma[1] and a
+    +-10% smooth spatial ripple, and n_flagged channel ranges (widths
+    integer-uniform in flag_width, positions uniform) set to 0, as flagged
+    channels are.  Parameters from numpy PCG64(seed + 2)."""
+    nx, ny, nz = (int(s) for s in shape)
+    rng = np.random.Generator(np.random.PCG64(int(seed) + 2))
+    z = np.arange(nz, dtype=np.float64)
+    sig = noise_sigma[0] + (noise_sigma[1] - noise_sigma[0]) * z / max(1, nz - 1)
+    px, py = rng.uniform(0.0, 2 * math.pi, size=2)
+    x = np.arange(nx, dtype=np.float64)[:, None]
+    y = np.arange(ny, dtype=np.float64)[None, :]
+    ripple = 1.0 + 0.1 * np.sin(2 * math.pi * x / max(8, nx) + px) * np.cos(2 * math.pi * y / max(8, ny) + py)
+    w = (ripple[:, :, None] / (sig * sig)[None, None, :]).astype(np.float32)
+    for _ in range(int(n_flagged)):
+        width = int(rng.integers(flag_width[0], flag_width[1] + 1))
+        start = int(rng.integers(0, max(1, nz - width)))
+        w[:, :, start:start + width] = 0.0
+    return torch.from_numpy(np.ascontiguousarray(w)).to(device)
