@@ -340,6 +340,40 @@ def run_ours(args):
                               "peak_gbs": hbm_peak,
                               "frac": lbytes / (msl * 1e-3) / 1e9 / hbm_peak}}
 
+    # weighted form (Eq. 1, normalised denominator): same cube and bank with
+    # a synthetic inverse-variance weights cube (flagged channels at 0)
+    weighted = None
+    if not args.no_weighted and storage == "f32":
+        wts = synth.make_weights(w.shape, w.seed, device=dev)
+        wmask = torch.empty(sf.mask_shape, dtype=torch.int32, device=dev)
+        for _ in range(3):
+            sf.weighted_detect(cube, wts, "fw", wmask)
+        torch.cuda.synchronize(dev)
+        n_w = max(5, min(args.steps // 10, 30))
+        w0 = torch.cuda.Event(enable_timing=True)
+        w1 = torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
+        for _ in range(n_w):
+            sf.weighted_detect(cube, wts, "fw", wmask)
+        w1.record(stream)
+        torch.cuda.synchronize(dev)
+        msw = w0.elapsed_time(w1) / n_w
+        nf = len(w.bank)
+        n_xy = sum(1 for b in w.bank if b[0] > 0)
+        # composed traffic per voxel: product (8 B in, 4 out); per filter the
+        # filter of d*w and of w (x pass 8 B where sigma_xy > 0, y/z pass 8 B
+        # each), the ratio (8 in, 4 out), window stats (4 in), threshold (4 in,
+        # mask words written, then read and written)
+        wbytes = nvox * (12 + 2 * (8 * nf + 8 * n_xy) + nf * (12 + 4 + 4) + 0.125 + 0.25 * (nf - 1))
+        weighted = {"value": units / (msw * 1e-3), "unit": UNIT, "ms_per_step": msw, "steps": n_w,
+                    "denominator": "sum f w (normalised convolution)",
+                    "weights": "inverse noise variance rising 0.8 -> 1.5 sigma along z, 3 flagged channel ranges",
+                    "path": "product; per filter: filter of d*w and of w, ratio, window stats, threshold",
+                    "hbm_view": {"bytes_per_step": wbytes, "achieved_gbs": wbytes / (msw * 1e-3) / 1e9,
+                                 "peak_gbs": hbm_peak,
+                                 "frac": wbytes / (msw * 1e-3) / 1e9 / hbm_peak}}
+        del wts
+
     # batched form: 64 uneven subcubes in one persistent launch (CUDA graph)
     batch = None
     if not args.no_batch and world == 1 and storage == "f32":
@@ -389,7 +423,7 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({nvox * sbytes / 2**20:.0f} MiB cube, "
                              "129 MB L2)"},
             "roofline": roof, "kernels": other, "clocks": clocks, "storage_forms": forms,
-            "local_stats_form": local,
+            "local_stats_form": local, "weighted_form": weighted,
             "serving": serving,
             "path": "persistent (x-pass + windows in one launch)" if persistent else
                     "x pass + window kernel", "autotune": tune_rep, "batched_form": batch,
@@ -626,6 +660,7 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 64-subcube form")
     ap.add_argument("--no-local", action="store_true", help="skip the sliding-statistics form")
+    ap.add_argument("--no-weighted", action="store_true", help="skip the weighted (Eq. 1) form")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving form")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per offered-load level of the serving form")

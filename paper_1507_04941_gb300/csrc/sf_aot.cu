@@ -40,18 +40,21 @@ sf_window_stats_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int 
     const i64 x0 = (i64)a * wx, y0 = (i64)b * wy, z0 = (i64)e * wz;
     const int ex = (int)min((i64)wx, nx - x0), ey = (int)min((i64)wy, ny - y0),
               ez = (int)min((i64)wz, nz - z0);
-    const i64 n = (i64)ex * ey * ez;
     float K = 0.f, s1 = 0.f, s2 = 0.f, cnt = 0.f;
-    for (i64 i = threadIdx.x; i < n; i += kStatThreads) {
-        const int dz = (int)(i % ez);
-        const i64 r = i / ez;
-        const int dy = (int)(r % ey), dx = (int)(r / ey);
-        const float v = __ldg(c + ((x0 + dx) * ny + (y0 + dy)) * nz + (z0 + dz));
-        if (cnt == 0.f) K = v;
-        const float d = v - K;
-        s1 += d;
-        s2 = fmaf(d, d, s2);
-        cnt += 1.f;
+    /* warps over the window's (x, y) rows, lanes over z: coalesced, one
+     * division per row */
+    const int lane0 = threadIdx.x & 31, warp0 = threadIdx.x >> 5;
+    for (int row = warp0; row < ex * ey; row += kStatThreads / 32) {
+        const int dx = row / ey, dy = row - dx * ey;
+        const float *p = c + ((x0 + dx) * ny + (y0 + dy)) * nz + z0;
+        for (int dz = lane0; dz < ez; dz += 32) {
+            const float v = __ldg(p + dz);
+            if (cnt == 0.f) K = v;
+            const float d = v - K;
+            s1 += d;
+            s2 = fmaf(d, d, s2);
+            cnt += 1.f;
+        }
     }
     Mom m{0.f, 0.f, 0.f};
     if (cnt > 0.f) {
@@ -81,28 +84,34 @@ sf_window_stats_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int 
 
 constexpr int kThrThreads = 256;
 
-/* One warp per mask word: lane l tests voxel z = 32*word_z + l against
- * mean + k*std of its window and the warp ballot is the word. */
+/* One warp per (x, y) row, walking its mask words: lane l tests voxel
+ * z = 32*word + l against mean + k*std of its window and the warp ballot is
+ * the word (OR-ed into the word already there when accumulating). */
 __global__ void __launch_bounds__(kThrThreads)
 sf_threshold_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int wx, int wy, int wz,
                     int nwy, int nwz, const float *__restrict__ mean, const float *__restrict__ stdv,
-                    float k, unsigned int *__restrict__ mask, int accumulate, i64 nw32, i64 nwords)
+                    float k, unsigned int *__restrict__ mask, int accumulate, i64 nw32, i64 nrows)
 {
-    const i64 word = (i64)blockIdx.x * (kThrThreads / 32) + (threadIdx.x >> 5);
-    if (word >= nwords) return;
+    const i64 xy = (i64)blockIdx.x * (kThrThreads / 32) + (threadIdx.x >> 5);
+    if (xy >= nrows) return;
     const int lane = threadIdx.x & 31;
-    const i64 xy = word / nw32, zw = word % nw32;
-    const i64 x = xy / ny, y = xy % ny;
-    const i64 z = zw * 32 + lane;
-    bool fire = false;
-    if (z < nz) {
-        const float v = __ldg(c + xy * nz + z);
-        const i64 wi = ((x / wx) * nwy + y / wy) * nwz + z / wz;
-        const float T = fmaf(k, __ldg(stdv + wi), __ldg(mean + wi));
-        fire = v > T;
+    const i64 x = xy / ny, y = xy - x * ny;
+    const int wbase = (int)(((x / wx) * nwy + y / wy) * nwz);
+    const float *row = c + xy * nz;
+    unsigned int *mrow = mask + xy * nw32;
+    for (int zw = 0; zw < (int)nw32; ++zw) {
+        const int z = zw * 32 + lane;
+        bool fire = false;
+        if (z < nz) {
+            const int wi = wbase + z / wz;
+            fire = __ldg(row + z) > fmaf(k, __ldg(stdv + wi), __ldg(mean + wi));
+        }
+        const unsigned int bits = __ballot_sync(0xffffffffu, fire);
+        if (lane == 0) {
+            if (!accumulate) mrow[zw] = bits;
+            else if (bits) atomicOr(mrow + zw, bits);
+        }
     }
-    const unsigned int bits = __ballot_sync(0xffffffffu, fire);
-    if (lane == 0) mask[word] = accumulate ? (mask[word] | bits) : bits;
 }
 
 }  // namespace
@@ -123,11 +132,11 @@ cudaError_t sf_launch_threshold(const float *c, long long nx, long long ny, long
                                 cudaStream_t st)
 {
     const long long nw32 = (nz + 31) / 32;
-    const long long nwords = nx * ny * nw32;
+    const long long nrows = nx * ny;
     const long long per = kThrThreads / 32;
-    const long long blocks = (nwords + per - 1) / per;
+    const long long blocks = (nrows + per - 1) / per;
     sf_threshold_kernel<<<(unsigned)blocks, kThrThreads, 0, st>>>(c, nx, ny, nz, wx, wy, wz, nwy, nwz,
                                                                    mean, stdv, k, mask, accumulate,
-                                                                   nw32, nwords);
+                                                                   nw32, nrows);
     return cudaGetLastError();
 }
