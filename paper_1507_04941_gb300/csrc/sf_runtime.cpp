@@ -1785,7 +1785,8 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
      * compute streams, so one chunk's kernels fill the tail of the other's. */
     const long long wx = c->cfg.wx;
     const long long nx = c->cfg.nx;
-    long long S = (nx + 15) / 16;
+    const long long nch = std::max(1, std::min(256, env_int("SF_HCHUNKS", 16)));
+    long long S = (nx + nch - 1) / nch;
     S = std::max(wx, (S + wx - 1) / wx * wx);
     const int K = (int)((nx + S - 1) / S);
     int rxm = 0;
