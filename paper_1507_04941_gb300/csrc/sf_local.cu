@@ -130,9 +130,16 @@ __global__ void __launch_bounds__(kYZThreads) sf_local_yz(const float *__restric
     __syncthreads();
     /* y: output row i sums staged rows i .. i + 2 sy */
     constexpr int nseg_y = kYT / kYSeg;
+    /* clipped box counts factor into a y and a z part (32-bit) */
+    const int nyi = (int)ny, nzi = (int)nz;
+    auto cnt = [](int v, int h, int n) { return min(v + h, n - 1) - max(v - h, 0) + 1; };
     for (int task = threadIdx.x; task < kZT * nseg_y; task += kYZThreads) {
         const int j = task % kZT, i0 = (task / kZT) * kYSeg;
-        const i64 z = z0 + j;
+        const int z = (int)z0 + j;
+        const bool zin = z < nzi;
+        const float cz = (float)cnt(z, sz, nzi);
+        float *pa = A + (x * ny + y0 + i0) * nz + z;
+        float *pm = M + (x * ny + y0 + i0) * nz + z;
         float p = 0.f, q = 0.f;
 #pragma unroll 4
         for (int o = 0; o <= 2 * sy; ++o) {
@@ -151,14 +158,16 @@ __global__ void __launch_bounds__(kYZThreads) sf_local_yz(const float *__restric
                 p += Pz[(i + 2 * sy) * kPZ + j] - Pz[(i - 1) * kPZ + j];
                 q += Qz[(i + 2 * sy) * kPZ + j] - Qz[(i - 1) * kPZ + j];
             }
-            const i64 y = y0 + i;
-            if (y < ny && z < nz) {
-                const float n = (float)(clipped(y, sy, ny) * clipped(z, sz, nz));
-                A[(x * ny + y) * nz + z] = st + p / n;
+            const int y = (int)y0 + i;
+            if (y < nyi && zin) {
+                const float n = (float)cnt(y, sy, nyi) * cz;
+                *pa = st + p / n;
                 /* a rounded product (no contraction into an fma): for a
                  * one-voxel box q and p*p round alike and M is exactly 0 */
-                M[(x * ny + y) * nz + z] = fmaxf(q - __fmul_rn(p, p / n), 0.f);
+                *pm = fmaxf(q - __fmul_rn(p, p / n), 0.f);
             }
+            pa += nz;
+            pm += nz;
         }
     }
 }
@@ -177,7 +186,7 @@ struct Kahan {
 
 /* MODE 0: mean / std cubes; 1: mask words set; 2: mask words OR-ed */
 template <int MODE>
-__global__ void __launch_bounds__(kXThreads, 12)
+__global__ void __launch_bounds__(kXThreads, 10)
     sf_local_x(const float *__restrict__ c, const float *__restrict__ A, const float *__restrict__ M, i64 nx,
                i64 ny, i64 nz, i64 nw32, int sx, int sy, int sz, float k, float *__restrict__ mean,
                float *__restrict__ stdv, unsigned int *__restrict__ mask)
@@ -194,6 +203,7 @@ __global__ void __launch_bounds__(kXThreads, 12)
     const i64 off = y * nz + (valid ? z : 0);
     const float *pa = A + off, *pm = M + off, *pc = c + off;
     const float nyz = (float)(clipped(y, sy, ny) * clipped(z, sz, nz));
+    const int nxi = (int)nx;
     const i64 x0 = (i64)blockIdx.y * kXSeg;
     const i64 x1 = x0 + kXSeg < nx ? x0 + kXSeg : nx;
     /* segment blockIdx.y of kXSeg planes: the sums start from a direct sum
@@ -210,15 +220,25 @@ __global__ void __launch_bounds__(kXThreads, 12)
             sm.add(pm[xi * plane]);
         }
     }
+    /* pointers to the planes entering (x + sx) and leaving (x - sx - 1) the
+     * box, and to plane x; unused ones stay at plane 0 */
+    const float *ain_p = pa + (x0 + sx) * plane, *min_p = pm + (x0 + sx) * plane;
+    const float *aout_p = pa + (x0 - sx - 1) * plane, *mout_p = pm + (x0 - sx - 1) * plane;
+    const float *c_p = pc + x0 * plane;
 #pragma unroll 4
     for (i64 x = x0; x < x1; ++x) {
         /* the step's loads, unconditional (unused ones read plane 0) so they
          * issue together */
-        const i64 xin = x + sx, xout = x - sx - 1;
-        const bool hin = x > x0 && xin < nx, hout = x > x0 && xout >= 0;
-        const i64 oin = (hin ? xin : 0) * plane, oout = (hout ? xout : 0) * plane;
-        const float ain = pa[oin], min_ = pm[oin], aout = pa[oout], mout = pm[oout];
-        const float cv = MODE != 0 ? pc[x * plane] : 0.f;
+        const int xi = (int)x;
+        const bool hin = x > x0 && xi + sx < nxi, hout = x > x0 && xi - sx - 1 >= 0;
+        const float ain = hin ? ain_p[0] : pa[0], min_ = hin ? min_p[0] : pm[0];
+        const float aout = hout ? aout_p[0] : pa[0], mout = hout ? mout_p[0] : pm[0];
+        const float cv = MODE != 0 ? c_p[0] : 0.f;
+        ain_p += plane;
+        min_p += plane;
+        aout_p += plane;
+        mout_p += plane;
+        c_p += plane;
         if (hin) {
             const float d = ain - s;
             sa.add(d);
@@ -238,7 +258,7 @@ __global__ void __launch_bounds__(kXThreads, 12)
             mu = pa[x * plane];
             m2 = pm[x * plane];
         } else {
-            X = (float)clipped(x, sx, nx);
+            X = (float)(min(xi + sx, nxi - 1) - max(xi - sx, 0) + 1);
             const float da = sa.s / X;
             mu = s + da;
             /* a rounded product (no contraction into an fma) */
