@@ -429,6 +429,9 @@ sf_xpass_batch(const __grid_constant__ sf_xbargs a, const __grid_constant__ sfx_
 #ifndef SFD_X2
 #define SFD_X2 0
 #endif
+#ifndef SFD_WEIGHTED
+#define SFD_WEIGHTED 0   /* Eq. 1: inputs come as (denominator, numerator) pairs */
+#endif
 /* Prelude: SFD_WY, SFD_WZ (tile of one plane), SFD_P (z outputs per thread),
  * SFD_THREADS (= WY*WZ/P), SFD_NSRC, SFD_NZF, SFD_RYM, SFD_RZM, SFD_HZ (z halo,
  * multiple of 4 and of SFD_CH), SFD_CH (elements per cp.async, 0 = synchronous
@@ -883,6 +886,7 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr u32 FULL = SFD_P == 32 ? 0xffffffffu : ((1u << SFD_P) - 1u);
+    constexpr int NEXT = SFD_WEIGHTED ? IDX + 2 : IDX + 1;   /* the next input (pair) */
     const bool full = S.vmask == FULL;
     /* per-thread shifted sums: K = the thread's first value of the window */
     float K[SFD_NZF], s1[SFD_NZF], s2[SFD_NZF];
@@ -918,14 +922,38 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
         int np = -1;
         if (!pass2) np = p + 1 < S.npl ? p + 1 : -1;
         else np = next_flag(p);
+        float c[SFD_NZF][SFD_P];
+#if SFD_WEIGHTED
+        {
+            /* Eq. 1: the denominator source IDX, then the numerator source
+             * IDX+1 of the same plane, each through the buffer ring; the
+             * denominator's filtered values wait in registers */
+            const bool ok = sfw_wait_buf(S, b, false);
+            if (__syncthreads_or(!ok)) { S.dead = true; return; }
+            sfw_load<IDX + 1, RY>(a, mp, S, p, b ^ 1);
+            float cd[SFD_NZF][SFD_P];
+            sfw_plane<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(t, S, b, cd);
+            ++S.it;
+            const int b2 = b ^ 1;
+            const bool ok2 = sfw_wait_buf(S, b2, false);
+            if (__syncthreads_or(!ok2)) { S.dead = true; return; }
+            if (np >= 0) sfw_load<IDX, RY>(a, mp, S, np, b);
+            else if (pass2 && NEXT < SFD_NSRC) sfw_first_load<NEXT>(a, mp, S, b);
+            sfw_plane<IDX + 1, RY, NZ, RZ0, RZ1, RZ2, RZ3>(t, S, b2, c);
+#pragma unroll
+            for (int f = 0; f < NZ; ++f)
+#pragma unroll
+                for (int i = 0; i < SFD_P; ++i) c[f][i] = cd[f][i] != 0.f ? c[f][i] / cd[f][i] : 0.f;
+        }
+#else
         /* wait for this plane, then (everyone being past the previous plane)
          * start the next load into the other buffer */
         const bool ok = sfw_wait_buf(S, b, false);
         if (__syncthreads_or(!ok)) { S.dead = true; return; }
         if (np >= 0) sfw_load<IDX, RY>(a, mp, S, np, b ^ 1);
-        else if (pass2 && IDX + 1 < SFD_NSRC) sfw_first_load<IDX + 1>(a, mp, S, b ^ 1);
-        float c[SFD_NZF][SFD_P];
+        else if (pass2 && NEXT < SFD_NSRC) sfw_first_load<NEXT>(a, mp, S, b ^ 1);
         sfw_plane<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(t, S, b, c);
+#endif
         if (!pass2) {
             if (p == 0) {
 #pragma unroll
@@ -1040,7 +1068,7 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
             p = next_flag(-1);
             if (p < 0) {
                 /* nothing can be selected in this window for this input */
-                if (IDX + 1 < SFD_NSRC) sfw_first_load<IDX + 1>(a, mp, S, S.it & 1);
+                if (NEXT < SFD_NSRC) sfw_first_load<NEXT>(a, mp, S, S.it & 1);
                 return;
             }
             sfw_load<IDX, RY>(a, mp, S, p, S.it & 1);
@@ -1063,6 +1091,15 @@ SFD_SOURCES(SFW_FIRST)
 template <int IDX> __device__ __forceinline__ void sfw_first_load(const sf_dargs &, const sf_tmap *,
                                                                   sfw_state &, int)
 {
+}
+
+/* one input, or (Eq. 1) one (denominator, numerator) pair starting at an
+ * even index */
+template <int IDX, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
+__device__ __forceinline__ void sfw_run(const sf_dargs &a, const sfd_taps &t, const sf_tmap *mp,
+                                        sfw_state &S)
+{
+    if constexpr (SFD_WEIGHTED == 0 || IDX % 2 == 0) sfw_input<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(a, t, mp, S);
 }
 
 /* shared-memory carve-up, thread roles and barrier set-up (once per CTA) */
@@ -1128,7 +1165,7 @@ __device__ __forceinline__ bool sfw_window(const sf_dargs &a, const sfd_taps &t,
     sfw_first_load<0>(a, mp, S, 0);
 
 #define SFW_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                                 \
-    if (!S.dead) sfw_input<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(a, t, mp, S);
+    if (!S.dead) sfw_run<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(a, t, mp, S);
     SFD_SOURCES(SFW_RUN)
 #undef SFW_RUN
 

@@ -97,6 +97,7 @@ struct DetectSource {
     int slot;                     /* -1 = the cube itself */
     int ry;
     std::vector<int> filters;     /* <= nzf entries */
+    bool den = false;             /* Eq. 1 plans: the denominator of a (den, num) pair */
 };
 
 struct Launch {
@@ -253,6 +254,14 @@ struct sf_ctx {
     float *wscratch = nullptr;        /* weighted form: product, numerator, denominator */
     float *wstats = nullptr;          /* weighted form: window mean / std of one filter */
     sf_ctx *boxtwin = nullptr;        /* the bank's radii with unit taps (printed Eq. 1 denominator) */
+    sf_ctx *gausstwin = nullptr;      /* the same bank: its scratch holds the x-filtered weights */
+    struct WPlan {                    /* fused Eq. 1 window kernel, per denominator reading */
+        bool tried = false, ready = false, tma = false;
+        Launch L;
+        std::vector<float> taps;
+        std::vector<DetectSource> srcs;
+        std::vector<CUtensorMap> maps;
+    } wplan[2];
     std::vector<cudaEvent_t> hev;
 
     /* stage timing: pairs of events per recorded stage instance */
@@ -615,13 +624,25 @@ std::vector<DetectSource> window_sources(const sf_ctx *c)
 
 /* CH: elements per cp.async copy; tma_shape: halo and row pitch usable by TMA.
  * Returns false when the window shape cannot be tiled by the window code. */
-bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, WindowPlan &wp)
+bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, WindowPlan &wp,
+                      int weighted = -1)
 {
     const sf_config &g = c->cfg;
     if (g.wy % 8 != 0 || g.wz % 32 != 0 || g.wx > 64 || g.wz % (4 * P) != 0) return false;
     const long long threads = (long long)g.wy * g.wz / P;
     if (threads < 32 || threads > 1024) return false;
     wp.srcs = window_sources(c);
+    if (weighted >= 0) {
+        /* Eq. 1: each input becomes a (denominator, numerator) pair */
+        std::vector<DetectSource> pairs;
+        for (const DetectSource &d : wp.srcs) {
+            DetectSource den = d;
+            den.den = true;
+            pairs.push_back(den);
+            pairs.push_back(d);
+        }
+        wp.srcs.swap(pairs);
+    }
     if ((int)wp.srcs.size() > SF_MAX_SRC) return false;
     wp.P = P;
     wp.minb = minb;
@@ -689,8 +710,20 @@ bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, 
     p += "#define SFD_OFF_THR " + std::to_string(wp.off_th) + "\n";
     p += "#define SFD_OFF_FLAGS " + std::to_string(wp.off_fl) + "\n";
     p += "#define SFD_OFF_MBAR " + std::to_string(wp.off_mb) + "\n";
+    if (weighted >= 0) p += "#define SFD_WEIGHTED 1\n";
     wp.prelude = p;
     wp.taps = yz_taps(c, sh, wp.srcs);
+    if (weighted == 1) {
+        /* the printed denominator of Eq. 1 sums w alone: unit taps */
+        for (size_t i = 0; i < wp.srcs.size(); ++i) {
+            if (!wp.srcs[i].den) continue;
+            for (int j = 0; j <= wp.srcs[i].ry; ++j) wp.taps[i * (sh.RYM + 1) + j] = 1.f;
+            for (size_t q = 0; q < wp.srcs[i].filters.size(); ++q) {
+                float *gz = &wp.taps[sh.nsrc * (sh.RYM + 1) + (i * sh.nzf + q) * (sh.RZM + 1)];
+                for (int j = 0; j <= c->filt[wp.srcs[i].filters[q]].rz; ++j) gz[j] = 1.f;
+            }
+        }
+    }
     return true;
 }
 
@@ -1402,6 +1435,7 @@ sf_status sf_destroy(sf_ctx *c)
     cudaFree(c->wscratch);
     cudaFree(c->wstats);
     if (c->boxtwin) sf_destroy(c->boxtwin);
+    if (c->gausstwin) sf_destroy(c->gausstwin);
     for (cudaStream_t x : c->hcopy)
         if (x) cudaStreamDestroy(x);
     if (c->hback) cudaStreamDestroy(c->hback);
@@ -1958,6 +1992,51 @@ sf_status weighted_scratch(sf_ctx *c, int den)
     return SF_OK;
 }
 
+/* a twin of the context (same shape, bank and window): its scratch cubes
+ * hold the x-filtered weights of the fused Eq. 1 path */
+sf_status weighted_gauss_twin(sf_ctx *c)
+{
+    if (c->gausstwin) return SF_OK;
+    sf_config cfg = c->cfg;
+    std::vector<sf_filter_spec> specs;
+    for (const Filt &f : c->filt) specs.push_back(sf_filter_spec{f.sxy, f.sz});
+    cfg.filters = specs.data();
+    cfg.device = c->device;
+    sf_ctx *t = nullptr;
+    sf_status s = create_impl(&cfg, 0, nullptr, &t);
+    if (s != SF_OK) return fail(c, s, "twin context");
+    c->gausstwin = t;
+    return SF_OK;
+}
+
+/* the fused Eq. 1 window kernel for denominator reading den, built once;
+ * not ready when the window cannot be tiled (the composed path runs then) */
+sf_status weighted_plan(sf_ctx *c, int den)
+{
+    sf_ctx::WPlan &W = c->wplan[den];
+    if (W.tried) return SF_OK;
+    W.tried = true;
+    if (env_int("SF_WCOMPOSED", 0)) return SF_OK;
+    const sf_config &g = c->cfg;
+    WindowPlan wp;
+    if (!make_window_plan(c, 8, 2, copy_chunk(c->ebytes, g.nz), true, wp, den)) return SF_OK;
+    W.tma = tma_usable(c, wp, g.nz);
+    std::string p = "#define SF_KERNEL_DETECT 1\n" + wp.prelude;
+    p += std::string("#define SFD_TMA ") + (W.tma ? "1" : "0") + "\n";
+    std::string err;
+    sf_status s = jit_kernel(p, "sf_window_detect", c->device, &W.L.kernel, err);
+    if (s != SF_OK) return fail(c, s, "weighted window kernel: %s", err.c_str());
+    W.L.smem = wp.smem;
+    if (wp.smem > 48 * 1024 && (s = set_smem(c, W.L.kernel, wp.smem)) != SF_OK) return s;
+    W.L.block = dim3((unsigned)wp.threads);
+    W.L.grid = dim3((unsigned)c->nwin);
+    W.taps = wp.taps;
+    W.srcs = wp.srcs;
+    W.maps.assign(wp.srcs.size(), CUtensorMap{});
+    W.ready = true;
+    return SF_OK;
+}
+
 /* c = Eq. 1 for filter f of the bank, into out; p = d * w already formed */
 sf_status weighted_one(sf_ctx *c, const float *p, const float *d_w, int f, int den, float *out, cudaStream_t st)
 {
@@ -2003,6 +2082,49 @@ sf_status sf_weighted_detect(sf_ctx *c, const float *d_cube, const float *d_weig
     float *p = c->wscratch, *num = c->wscratch + cube;
     cudaError_t e = sf_launch_w_product(d_cube, d_weights, p, c->nvox, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "product launch");
+    if (c->fused && (s = weighted_plan(c, den)) != SF_OK) return s;
+    const sf_ctx::WPlan &W = c->wplan[den];
+    if (c->fused && W.ready && (den == 1 || (s = weighted_gauss_twin(c)) == SF_OK)) {
+        /* fused: x passes of d*w (this context's scratch) and of w (the
+         * twin's), then one window kernel over (denominator, numerator)
+         * pairs that divides before the moments */
+        sf_ctx *tw = den == 1 ? c->boxtwin : c->gausstwin;
+        for (size_t i = 0; i < c->xlaunch.size(); ++i)
+            if ((s = run_xpass(c, c->xlaunch[i], c->xgroups[i], p, st)) != SF_OK) return s;
+        for (size_t i = 0; i < tw->xlaunch.size(); ++i)
+            if ((s = run_xpass(tw, tw->xlaunch[i], tw->xgroups[i], d_weights, st)) != SF_OK)
+                return fail(c, s, "%s", tw->err.c_str());
+        sf_dargs da{};
+        sf_ctx::WPlan &Wm = c->wplan[den];
+        for (size_t i = 0; i < W.srcs.size(); ++i) {
+            const DetectSource &d = W.srcs[i];
+            const void *src = d.den ? (d.slot < 0 ? (const void *)d_weights
+                                                  : (const void *)((const char *)tw->scratch + (size_t)d.slot * tw->cube_bytes))
+                                    : (d.slot < 0 ? (const void *)p
+                                                  : (const void *)((const char *)c->scratch + (size_t)d.slot * c->cube_bytes));
+            da.src[i] = src;
+            for (size_t q = 0; q < d.filters.size(); ++q) da.fidx[i][q] = d.filters[q];
+            if (W.tma && !encode_map_dims(c, src, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->dSROW, d.ry, &Wm.maps[i]))
+                return fail(c, SF_ECUDA, "tensor map encoding failed");
+        }
+        da.mask = d_mask;
+        da.mean = d_mean;
+        da.stdv = d_std;
+        da.nx = c->cfg.nx;
+        da.ny = c->cfg.ny;
+        da.nz = c->cfg.nz;
+        da.nw32 = c->nw32;
+        da.nwx = c->nwx;
+        da.nwy = c->nwy;
+        da.nwz = c->nwz;
+        da.nwin = c->nwin;
+        da.k = c->cfg.k;
+        da.err = c->err_flag;
+        da.wid0 = 0;
+        void *args[] = {&da, (void *)W.taps.data(), (void *)Wm.maps.data()};
+        return launch(c, W.L, args, st, "weighted window kernel launch");
+    }
+    if (s != SF_OK) return s;
     for (int f = 0; f < (int)c->filt.size(); ++f) {
         /* the ratio overwrites the numerator in place */
         if ((s = weighted_one(c, p, d_weights, f, den, num, st)) != SF_OK) return s;

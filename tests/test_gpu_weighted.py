@@ -121,3 +121,29 @@ def test_weighted_full_tile_sampled(dev, oracle):
                     ref = oracle.weighted_filter_box(dn, wn, sxy, sz, wk.truncation, den, box)[0, 0, 0]
                     A = oracle.weighted_filter_box(np.abs(dn), wn, sxy, sz, wk.truncation, den, box)[0, 0, 0]
                     assert abs(g[x, y, z] - ref) <= 1e-5 * max(abs(ref), A), (f, den, x, y, z)
+
+
+@pytest.mark.parametrize("composed,shape", [(True, (40, 36, 100)), (False, (24, 32, 70))])
+def test_weighted_detect_paths(dev, oracle, monkeypatch, composed, shape):
+    """The composed path (forced) and the fused kernel's cp.async slabs
+    (nz % 4 != 0) against the oracle."""
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder, words_to_bits
+    if composed:
+        monkeypatch.setenv("SF_WCOMPOSED", "1")
+    window, k = (16, 16, 32), 3.0
+    d, w = _inputs(shape, 55)
+    for den in ("fw", "w"):
+        with SourceFinder(shape, BANK6, 3.0, window, k=k, device=dev) as sf:
+            mask, mean, std = sf.weighted_detect(d.to(dev), w.to(dev), den, stats=True)
+            torch.cuda.synchronize(dev)
+            got = words_to_bits(mask.cpu().numpy(), shape[2])
+            gm, gs = mean.cpu().numpy(), std.cpu().numpy()
+        ref = oracle.weighted_detect(d.numpy(), w.numpy(), BANK6, 3.0, window, k, den)
+        want = oracle.unpack_bits(ref["mask"], shape[2])
+        sure = oracle.unpack_bits(ref["sure"], shape[2])
+        diff = (got != want) & sure
+        assert not diff.any(), f"den={den}: {int(diff.sum())} certain mask bits differ"
+        scale = np.maximum(ref["std"], np.abs(ref["mean"]))
+        assert (np.abs(gm - ref["mean"]) <= 1e-5 * scale).all(), den
+        assert (np.abs(gs - ref["std"]) <= 1e-5 * scale).all(), den
