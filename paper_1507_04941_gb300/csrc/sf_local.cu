@@ -6,19 +6,24 @@
  * box; population statistics.  The box sums are separable, as in the paper's
  * three directional sums:
  *
- *   sf_local_yz  one CTA per (x, 32-row, 64-column) tile: the tile with its y
- *                and z halo is staged in shared memory, shifted by one of its
- *                values s_t (entries outside the cube are 0: they are not in
- *                any box); box sums of (c - s_t) and (c - s_t)^2 along z and
- *                then along y are formed as running sums restarted every 16
- *                outputs (direct sums per output for half-widths up to 16),
- *                and each voxel's y-z box mean A and second central
- *                moment M = sum (c - A)^2 are written as two float32 cubes;
- *   sf_local_x   one thread per (y, z) and 32-plane x segment, marching along
- *                x with compensated (Kahan) running sums over the x box of
- *                (A - s), (A - s)^2 and M, started from a direct sum with s
- *                the segment's first A; the box statistics then
- *                follow from the parallel-axis rule
+ *   sf_local_yz  one CTA per (x, 128-column z tile, y segment of up to 256
+ *                rows) marching along y in steps of 16 rows.  Each step
+ *                stages 16 rows of the tile with their z halo (cp.async, zeros
+ *                outside the cube), forms the z box sums of (c - s) and
+ *                (c - s)^2 of every row (s: one value of the data near the
+ *                segment's centre) as running sums over 16-column segments
+ *                started from 16-column block sums, and pushes them into a
+ *                ring of the last 2 sy + 17 rows.  The y box sums run down
+ *                the ring, one thread per column, restarted from a direct sum
+ *                every 16 rows.  Each voxel's y-z box mean A and second central
+ *                moment M = sum (c - A)^2 are written as two float32 cubes.
+ *                Half-widths up to 2 use direct sums for every output, so that
+ *                a one-voxel box gives M = 0 exactly;
+ *   sf_local_x   one thread per (y, z) and x segment, marching along x with
+ *                compensated (Kahan) running sums over the x box of (A - s),
+ *                (A - s)^2 and M, started from a direct sum with s the
+ *                segment's first A; the box statistics then follow from the
+ *                parallel-axis rule
  *                  mean = s + sum(A - s)/X,
  *                  M2   = sum M + n_yz (sum (A - s)^2 - (sum (A - s))^2 / X)
  *                (X planes of n_yz voxels each), var = M2 / (X n_yz); either
@@ -35,140 +40,357 @@ namespace {
 
 typedef long long i64;
 
-constexpr int kYT = 32;          /* tile rows (y) */
-constexpr int kZT = 64;          /* tile columns (z) */
-constexpr int kPZ = kZT + 1;     /* row stride of the z sums (odd: conflict-free) */
-constexpr int kSeg = 16;         /* outputs per running-sum segment */
 constexpr int kDirect = 2;       /* half-widths up to this: direct sums per output */
-constexpr int kYSeg = 8;         /* rows per y running-sum segment */
-constexpr int kYZThreads = 256;
 constexpr int kXThreads = 128;
-constexpr int kXSeg = 32;        /* x planes per re-anchored segment */
+constexpr int kXSeg = 128;       /* x planes per re-anchored segment */
 
-__host__ __device__ inline int stage_cols(int sz) { return (kZT + 2 * sz) | 1; }   /* odd: fewer bank conflicts */
+/* ---- y-z box sums ---- */
+constexpr int kMZ = 128;         /* output columns per CTA */
+constexpr int kMT = 256;         /* threads: two per column (one per sum) */
+constexpr int kRB = 16;          /* rows per step */
+constexpr int kBS = 16;          /* z block and segment length */
+constexpr int kRS = kMZ + 4;     /* ring row stride: 33 quads (odd) */
+constexpr int kYRows = 256;      /* output rows per CTA at most */
+
+/* staged row stride: columns up to 131 + 2 sz are read, in float4 quads; an
+ * odd number of quads keeps eight rows' quads in distinct banks */
+__host__ __device__ inline int yz_sw(int sz)
+{
+    int w = (132 + 2 * sz + 3) & ~3;
+    if (((w >> 2) & 1) == 0) w += 4;
+    return w;
+}
+/* 16-column block sums per row: the anchors of segments 0..7 span blocks
+ * 0 .. 7 + nf - 1 */
+__host__ __device__ inline int yz_nbk(int sz)
+{
+    const int nf = (2 * sz + 1) / kBS;
+    return sz <= kDirect || nf == 0 ? 0 : kMZ / kBS - 1 + nf;
+}
+__host__ __device__ inline int yz_ring(int sy) { return 2 * sy + 1 + kRB; }
+/* the Q ring starts 16 banks after the P ring, so that a warp reading one row
+ * of P (lanes 0-15) and of Q (lanes 16-31) hits 32 distinct banks */
+__host__ __device__ inline int yz_qpad(int sy) { return (16 - (yz_ring(sy) * kRS) % 32 + 32) % 32; }
+__host__ __device__ inline size_t yz_smem_floats(int sy, int sz)
+{
+    return (size_t)kRB * yz_sw(sz) + 2 * (size_t)yz_nbk(sz) * kRB + 2 * (size_t)yz_ring(sy) * kRS + yz_qpad(sy);
+}
 
 __device__ __forceinline__ i64 clipped(i64 v, int h, i64 n)
 {
     const i64 lo = v - h < 0 ? 0 : v - h, hi = v + h >= n ? n - 1 : v + h;
     return hi - lo + 1;
 }
+__device__ __forceinline__ int clipped32(int v, int h, int n) { return min(v + h, n - 1) - max(v - h, 0) + 1; }
 
-__global__ void __launch_bounds__(kYZThreads) sf_local_yz(const float *__restrict__ c, float *__restrict__ A,
-                                                        float *__restrict__ M, i64 nx, i64 ny, i64 nz, int sy,
-                                                        int sz)
+__device__ __forceinline__ void ld4(const float *p, float *v)
 {
-    extern __shared__ float sm[];
-    const int rows = kYT + 2 * sy, cols = stage_cols(sz);
-    float *T = sm;                       /* [rows][cols] staged c - s_t */
-    float *Pz = T + rows * cols;         /* [rows][kPZ] z box sums of c - s_t */
-    float *Qz = Pz + rows * kPZ;         /* [rows][kPZ] z box sums of (c - s_t)^2 */
-    const i64 x = blockIdx.z, y0 = (i64)blockIdx.y * kYT, z0 = (i64)blockIdx.x * kZT;
-    (void)nx;
-    /* the tile's shift: the value nearest its centre inside the cube */
-    const i64 yc = min(ny - 1, y0 + kYT / 2), zc = min(nz - 1, z0 + kZT / 2);
-    const float st = c[(x * ny + yc) * nz + zc];
-    /* staging by cp.async (4 bytes, zero fill outside the cube), then each
-     * thread shifts the elements its own copies wrote */
-    const unsigned int tbase = (unsigned int)__cvta_generic_to_shared(T);
-    for (int r = threadIdx.x >> 5; r < rows; r += kYZThreads / 32) {
-        const i64 y = y0 - sy + r;
-        const bool yin = y >= 0 && y < ny;
-        const float *src = c + (x * ny + (yin ? y : 0)) * nz;
-        for (int q = threadIdx.x & 31; q < cols; q += 32) {
-            const i64 z = z0 - sz + q;
-            const bool in = yin && z >= 0 && z < nz && q < kZT + 2 * sz;
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(tbase + 4u * (unsigned)(r * cols + q)),
-                         "l"(in ? src + z : c), "r"(in ? 4 : 0)
-                         : "memory");
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+__device__ __forceinline__ void st4(float *p, const float *v)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+/* term of the sums: SQ 0 -> d, 1 -> d^2, added to acc */
+template <int SQ>
+__device__ __forceinline__ float yz_add(float acc, float d)
+{
+    return SQ ? fmaf(d, d, acc) : acc + d;
+}
+
+/* one z sum (SQ 0: of c - s, 1: of (c - s)^2) of one staged row for outputs
+ * j0 .. j0+15 into the ring row.  SH = (2 sz + 1) mod 4 places the entering
+ * columns j + 2 sz inside the float4 quads loaded from the aligned column
+ * j0 + 2 sz + 1 - SH. */
+template <bool SHIFTED, int SH, int SQ>
+__device__ __forceinline__ void yz_segment(const float *__restrict__ u, const float2 *__restrict__ bs, float *ring,
+                                           int j0, int nf, int rem, int sz, float s)
+{
+    const float s0 = SHIFTED ? 0.f : s;
+    float acc = 0.f;
+    for (int k = 0; k < nf; ++k) {
+        const float2 b = bs[k * kRB];
+        acc += SQ ? b.y : b.x;
+    }
+    /* the box's last rem columns after the full blocks (rem odd, <= 15) */
+    const float *rp = u + j0 + kBS * nf;
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+        if (4 * ch < rem) {
+            float v[4];
+            ld4(rp + 4 * ch, v);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (4 * ch + i < rem) acc = yz_add<SQ>(acc, v[i] - s0);
         }
     }
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-    for (int r = threadIdx.x >> 5; r < rows; r += kYZThreads / 32) {
-        const i64 y = y0 - sy + r;
-        const bool yin = y >= 0 && y < ny;
-        for (int q = threadIdx.x & 31; q < cols; q += 32) {
-            const i64 z = z0 - sz + q;
-            if (yin && z >= 0 && z < nz && q < kZT + 2 * sz) T[r * cols + q] -= st;
+    float L[16], E[20];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) ld4(u + j0 + 4 * i, L + 4 * i);
+    const float *ep = u + j0 + (2 * sz + 1 - SH);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ld4(ep + 4 * i, E + 4 * i);
+    float o4[4];
+    o4[0] = acc;
+#pragma unroll
+    for (int i = 1; i < 16; ++i) {
+        const float vin = E[SH - 1 + i] - s0, vout = L[i - 1] - s0;
+        if (SQ) acc = fmaf(-vout, vout, fmaf(vin, vin, acc));
+        else acc += vin - vout;
+        o4[i & 3] = acc;
+        if ((i & 3) == 3) st4(ring + j0 + i - 3, o4);
+    }
+}
+
+/* short boxes (sz <= kDirect): a direct sum for every output */
+template <bool SHIFTED, int SQ>
+__device__ __forceinline__ void yz_segment_direct(const float *__restrict__ u, float *ring, int j0, int sz, float s)
+{
+    const float s0 = SHIFTED ? 0.f : s;
+    float v[20];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) ld4(u + j0 + 4 * i, v + 4 * i);
+    float o4[4];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        float acc = 0.f;
+#pragma unroll
+        for (int o = 0; o <= 2 * kDirect; ++o)
+            if (o <= 2 * sz) acc = yz_add<SQ>(acc, v[i + o] - s0);
+        o4[i & 3] = acc;
+        if ((i & 3) == 3) st4(ring + j0 + i - 3, o4);
+    }
+}
+
+template <bool SHIFTED, int SQ>
+__device__ __forceinline__ void yz_task(const float *u, const float2 *bs, float *ring, int j0, int nf, int rem,
+                                        int sz, int sh, float s)
+{
+    if (sz <= kDirect) yz_segment_direct<SHIFTED, SQ>(u, ring, j0, sz, s);
+    else if (sh == 1) yz_segment<SHIFTED, 1, SQ>(u, bs, ring, j0, nf, rem, sz, s);
+    else yz_segment<SHIFTED, 3, SQ>(u, bs, ring, j0, nf, rem, sz, s);
+}
+
+struct YzGeom {
+    const float *c;
+    i64 plane0;          /* offset of plane x */
+    int ny, nz;          /* extents (the launcher checks they fit 31 bits) */
+    int sy, sz, SW, NBK, RING, nf, rem, sh;
+    int ys, zst, zt0;    /* first output row, first staged column, first output column */
+    int nout, NR;        /* output rows, staged rows (nout + 2 sy) */
+};
+
+/* stage rows rr0 .. rr0+15 of the segment (y = ys - sy + rr) into U:
+ * CH-element cp.async chunks, zero-filled past the cube's z range (EDGE
+ * tiles only); rows outside the cube are left as they are (their ring rows
+ * are set to 0) */
+template <int CH, bool EDGE>
+__device__ __forceinline__ void yz_stage(float *U, const YzGeom &g, int rr0)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned int ub = (unsigned int)__cvta_generic_to_shared(U);
+    for (int r = threadIdx.x >> 5; r < kRB; r += kMT / 32) {
+        const int rr = rr0 + r;
+        const int y = g.ys - g.sy + rr;
+        if (rr >= g.NR || y < 0 || y >= g.ny) continue;
+        const float *row = g.c + g.plane0 + (i64)y * g.nz + g.zst;   /* staged column 0 */
+        for (int ch = lane; ch < g.SW / CH; ch += 32) {
+            const int q = ch * CH;
+            unsigned int bytes = 4u * CH;
+            const float *src = row + q;
+            if (EDGE) {
+                const int z = g.zst + q, left = g.nz - z;
+                bytes = z >= 0 && left > 0 ? 4u * (unsigned int)(left < CH ? left : CH) : 0u;
+                if (!bytes) src = g.c;
+            }
+            const unsigned int dst = ub + 4u * (unsigned int)(r * g.SW + q);
+            if constexpr (CH == 4)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
+                             : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(src), "r"(bytes)
+                             : "memory");
         }
     }
-    __syncthreads();
-    /* z: output column j of staged row r sums staged columns j .. j + 2 sz */
-    constexpr int nseg_z = kZT / kSeg;
-    for (int task = threadIdx.x; task < rows * nseg_z; task += kYZThreads) {
-        /* consecutive lanes take consecutive rows: with an odd row stride the
-         * shared loads of a warp hit 32 different banks */
-        const int seg = task / rows, r = task - seg * rows, j0 = seg * kSeg;
-        const float *row = T + r * cols;
-        float p = 0.f, q = 0.f;
-#pragma unroll 4
-        for (int o = 0; o <= 2 * sz; ++o) {
-            const float v = row[j0 + o];
-            p += v;
-            q = fmaf(v, v, q);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+/* after the copies landed: subtract s from the staged values inside the cube
+ * (each thread the chunks its own copies wrote); zeros stay zeros */
+template <int CH>
+__device__ __forceinline__ void yz_shift(float *U, const YzGeom &g, int rr0, float s)
+{
+    const int lane = threadIdx.x & 31;
+    for (int r = threadIdx.x >> 5; r < kRB; r += kMT / 32) {
+        const int rr = rr0 + r;
+        const int y = g.ys - g.sy + rr;
+        if (rr >= g.NR || y < 0 || y >= g.ny) continue;
+        for (int ch = lane; ch < g.SW / CH; ch += 32) {
+            const int z = g.zst + ch * CH;
+#pragma unroll
+            for (int e = 0; e < CH; ++e)
+                if (z + e >= 0 && z + e < g.nz) U[r * g.SW + ch * CH + e] -= s;
         }
-        Pz[r * kPZ + j0] = p;
-        Qz[r * kPZ + j0] = q;
-        for (int j = j0 + 1; j < j0 + kSeg; ++j) {
-            if (sz <= kDirect) {
-                /* short boxes: a direct sum per output (exact for one voxel) */
-                p = 0.f;
-                q = 0.f;
-                for (int o = 0; o <= 2 * sz; ++o) {
-                    const float v = row[j + o];
-                    p += v;
-                    q = fmaf(v, v, q);
+    }
+}
+
+/* EDGE: some staged columns lie outside the cube; the staged values are then
+ * shifted in place, otherwise s is subtracted as they are read */
+template <int CH, bool EDGE>
+__device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict__ M, const YzGeom &g, float s,
+                                        float *sm)
+{
+    float *U = sm;                                              /* [kRB][SW] staged rows */
+    float2 *Bs = reinterpret_cast<float2 *>(U + kRB * g.SW);    /* [NBK][kRB] block sums */
+    float *P = U + kRB * g.SW + 2 * g.NBK * kRB;                /* [RING][kRS] z sums of c - s */
+    float *Q = P + g.RING * kRS + yz_qpad(g.sy);                /* [RING][kRS] z sums of (c - s)^2 */
+    const int t = threadIdx.x, lane = t & 31;
+    const bool direct_y = g.sy <= kDirect;
+    /* y march: lanes 0-15 of warp w carry the sum of c - s, lanes 16-31 the
+     * sum of (c - s)^2, of column 16 w + (lane & 15) */
+    const int col = 16 * (t >> 5) + (lane & 15), sq = lane >> 4;
+    const float *ring = sq ? Q : P;
+    const int z = g.zt0 + col;
+    const bool zok = z >= 0 && z < g.nz;
+    const float rcz = zok ? 1.f / (float)clipped32(z, g.sz, g.nz) : 1.f;
+    const int cy_full = 2 * g.sy + 1;
+    const float rcy_full = 1.f / (float)cy_full;
+    float *out = (sq ? M : A) + g.plane0 + (i64)g.ys * g.nz + z;
+    const int nsteps = (g.NR + kRB - 1) / kRB;
+    float acc = 0.f;   /* this lane's y box sum of the current output row */
+    if (EDGE) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        yz_shift<CH>(U, g, 0, s);
+    }
+    for (int b = 0; b < nsteps; ++b) {
+        const int rr0 = b * kRB;
+        __syncthreads();   /* U holds this step's rows; the ring reads of the last step are done */
+        if (g.NBK > 0) {
+            const float s0 = EDGE ? 0.f : s;
+            for (int task = t; task < g.NBK * kRB; task += kMT) {
+                const int k = task >> 4, r = task & 15;
+                const float *u = U + r * g.SW + kBS * k;
+                float pa2[2] = {0.f, 0.f}, qa2[2] = {0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float v[4];
+                    ld4(u + 4 * i, v);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float d = v[e] - s0;
+                        pa2[e & 1] += d;
+                        qa2[e & 1] = fmaf(d, d, qa2[e & 1]);
+                    }
                 }
+                Bs[task] = make_float2(pa2[0] + pa2[1], qa2[0] + qa2[1]);
+            }
+        }
+        __syncthreads();
+        {
+            /* z sums: task (row r, segment gi), warps 0-3 the sums of c - s and
+             * warps 4-7 those of (c - s)^2; the eight lanes of a float4 phase
+             * hold eight rows of one segment */
+            const int task = t & 127, r = task & 15, gi = task >> 4, j0 = kBS * gi;
+            const int rr = rr0 + r;
+            const int y = g.ys - g.sy + rr;
+            int slot = rr0 % g.RING + r;
+            if (slot >= g.RING) slot -= g.RING;
+            const bool qsum = t >= 128;
+            float *rw = (qsum ? Q : P) + slot * kRS;
+            if (rr >= g.NR || y < 0 || y >= g.ny) {
+                const float zero[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) st4(rw + j0 + 4 * i, zero);
             } else {
-                const float vin = row[j + 2 * sz], vout = row[j - 1];
-                p += vin - vout;
-                q = fmaf(-vout, vout, fmaf(vin, vin, q));
+                const float *u = U + r * g.SW;
+                const float2 *bs = Bs + gi * kRB + r;
+                if (qsum) yz_task<EDGE, 1>(u, bs, rw, j0, g.nf, g.rem, g.sz, g.sh, s);
+                else yz_task<EDGE, 0>(u, bs, rw, j0, g.nf, g.rem, g.sz, g.sh, s);
             }
-            Pz[r * kPZ + j] = p;
-            Qz[r * kPZ + j] = q;
+        }
+        __syncthreads();   /* U is free; the ring holds this step's rows */
+        if (b + 1 < nsteps) yz_stage<CH, EDGE>(U, g, rr0 + kRB);
+        /* y sums down the ring for the outputs whose last box row arrived */
+        int si = rr0 % g.RING;   /* slot of staged row rr */
+        const int rend = min(kRB, g.NR - rr0);
+        for (int r = 0; r < rend; ++r) {
+            const int o = rr0 + r - 2 * g.sy;
+            if (o >= 0) {
+                if (direct_y || (o & 15) == 0) {
+                    int sl = si + kRB + 1;   /* slot of row o = rr - 2 sy */
+                    if (sl >= g.RING) sl -= g.RING;
+                    /* rows sl .. RING-1, then 0 .. (wrapped part) */
+                    const int n1 = min(cy_full, g.RING - sl);
+                    acc = 0.f;
+                    for (int i = 0; i < n1; ++i) acc += ring[(sl + i) * kRS + col];
+                    for (int i = 0; i < cy_full - n1; ++i) acc += ring[i * kRS + col];
+                } else {
+                    int so = si + kRB;       /* slot of row o - 1 */
+                    if (so >= g.RING) so -= g.RING;
+                    acc += ring[si * kRS + col] - ring[so * kRS + col];
+                }
+                const float p = __shfl_sync(0xffffffffu, acc, lane & 15);
+                const float q = __shfl_sync(0xffffffffu, acc, (lane & 15) + 16);
+                if (zok) {
+                    const int y = g.ys + o;
+                    const int cy = clipped32(y, g.sy, g.ny);
+                    const float rn = (cy == cy_full ? rcy_full : 1.f / (float)cy) * rcz;
+                    const float da = p * rn;
+                    /* a rounded product (no contraction into an fma): for a
+                     * one-voxel box q and p*p round alike and M is exactly 0 */
+                    out[(i64)o * g.nz] = sq ? fmaxf(q - __fmul_rn(p, da), 0.f) : s + da;
+                }
+            }
+            if (++si == g.RING) si = 0;
+        }
+        if (b + 1 < nsteps) {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+            if (EDGE) yz_shift<CH>(U, g, rr0 + kRB, s);
         }
     }
-    __syncthreads();
-    /* y: output row i sums staged rows i .. i + 2 sy */
-    constexpr int nseg_y = kYT / kYSeg;
-    /* clipped box counts factor into a y and a z part (32-bit) */
-    const int nyi = (int)ny, nzi = (int)nz;
-    auto cnt = [](int v, int h, int n) { return min(v + h, n - 1) - max(v - h, 0) + 1; };
-    for (int task = threadIdx.x; task < kZT * nseg_y; task += kYZThreads) {
-        const int j = task % kZT, i0 = (task / kZT) * kYSeg;
-        const int z = (int)z0 + j;
-        const bool zin = z < nzi;
-        const float cz = (float)cnt(z, sz, nzi);
-        float *pa = A + (x * ny + y0 + i0) * nz + z;
-        float *pm = M + (x * ny + y0 + i0) * nz + z;
-        float p = 0.f, q = 0.f;
-#pragma unroll 4
-        for (int o = 0; o <= 2 * sy; ++o) {
-            p += Pz[(i0 + o) * kPZ + j];
-            q += Qz[(i0 + o) * kPZ + j];
-        }
-        for (int i = i0; i < i0 + kYSeg; ++i) {
-            if (i > i0 && sy <= kDirect) {
-                p = 0.f;
-                q = 0.f;
-                for (int o = 0; o <= 2 * sy; ++o) {
-                    p += Pz[(i + o) * kPZ + j];
-                    q += Qz[(i + o) * kPZ + j];
-                }
-            } else if (i > i0) {
-                p += Pz[(i + 2 * sy) * kPZ + j] - Pz[(i - 1) * kPZ + j];
-                q += Qz[(i + 2 * sy) * kPZ + j] - Qz[(i - 1) * kPZ + j];
-            }
-            const int y = (int)y0 + i;
-            if (y < nyi && zin) {
-                const float n = (float)cnt(y, sy, nyi) * cz;
-                *pa = st + p / n;
-                /* a rounded product (no contraction into an fma): for a
-                 * one-voxel box q and p*p round alike and M is exactly 0 */
-                *pm = fmaxf(q - __fmul_rn(p, p / n), 0.f);
-            }
-            pa += nz;
-            pm += nz;
-        }
+}
+
+template <int CH>
+__global__ void __launch_bounds__(kMT) sf_local_yz(const float *__restrict__ c, float *__restrict__ A,
+                                                   float *__restrict__ M, i64 ny, i64 nz, int sy, int sz, int yrows)
+{
+    extern __shared__ __align__(16) float sm[];
+    YzGeom g;
+    g.c = c;
+    g.ny = (int)ny;
+    g.nz = (int)nz;
+    g.plane0 = (i64)blockIdx.z * ny * nz;
+    g.sy = sy;
+    g.sz = sz;
+    g.SW = yz_sw(sz);
+    g.NBK = yz_nbk(sz);
+    g.RING = yz_ring(sy);
+    g.nf = (2 * sz + 1) / kBS;
+    g.rem = 2 * sz + 1 - kBS * g.nf;
+    g.sh = (2 * sz + 1) & 3;
+    const int hz = (sz + 3) & ~3;
+    g.ys = (int)blockIdx.y * yrows;
+    g.nout = min(g.ny - g.ys, yrows);
+    if (g.nout <= 0) return;   /* whole CTA: before any barrier */
+    g.NR = g.nout + 2 * sy;
+    g.zst = (int)blockIdx.x * kMZ - hz;      /* 16-byte aligned first staged column */
+    g.zt0 = g.zst + sz;                      /* first output column */
+    /* the segment's shift: a value of the data near its centre */
+    const int yc = g.ys + g.nout / 2, zc = min(g.nz - 1, max(g.zt0 + kMZ / 2, 0));
+    const float s = c[g.plane0 + (i64)yc * g.nz + zc];
+    if (g.zst >= 0 && g.zst + g.SW <= g.nz) {
+        /* interior tile: every staged value is data; subtract s on the fly */
+        yz_stage<CH, false>(sm, g, 0);
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        yz_body<CH, false>(A, M, g, s, sm);
+    } else {
+        yz_stage<CH, true>(sm, g, 0);
+        yz_body<CH, true>(A, M, g, s, sm);
     }
 }
 
@@ -287,20 +509,28 @@ __global__ void __launch_bounds__(kXThreads, 10)
 }  // namespace
 
 /* shared memory of sf_local_yz for half-widths (sy, sz) */
-size_t sf_local_yz_smem(int sy, int sz)
-{
-    const size_t rows = (size_t)kYT + 2 * (size_t)sy;
-    return sizeof(float) * rows * ((size_t)stage_cols(sz) + 2 * kPZ);
-}
+size_t sf_local_yz_smem(int sy, int sz) { return sizeof(float) * yz_smem_floats(sy, sz); }
 
 cudaError_t sf_launch_local_yz(const float *c, float *A, float *M, long long nx, long long ny, long long nz, int sy,
                                int sz, cudaStream_t st)
 {
+    if (ny > (1LL << 30) || nz > (1LL << 30)) return cudaErrorInvalidValue;
     const size_t smem = sf_local_yz_smem(sy, sz);
-    cudaError_t e = cudaFuncSetAttribute(sf_local_yz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const dim3 grid((unsigned)((nz + kZT - 1) / kZT), (unsigned)((ny + kYT - 1) / kYT), (unsigned)nx);
-    sf_local_yz<<<grid, kYZThreads, smem, st>>>(c, A, M, nx, ny, nz, sy, sz);
+    /* y segments of at most kYRows rows, split evenly */
+    const long long nseg = (ny + kYRows - 1) / kYRows;
+    const int yrows = (int)((ny + nseg - 1) / nseg);
+    const int hz = (sz + 3) & ~3;
+    const dim3 grid((unsigned)((nz + hz - sz + kMZ - 1) / kMZ), (unsigned)nseg, (unsigned)nx);
+    cudaError_t e;
+    if (nz % 4 == 0) {
+        e = cudaFuncSetAttribute(sf_local_yz<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        sf_local_yz<4><<<grid, kMT, smem, st>>>(c, A, M, ny, nz, sy, sz, yrows);
+    } else {
+        e = cudaFuncSetAttribute(sf_local_yz<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        sf_local_yz<1><<<grid, kMT, smem, st>>>(c, A, M, ny, nz, sy, sz, yrows);
+    }
     return cudaGetLastError();
 }
 

@@ -41,7 +41,9 @@ def _assert_stats(gm, gs, rm, rs, rel=1e-5, what=""):
                                         ((9, 7, 5), (2, 3, 1)),          # smaller than one tile
                                         ((20, 80, 200), (3, 40, 100)),   # big y/z box: deep halo
                                         ((12, 33, 65), (0, 0, 0)),       # the voxel itself
-                                        ((6, 40, 70), (9, 50, 90))])     # box wider than the cube
+                                        ((6, 40, 70), (9, 50, 90)),      # box wider than the cube
+                                        ((6, 40, 520), (2, 5, 20)),      # interior z tiles
+                                        ((3, 300, 136), (1, 7, 4))])     # two y segments
 def test_local_stats_parity(dev, oracle, shape, half):
     import torch
     from paper_1507_04941_gb300 import SourceFinder
