@@ -257,9 +257,9 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
     const float *ring = sq ? Q : P;
     const int z = g.zt0 + col;
     const bool zok = z >= 0 && z < g.nz;
-    const float rcz = zok ? 1.f / (float)clipped32(z, g.sz, g.nz) : 1.f;
+    const float rcz = zok ? __frcp_rn((float)clipped32(z, g.sz, g.nz)) : 1.f;
     const int cy_full = 2 * g.sy + 1;
-    const float rcy_full = 1.f / (float)cy_full;
+    const float rn_full = rcz * __frcp_rn((float)cy_full);
     float *out = (sq ? M : A) + g.plane0 + (i64)g.ys * g.nz + z;
     const int nsteps = (g.NR + kRB - 1) / kRB;
     float acc = 0.f;   /* this lane's y box sum of the current output row */
@@ -315,38 +315,44 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
         }
         __syncthreads();   /* U is free; the ring holds this step's rows */
         if (b + 1 < nsteps) yz_stage<CH, EDGE>(U, g, rr0 + kRB);
-        /* y sums down the ring for the outputs whose last box row arrived */
-        int si = rr0 % g.RING;   /* slot of staged row rr */
+        /* y sums down the ring for the outputs whose last box row arrived:
+         * the step's first output is a direct sum over its box rows, the
+         * others run from it (at most 16 outputs per chain) */
         const int rend = min(kRB, g.NR - rr0);
-        for (int r = 0; r < rend; ++r) {
-            const int o = rr0 + r - 2 * g.sy;
-            if (o >= 0) {
-                if (direct_y || (o & 15) == 0) {
-                    int sl = si + kRB + 1;   /* slot of row o = rr - 2 sy */
+        const int o0 = max(0, rr0 - 2 * g.sy), o1 = rr0 + rend - 2 * g.sy;   /* outputs [o0, o1) */
+        if (o1 > o0) {
+            int si = rr0 % g.RING + (o0 + 2 * g.sy - rr0);   /* slot of row o0 + 2 sy */
+            if (si >= g.RING) si -= g.RING;
+            int so = si + kRB + 1;                             /* slot of row o0 */
+            if (so >= g.RING) so -= g.RING;
+            /* full y boxes for every output of the step: one reciprocal */
+            const bool yfull = g.ys + o0 - g.sy >= 0 && g.ys + o1 - 1 + g.sy < g.ny;
+            float *op = out + (i64)o0 * g.nz;
+            for (int o = o0; o < o1; ++o) {
+                if (o == o0 || direct_y) {
+                    int sl = si + kRB + 1;   /* slot of row o */
                     if (sl >= g.RING) sl -= g.RING;
-                    /* rows sl .. RING-1, then 0 .. (wrapped part) */
                     const int n1 = min(cy_full, g.RING - sl);
                     acc = 0.f;
                     for (int i = 0; i < n1; ++i) acc += ring[(sl + i) * kRS + col];
                     for (int i = 0; i < cy_full - n1; ++i) acc += ring[i * kRS + col];
                 } else {
-                    int so = si + kRB;       /* slot of row o - 1 */
-                    if (so >= g.RING) so -= g.RING;
+                    /* rows o + 2 sy (slot si) in, o - 1 (slot so) out */
                     acc += ring[si * kRS + col] - ring[so * kRS + col];
+                    if (++so == g.RING) so = 0;
                 }
+                /* the second-moment lane takes p from its partner */
                 const float p = __shfl_sync(0xffffffffu, acc, lane & 15);
-                const float q = __shfl_sync(0xffffffffu, acc, (lane & 15) + 16);
-                if (zok) {
-                    const int y = g.ys + o;
-                    const int cy = clipped32(y, g.sy, g.ny);
-                    const float rn = (cy == cy_full ? rcy_full : 1.f / (float)cy) * rcz;
-                    const float da = p * rn;
-                    /* a rounded product (no contraction into an fma): for a
-                     * one-voxel box q and p*p round alike and M is exactly 0 */
-                    out[(i64)o * g.nz] = sq ? fmaxf(q - __fmul_rn(p, da), 0.f) : s + da;
-                }
+                const float rn =
+                    yfull ? rn_full : rcz * __frcp_rn((float)clipped32(g.ys + o, g.sy, g.ny));
+                const float da = p * rn;
+                /* a rounded product (no contraction into an fma): for a
+                 * one-voxel box q and p*p round alike and M is exactly 0 */
+                const float v = sq ? fmaxf(acc - __fmul_rn(p, da), 0.f) : s + da;
+                if (zok) *op = v;
+                op += g.nz;
+                if (++si == g.RING) si = 0;
             }
-            if (++si == g.RING) si = 0;
         }
         if (b + 1 < nsteps) {
             asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -356,7 +362,7 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
 }
 
 template <int CH>
-__global__ void __launch_bounds__(kMT) sf_local_yz(const float *__restrict__ c, float *__restrict__ A,
+__global__ void __launch_bounds__(kMT, 3) sf_local_yz(const float *__restrict__ c, float *__restrict__ A,
                                                    float *__restrict__ M, i64 ny, i64 nz, int sy, int sz, int yrows)
 {
     extern __shared__ __align__(16) float sm[];
