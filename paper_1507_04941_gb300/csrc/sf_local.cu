@@ -412,102 +412,169 @@ struct Kahan {
     }
 };
 
-/* MODE 0: mean / std cubes; 1: mask words set; 2: mask words OR-ed */
-template <int MODE>
-__global__ void __launch_bounds__(kXThreads, 10)
+__device__ __forceinline__ void ldv(const float *p, float *v, int V)
+{
+    if (V == 2) {
+        const float2 q = *reinterpret_cast<const float2 *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    } else {
+        v[0] = *p;
+    }
+}
+
+/* the low 16 bits of x moved to the even bit positions */
+__device__ __forceinline__ unsigned int spread16(unsigned int x)
+{
+    x &= 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+/* MODE 0: mean / std cubes; 1: mask words set; 2: mask words OR-ed.
+ * V z per thread (2 when nz is even: 8-byte loads, a warp covers 64 z and
+ * two mask words).  Each step's loads are issued one step ahead. */
+template <int MODE, int V>
+__global__ void __launch_bounds__(kXThreads, 8)
     sf_local_x(const float *__restrict__ c, const float *__restrict__ A, const float *__restrict__ M, i64 nx,
                i64 ny, i64 nz, i64 nw32, int sx, int sy, int sz, float k, float *__restrict__ mean,
                float *__restrict__ stdv, unsigned int *__restrict__ mask)
 {
+    /* lanes per row: 32 / V per mask word, whole warps per row */
+    const i64 words_pad = V == 2 ? (nw32 + 1) & ~1LL : nw32;
+    const i64 per_row = words_pad * (32 / V);
     const i64 lane = (i64)blockIdx.x * kXThreads + threadIdx.x;
-    const i64 per_row = nw32 * 32;
     const i64 y = lane / per_row;
-    if (y >= ny) return;   /* whole warps: a row holds a multiple of 32 lanes */
-    const int zw = (int)((lane - y * per_row) >> 5);
-    const int bit = (int)(lane & 31);
-    const i64 z = (i64)zw * 32 + bit;
-    const bool valid = z < nz;
+    if (y >= ny) return;   /* whole warps */
+    const i64 lr = lane - y * per_row;
+    const i64 z = lr * V;
+    const int wl = threadIdx.x & 31;
+    bool valid[V];
+    float nyz[V], rnyz[V];
+    for (int e = 0; e < V; ++e) {
+        valid[e] = z + e < nz;
+        nyz[e] = (float)(clipped(y, sy, ny) * (valid[e] ? clipped(z + e, sz, nz) : 1));
+        rnyz[e] = __frcp_rn(nyz[e]);
+    }
     const i64 plane = ny * nz;
-    const i64 off = y * nz + (valid ? z : 0);
+    const i64 off = y * nz + (valid[0] ? z : 0);
     const float *pa = A + off, *pm = M + off, *pc = c + off;
-    const float nyz = (float)(clipped(y, sy, ny) * clipped(z, sz, nz));
     const int nxi = (int)nx;
-    const i64 x0 = (i64)blockIdx.y * kXSeg;
-    const i64 x1 = x0 + kXSeg < nx ? x0 + kXSeg : nx;
+    const int x0 = (int)blockIdx.y * kXSeg;
+    const int x1 = min(x0 + kXSeg, nxi);
+    const int Xfull = 2 * sx + 1;
+    const float rXfull = __frcp_rn((float)Xfull);
     /* segment blockIdx.y of kXSeg planes: the sums start from a direct sum
      * over the box of the segment's first plane, shifted by that plane's A,
      * so the running updates neither drift nor cancel */
-    const float s = pa[x0 * plane];
-    Kahan sa, sb, sm;   /* sums over the x box of A - s, (A - s)^2, M */
+    float s[V];
+    ldv(pa + (i64)x0 * plane, s, V);
+    Kahan sa[V], sb[V], sm[V];   /* sums over the x box of A - s, (A - s)^2, M */
     {
-        const i64 lo = x0 - sx < 0 ? 0 : x0 - sx, hi = x0 + sx >= nx ? nx - 1 : x0 + sx;
-        for (i64 xi = lo; xi <= hi; ++xi) {
-            const float d = pa[xi * plane] - s;
-            sa.add(d);
-            sb.add(d * d);
-            sm.add(pm[xi * plane]);
+        const int lo = max(x0 - sx, 0), hi = min(x0 + sx, nxi - 1);
+        for (int xi = lo; xi <= hi; ++xi) {
+            float a[V], m[V];
+            ldv(pa + (i64)xi * plane, a, V);
+            ldv(pm + (i64)xi * plane, m, V);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const float d = a[e] - s[e];
+                sa[e].add(d);
+                sb[e].add(d * d);
+                sm[e].add(m[e]);
+            }
         }
     }
-    /* pointers to the planes entering (x + sx) and leaving (x - sx - 1) the
-     * box, and to plane x; unused ones stay at plane 0 */
-    const float *ain_p = pa + (x0 + sx) * plane, *min_p = pm + (x0 + sx) * plane;
-    const float *aout_p = pa + (x0 - sx - 1) * plane, *mout_p = pm + (x0 - sx - 1) * plane;
-    const float *c_p = pc + x0 * plane;
-#pragma unroll 4
-    for (i64 x = x0; x < x1; ++x) {
-        /* the step's loads, unconditional (unused ones read plane 0) so they
-         * issue together */
-        const int xi = (int)x;
-        const bool hin = x > x0 && xi + sx < nxi, hout = x > x0 && xi - sx - 1 >= 0;
-        const float ain = hin ? ain_p[0] : pa[0], min_ = hin ? min_p[0] : pm[0];
-        const float aout = hout ? aout_p[0] : pa[0], mout = hout ? mout_p[0] : pm[0];
-        const float cv = MODE != 0 ? c_p[0] : 0.f;
-        ain_p += plane;
-        min_p += plane;
-        aout_p += plane;
-        mout_p += plane;
-        c_p += plane;
-        if (hin) {
-            const float d = ain - s;
-            sa.add(d);
-            sb.add(d * d);
-            sm.add(min_);
-        }
-        if (hout) {
-            const float d = aout - s;
-            sa.add(-d);
-            sb.add(-(d * d));
-            sm.add(-mout);
-        }
-        float X, mu, m2;
-        if (sx == 0) {
-            /* the x box is the plane itself */
-            X = 1.f;
-            mu = pa[x * plane];
-            m2 = pm[x * plane];
-        } else {
-            X = (float)(min(xi + sx, nxi - 1) - max(xi - sx, 0) + 1);
-            const float da = sa.s / X;
-            mu = s + da;
-            /* a rounded product (no contraction into an fma) */
-            m2 = sm.s + nyz * fmaxf(sb.s - __fmul_rn(sa.s, da), 0.f);
-        }
-        const float sd = sqrtf(m2 / (X * nyz));
-        if (MODE == 0) {
-            if (valid) {
-                mean[x * plane + off] = mu;
-                stdv[x * plane + off] = sd;
+    /* the loads of step x: planes entering (x + sx) and leaving (x - sx - 1)
+     * the box (plane 0 where there is none), and plane x */
+    auto load = [&](int x, float *ain, float *min_, float *aout, float *mout, float *cv) {
+        const bool hin = x > x0 && x + sx < nxi, hout = x > x0 && x - sx - 1 >= 0;
+        const i64 pin = hin ? (i64)(x + sx) * plane : 0, pout = hout ? (i64)(x - sx - 1) * plane : 0;
+        ldv(pa + pin, ain, V);
+        ldv(pm + pin, min_, V);
+        ldv(pa + pout, aout, V);
+        ldv(pm + pout, mout, V);
+        if (MODE != 0) ldv(pc + (i64)x * plane, cv, V);
+    };
+    float ain[V], min_[V], aout[V], mout[V], cv[V] = {};
+    load(x0, ain, min_, aout, mout, cv);
+    for (int x = x0; x < x1; ++x) {
+        float nain[V], nmin[V], naout[V], nmout[V], ncv[V] = {};
+        load(min(x + 1, x1 - 1), nain, nmin, naout, nmout, ncv);
+        const bool hin = x > x0 && x + sx < nxi, hout = x > x0 && x - sx - 1 >= 0;
+        const int X = min(x + sx, nxi - 1) - max(x - sx, 0) + 1;
+        const float rX = X == Xfull ? rXfull : __frcp_rn((float)X);
+        float mu[V], sd[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            if (hin) {
+                const float d = ain[e] - s[e];
+                sa[e].add(d);
+                sb[e].add(d * d);
+                sm[e].add(min_[e]);
             }
+            if (hout) {
+                const float d = aout[e] - s[e];
+                sa[e].add(-d);
+                sb[e].add(-(d * d));
+                sm[e].add(-mout[e]);
+            }
+            float m2;
+            if (sx == 0) {
+                /* the x box is the plane itself */
+                float a1[V], m1[V];
+                ldv(pa + (i64)x * plane, a1, V);
+                ldv(pm + (i64)x * plane, m1, V);
+                mu[e] = a1[e];
+                m2 = m1[e];
+            } else {
+                const float da = sa[e].s * rX;
+                mu[e] = s[e] + da;
+                /* a rounded product (no contraction into an fma) */
+                m2 = sm[e].s + nyz[e] * fmaxf(sb[e].s - __fmul_rn(sa[e].s, da), 0.f);
+            }
+            sd[e] = sqrtf(m2 * rX * rnyz[e]);
+        }
+        if (MODE == 0) {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (valid[e]) {
+                    mean[(i64)x * plane + off + e] = mu[e];
+                    stdv[(i64)x * plane + off + e] = sd[e];
+                }
         } else {
-            const unsigned int bits = __ballot_sync(0xffffffffu, valid && cv > fmaf(k, sd, mu));
-            if (bit == 0) {
-                unsigned int *w = mask + (x * ny + y) * nw32 + zw;
+            unsigned int bits[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                bits[e] = __ballot_sync(0xffffffffu, valid[e] && cv[e] > fmaf(k, sd[e], mu[e]));
+            unsigned int word = bits[0];
+            i64 wi = lr >> 5;   /* V == 1: word of this warp */
+            if (V == 2) {
+                /* lanes 0 and 1 assemble the warp's two words: word h holds
+                 * lanes 16 h .. 16 h + 15, two bits each */
+                const int h = wl & 1;
+                word = spread16(bits[0] >> (16 * h)) | (spread16(bits[V - 1] >> (16 * h)) << 1);
+                wi = ((lr >> 5) << 1) + h;
+            }
+            if (wl < (V == 2 ? 2 : 1) && wi < nw32) {
+                unsigned int *w = mask + ((i64)x * ny + y) * nw32 + wi;
                 if (MODE == 2) {
-                    if (bits) atomicOr(w, bits);   /* nothing waits on it */
+                    if (word) atomicOr(w, word);   /* nothing waits on it */
                 } else {
-                    *w = bits;
+                    *w = word;
                 }
             }
+        }
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            ain[e] = nain[e];
+            min_[e] = nmin[e];
+            aout[e] = naout[e];
+            mout[e] = nmout[e];
+            cv[e] = ncv[e];
         }
     }
 }
@@ -544,10 +611,20 @@ cudaError_t sf_launch_local_x(const float *c, const float *A, const float *M, lo
                               long long nz, long long nw32, int sx, int sy, int sz, float k, float *mean,
                               float *stdv, unsigned int *mask, int mode, cudaStream_t st)
 {
-    const long long lanes = ny * nw32 * 32;
+    if (nx > (1LL << 30)) return cudaErrorInvalidValue;
+    const bool v2 = nz % 2 == 0;
+    const long long lanes = v2 ? ny * ((nw32 + 1) & ~1LL) * 16 : ny * nw32 * 32;
     const dim3 grid((unsigned)((lanes + kXThreads - 1) / kXThreads), (unsigned)((nx + kXSeg - 1) / kXSeg));
-    if (mode == 0) sf_local_x<0><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask);
-    else if (mode == 1) sf_local_x<1><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask);
-    else sf_local_x<2><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask);
+#define SF_LX(MODE, V) sf_local_x<MODE, V><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask)
+    if (v2) {
+        if (mode == 0) SF_LX(0, 2);
+        else if (mode == 1) SF_LX(1, 2);
+        else SF_LX(2, 2);
+    } else {
+        if (mode == 0) SF_LX(0, 1);
+        else if (mode == 1) SF_LX(1, 1);
+        else SF_LX(2, 1);
+    }
+#undef SF_LX
     return cudaGetLastError();
 }
