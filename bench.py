@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -416,6 +417,37 @@ def run_ours(args):
                "steps": n_e2e, "h2d_bytes_per_step": int(nvox * sbytes),
                "d2h_bytes_per_step": int(mask.numel() * 4)}
 
+    # sectioned form: the same cube from pinned host memory in x sections of
+    # 128 planes with their halo, device memory bounded by the section size
+    sectioned = None
+    if not args.no_sections and world == 1:
+        from paper_1507_04941_gb300 import SectionedSourceFinder
+        sec = 128
+        h_cube_s = cube.cpu().pin_memory()
+        h_mask_s = torch.empty(sf.mask_shape, dtype=torch.int32, pin_memory=True)
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        with SectionedSourceFinder(w.shape, w.bank, w.truncation, w.window, w.k, section=sec,
+                                   storage=storage, device=dev) as ss:
+            dev_bytes = free0 - torch.cuda.mem_get_info(dev)[0]
+            for _ in range(2):
+                ss.detect_host(h_cube_s, h_mask_s)
+            n_s = max(3, min(args.steps, 20))
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(n_s):
+                ss.detect_host(h_cube_s, h_mask_s)
+            torch.cuda.synchronize(dev)
+            s_sec = (time.perf_counter() - t0) / n_s
+        rxm = max(int(math.ceil(w.truncation * b[0])) for b in w.bank)
+        halo = -(-rxm // w.window[0]) * w.window[0] if rxm else 0
+        sectioned = {"value": units / s_sec, "unit": UNIT, "ms_per_step": s_sec * 1e3, "steps": n_s,
+                     "section_planes": sec, "halo_planes": halo,
+                     "device_bytes": int(dev_bytes),
+                     "device_bytes_in_core": int(nvox * sbytes * (1 + len({b[0] for b in w.bank if b[0] > 0}))),
+                     "path": "x sections with halo: copy in, detect of the section, mask rows back, "
+                             "on three streams"}
+        del h_cube_s, h_mask_s
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -435,7 +467,7 @@ def run_ours(args):
             "serving": serving,
             "path": "persistent (x-pass + windows in one launch)" if persistent else
                     "x pass + window kernel", "autotune": tune_rep, "batched_form": batch,
-            "e2e": e2e, "gpu_launches": int(sum(st["launches_per_step"] for st in
+            "e2e": e2e, "sectioned_form": sectioned, "gpu_launches": int(sum(st["launches_per_step"] for st in
                                                 stages.values()) * args.steps),
             "cpu_baseline": cpu,
         }
@@ -670,6 +702,7 @@ def main():
     ap.add_argument("--no-local", action="store_true", help="skip the sliding-statistics form")
     ap.add_argument("--no-weighted", action="store_true", help="skip the weighted (Eq. 1) form")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving form")
+    ap.add_argument("--no-sections", action="store_true", help="skip the sectioned (out-of-core) form")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per offered-load level of the serving form")
     ap.add_argument("--no-forms", action="store_true",

@@ -134,6 +134,25 @@ sf_status sf_detect(sf_ctx *ctx, const void *d_cube, uint32_t *d_mask, float *d_
  * the copies asynchronous DMA; pageable ones work too. */
 sf_status sf_detect_host(sf_ctx *ctx, const void *h_cube, uint32_t *h_mask, void *stream);
 
+/* Sectioned form for cubes larger than device memory (Sec. 3.1: the cube is
+ * split into sections that each fit the device, with a halo).  The cube stays
+ * in host memory.  sf_detect_host on this context cuts it along x into
+ * sections of `section` planes, a positive multiple of cfg->wx (SF_EINVAL
+ * otherwise).  Each section goes to the device together with h halo planes
+ * on each side, where h is the largest x radius of the bank rounded up to a
+ * multiple of wx.  Halo planes outside the cube are zero.  The section's x
+ * pass and statistics windows then equal the whole cube's: every window lies
+ * in one section, since sections start on window boundaries.  The mask
+ * equals sf_detect's bit for bit.
+ *
+ * Device memory holds two section buffers and the scratch of one context of
+ * (section + 2h) planes, plus, when nx is not a multiple of wx, a second
+ * context for the last section.  It does not depend on nx.  Copies in, the
+ * section's detect and the copy back overlap on three streams.  Every other
+ * entry point except sf_synchronize and sf_destroy returns SF_EINVAL on this
+ * context. */
+sf_status sf_create_sectioned(const sf_config *cfg, int64_t section, sf_ctx **out);
+
 /* Batched form.  One context for n cubes of different shapes that share the
  * filter bank, window, threshold and storage of cfg (cfg->nx, ny, nz are
  * ignored; dims holds n triples nx, ny, nz).  The context plans one
@@ -222,6 +241,13 @@ sf_status sf_filter_noalloc(const float *d_cube, int64_t nx, int64_t ny, int64_t
  * that fails).  Not for batched contexts. */
 sf_status sf_local_stats(sf_ctx *ctx, const float *d_filtered, int32_t sx, int32_t sy, int32_t sz,
                          float *d_mean, float *d_std, void *stream);
+
+/* Per-voxel z-score over the same box: z = (c - mean) / std for every voxel
+ * of d_filtered, z = 0 where std = 0 (a box of equal values), float32
+ * [nx][ny][nz] into d_z (device).  The selection of sf_local_detect is
+ * z > k.  Same limits and scratch as sf_local_stats. */
+sf_status sf_local_zscore(sf_ctx *ctx, const float *d_filtered, int32_t sx, int32_t sy, int32_t sz,
+                          float *d_z, void *stream);
 
 /* The detect with per-voxel local statistics instead of windows: every
  * filter of the bank (Eq. 2), the local mean / std of each filtered cube over

@@ -364,6 +364,19 @@ def local_stats(c, half, idx=None, nthreads: int = 0) -> tuple[np.ndarray, np.nd
     return mean, std
 
 
+def local_zscore(c, half, idx=None) -> np.ndarray:
+    """Per-voxel z-score (c - mean) / std over the clipped box of half-widths
+    half (Sec. 3.3, the statistics the voxel selection tests against), 0
+    where std = 0.  idx: flat voxel indices (default: every voxel)."""
+    c = np.ascontiguousarray(np.asarray(c), dtype=np.float64)
+    mean, std = local_stats(c, half, idx)
+    cv = c if idx is None else c.ravel()[np.asarray(idx, dtype=np.int64).ravel()]
+    z = np.zeros_like(mean)
+    ok = std > 0
+    z[ok] = (cv[ok] - mean[ok]) / std[ok]
+    return z
+
+
 def local_detect(d, bank, truncation, half, k, band_rel: float = 1e-4, voxels=None):
     """The sliding-statistics form of the method (Sec. 3.3 read per voxel):
     every filter of the bank (Eq. 2), the local mean/std of each filtered cube

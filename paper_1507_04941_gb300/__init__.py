@@ -5,5 +5,5 @@ standard deviation of each filtered cube, the threshold mean + k*std and the
 OR of all filters into a packed mask (Westerlund & Harris, Eq. 2 and
 Sec. 3.3), as CUDA kernels for sm_103a behind the C ABI of include/sf.h.
 """
-from .sf import (BatchSourceFinder, Server, SfError, SourceFinder, lib,  # noqa: F401
-                 words_to_bits)
+from .sf import (BatchSourceFinder, SectionedSourceFinder, Server, SfError, SourceFinder,  # noqa: F401
+                 lib, words_to_bits)

@@ -434,7 +434,8 @@ __device__ __forceinline__ unsigned int spread16(unsigned int x)
     return x;
 }
 
-/* MODE 0: mean / std cubes; 1: mask words set; 2: mask words OR-ed.
+/* MODE 0: mean / std cubes; 1: mask words set; 2: mask words OR-ed;
+ * 3: z-score cube (c - mean) / std, 0 where std = 0, into `mean`.
  * V z per thread (2 when nz is even: 8-byte loads, a warp covers 64 z and
  * two mask words).  Each step's loads are issued one step ahead. */
 template <int MODE, int V>
@@ -545,6 +546,10 @@ __global__ void __launch_bounds__(kXThreads, 8)
                     mean[(i64)x * plane + off + e] = mu[e];
                     stdv[(i64)x * plane + off + e] = sd[e];
                 }
+        } else if (MODE == 3) {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (valid[e]) mean[(i64)x * plane + off + e] = sd[e] > 0.f ? (cv[e] - mu[e]) / sd[e] : 0.f;
         } else {
             unsigned int bits[V];
 #pragma unroll
@@ -619,11 +624,13 @@ cudaError_t sf_launch_local_x(const float *c, const float *A, const float *M, lo
     if (v2) {
         if (mode == 0) SF_LX(0, 2);
         else if (mode == 1) SF_LX(1, 2);
-        else SF_LX(2, 2);
+        else if (mode == 2) SF_LX(2, 2);
+        else SF_LX(3, 2);
     } else {
         if (mode == 0) SF_LX(0, 1);
         else if (mode == 1) SF_LX(1, 1);
-        else SF_LX(2, 1);
+        else if (mode == 2) SF_LX(2, 1);
+        else SF_LX(3, 1);
     }
 #undef SF_LX
     return cudaGetLastError();

@@ -281,6 +281,16 @@ struct sf_ctx {
         int xv;
     };
     bool batch = false;               /* created by sf_create_batch */
+    /* sectioned form (Sec. 3.1: cubes larger than device memory): x sections
+     * of sect_S planes plus sect_h halo planes on each side, each processed
+     * by a context of the section's shape; sub[1] serves a last section that
+     * ends in a partial statistics window */
+    bool sectioned = false;
+    long long sect_S = 0, sect_h = 0;
+    sf_ctx *sub[2] = {nullptr, nullptr};
+    long long sub_nx[2] = {0, 0};
+    void *sbuf[2] = {nullptr, nullptr};             /* section inputs */
+    unsigned int *smask[2] = {nullptr, nullptr};    /* section masks */
     bool use_persist = false;         /* sf_detect runs the persistent kernel */
     std::vector<Cube> cubes;
     void *bscratch = nullptr;         /* scratch of all cubes (batched contexts) */
@@ -1095,10 +1105,11 @@ sf_status run_persist(sf_ctx *c, const void *const *cubes, uint32_t *const *mask
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-sf_status check_live(sf_ctx *c)
+sf_status check_live(sf_ctx *c, bool sectioned_ok = false)
 {
     if (!c) return SF_EINVAL;
     if (c->dead) return fail(c, SF_ESTATE, "context unusable after an earlier CUDA error");
+    if (c->sectioned && !sectioned_ok) return fail(c, SF_EINVAL, "sectioned context: use sf_detect_host");
     return SF_OK;
 }
 
@@ -1415,6 +1426,73 @@ sf_status sf_create_batch(const sf_config *cfg, int32_t n, const int64_t *dims, 
     return create_impl(cfg, n, dims, out);
 }
 
+sf_status sf_create_sectioned(const sf_config *cfg, int64_t section, sf_ctx **out)
+{
+    if (!out) return fail(nullptr, SF_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, SF_EINVAL, "cfg is NULL");
+    const sf_config &g = *cfg;
+    if (g.wx < 1) return fail(nullptr, SF_EINVAL, "window sizes must be >= 1");
+    if (section < 1 || section % g.wx != 0)
+        return fail(nullptr, SF_EINVAL, "section must be a positive multiple of wx (%d)", g.wx);
+    if (g.nx < 1 || g.nx > (1LL << 31)) return fail(nullptr, SF_EINVAL, "nx must be in [1, 2^31]");
+    if (g.n_filters < 1 || g.n_filters > kMaxFilters || !g.filters)
+        return fail(nullptr, SF_EINVAL, "n_filters must be in [1, %d] with a filter array", kMaxFilters);
+    if (!(g.truncation > 0.f) || !std::isfinite(g.truncation))
+        return fail(nullptr, SF_EINVAL, "truncation must be positive");
+    int rxm = 0;
+    for (int i = 0; i < g.n_filters; ++i) {
+        const float sxy = g.filters[i].sigma_xy;
+        if (!(sxy >= 0.f) || !std::isfinite(sxy)) return fail(nullptr, SF_EINVAL, "filter %d: sigmas must be finite and >= 0", i);
+        rxm = std::max(rxm, radius_of(sxy, g.truncation));
+    }
+    /* halo: the largest x radius, rounded up to whole windows so that the
+     * section context's windows fall on the cube's */
+    const long long h = rxm > 0 ? ((long long)rxm + g.wx - 1) / g.wx * g.wx : 0;
+    const bool one = g.nx <= section;
+    const long long nsub[2] = {one ? g.nx : section + 2 * h,
+                               one || g.nx % g.wx == 0 ? 0 : g.nx - (g.nx - 1) / section * section + h};
+    sf_ctx *sub[2] = {nullptr, nullptr};
+    for (int i = 0; i < 2; ++i) {
+        if (!nsub[i]) continue;
+        sf_config q = g;
+        q.nx = nsub[i];
+        sf_status s = create_impl(&q, 0, nullptr, &sub[i]);
+        if (s != SF_OK) {
+            if (sub[0]) sf_destroy(sub[0]);
+            return s;
+        }
+    }
+    sf_ctx *c = new sf_ctx();
+    c->cfg = g;
+    c->cfg.filters = nullptr;
+    c->sectioned = true;
+    c->device = sub[0]->device;
+    c->ebytes = sub[0]->ebytes;
+    c->nvox = g.nx * g.ny * g.nz;
+    c->nw32 = sub[0]->nw32;
+    c->sect_S = one ? g.nx : section;
+    c->sect_h = one ? 0 : h;
+    for (int i = 0; i < 2; ++i) {
+        c->sub[i] = sub[i];
+        c->sub_nx[i] = nsub[i];
+    }
+    DeviceGuard dg(c->device);
+    const long long nmax = std::max(nsub[0], nsub[1]);
+    const size_t in_bytes = (size_t)nmax * (size_t)(g.ny * g.nz) * c->ebytes;
+    const size_t mask_bytes = (size_t)nmax * (size_t)(g.ny * c->nw32) * 4;
+    for (int i = 0; i < 2; ++i) {
+        if (cudaMalloc(&c->sbuf[i], in_bytes) != cudaSuccess ||
+            cudaMalloc((void **)&c->smask[i], mask_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            sf_destroy(c);
+            return fail(nullptr, SF_ENOMEM, "section buffers (2 x %zu bytes)", in_bytes + mask_bytes);
+        }
+    }
+    *out = c;
+    return SF_OK;
+}
+
 sf_status sf_destroy(sf_ctx *c)
 {
     if (!c) return SF_OK;
@@ -1434,6 +1512,11 @@ sf_status sf_destroy(sf_ctx *c)
     cudaFree(c->lscratch);
     cudaFree(c->wscratch);
     cudaFree(c->wstats);
+    for (int i = 0; i < 2; ++i) {
+        if (c->sub[i]) sf_destroy(c->sub[i]);
+        cudaFree(c->sbuf[i]);
+        cudaFree(c->smask[i]);
+    }
     if (c->boxtwin) sf_destroy(c->boxtwin);
     if (c->gausstwin) sf_destroy(c->gausstwin);
     for (cudaStream_t x : c->hcopy)
@@ -1781,12 +1864,105 @@ sf_status sf_profile_read(sf_ctx *c, double *ms, int64_t *launches, int32_t n_st
     return s;
 }
 
+/* Sectioned detect from host buffers (Sec. 3.1: the cube is cut along x
+ * into sections with a halo; Sec. 6: input overlapped with processing).
+ * Section k covers planes [x0, x1) = [kS, min(nx, kS + S)); its context sees
+ * planes [x0 - h, x0 - h + nsub), h a multiple of wx at least the largest x
+ * radius, with zeros where that range leaves the cube, so the x pass of
+ * planes [x0, x1) reads exactly the planes the whole-cube pass reads and the
+ * statistics windows of [x0, x1) are the whole cube's.  Copies in, the
+ * section's detect and the copy back of its mask rows run on three streams;
+ * two section buffers alternate. */
+sf_status detect_sections(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *stream)
+{
+    DeviceGuard dg(c->device);
+    const sf_config &g = c->cfg;
+    const size_t plane = (size_t)(g.ny * g.nz) * c->ebytes;
+    const size_t mplane = (size_t)(g.ny * c->nw32) * 4;
+    const long long nx = g.nx, S = c->sect_S, h = c->sect_h;
+    const int K = (int)((nx + S - 1) / S);
+    cudaError_t e;
+    if (!c->hback) {
+        if ((e = cudaStreamCreateWithFlags(&c->hcopy[0], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&c->hcomp[0], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&c->hback, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(c, e, "section streams");
+    }
+    while ((int)c->hev.size() < 3 * K + 2) {
+        cudaEvent_t ev;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "section events");
+        c->hev.push_back(ev);
+    }
+    cudaStream_t st = (cudaStream_t)stream, cs = c->hcopy[0], ks = c->hcomp[0], bs = c->hback;
+    cudaEvent_t *ev_in = &c->hev[0], *ev_run = &c->hev[K], *ev_out = &c->hev[2 * K];
+    /* nothing may overtake earlier work on the caller's stream */
+    cudaEventRecord(c->hev[3 * K], st);
+    cudaStreamWaitEvent(cs, c->hev[3 * K], 0);
+    cudaStreamWaitEvent(ks, c->hev[3 * K], 0);
+    cudaStreamWaitEvent(bs, c->hev[3 * K], 0);
+    sf_status s;
+    long long plo = 0, phi = 0, porigin = 0;   /* planes held by the previous section's buffer */
+    for (int k = 0; k < K; ++k) {
+        const long long x0 = k * S, x1 = std::min(nx, x0 + S);
+        const int b = k & 1;
+        const int u = (K > 1 && x1 == nx && nx % g.wx != 0) ? 1 : 0;
+        const long long origin = K == 1 ? 0 : x0 - h, nsub = c->sub_nx[u];
+        const long long lo = std::max(0LL, origin), hi = std::min(nx, origin + nsub);
+        char *buf = (char *)c->sbuf[b];
+        /* the buffers of section k - 2 are free once its mask rows are back */
+        if (k >= 2) cudaStreamWaitEvent(cs, ev_out[k - 2], 0);
+        if (lo > origin && (e = cudaMemsetAsync(buf, 0, (size_t)(lo - origin) * plane, cs)) != cudaSuccess)
+            return cuda_fail(c, e, "section padding");
+        if (origin + nsub > hi &&
+            (e = cudaMemsetAsync(buf + (size_t)(hi - origin) * plane, 0, (size_t)(origin + nsub - hi) * plane, cs)) !=
+                cudaSuccess)
+            return cuda_fail(c, e, "section padding");
+        /* planes the previous section also holds (its right part, this one's
+         * left halo) move device to device; only the rest crosses the host
+         * link, so each plane does so once */
+        const long long olo = k > 0 ? std::max(lo, plo) : lo, ohi = k > 0 ? std::min(hi, phi) : lo;
+        auto h2d = [&](long long a, long long z) -> cudaError_t {
+            if (z <= a) return cudaSuccess;
+            return cudaMemcpyAsync(buf + (size_t)(a - origin) * plane, (const char *)h_cube + (size_t)a * plane,
+                                   (size_t)(z - a) * plane, cudaMemcpyHostToDevice, cs);
+        };
+        if (ohi > olo) {
+            const char *prev = (const char *)c->sbuf[b ^ 1];
+            if ((e = cudaMemcpyAsync(buf + (size_t)(olo - origin) * plane, prev + (size_t)(olo - porigin) * plane,
+                                     (size_t)(ohi - olo) * plane, cudaMemcpyDeviceToDevice, cs)) != cudaSuccess)
+                return cuda_fail(c, e, "section overlap copy");
+            if ((e = h2d(lo, olo)) != cudaSuccess || (e = h2d(ohi, hi)) != cudaSuccess)
+                return cuda_fail(c, e, "section host-to-device copy");
+        } else if ((e = h2d(lo, hi)) != cudaSuccess) {
+            return cuda_fail(c, e, "section host-to-device copy");
+        }
+        plo = lo;
+        phi = hi;
+        porigin = origin;
+        cudaEventRecord(ev_in[k], cs);
+        cudaStreamWaitEvent(ks, ev_in[k], 0);
+        if ((s = sf_detect(c->sub[u], buf, c->smask[b], nullptr, nullptr, ks)) != SF_OK)
+            return fail(c, s, "section %d: %s", k, c->sub[u]->err.c_str());
+        cudaEventRecord(ev_run[k], ks);
+        cudaStreamWaitEvent(bs, ev_run[k], 0);
+        if ((e = cudaMemcpyAsync((char *)h_mask + (size_t)x0 * mplane,
+                                 (const char *)c->smask[b] + (size_t)(x0 - origin) * mplane,
+                                 (size_t)(x1 - x0) * mplane, cudaMemcpyDeviceToHost, bs)) != cudaSuccess)
+            return cuda_fail(c, e, "section device-to-host copy");
+        cudaEventRecord(ev_out[k], bs);
+    }
+    cudaStreamWaitEvent(st, ev_out[K - 1], 0);
+    return sf_synchronize(c, stream);
+}
+
 sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *stream)
 {
-    sf_status s = check_live(c);
+    sf_status s = check_live(c, true);
     if (s != SF_OK) return s;
     if (c->batch) return fail(c, SF_EINVAL, "batched context: use sf_detect_batch");
     if (!h_cube || !h_mask) return fail(c, SF_EINVAL, "NULL buffer");
+    if (c->sectioned) return detect_sections(c, h_cube, h_mask, stream);
     DeviceGuard dg(c->device);
     const size_t plane = (size_t)(c->cfg.ny * c->cfg.nz) * c->ebytes;
     const size_t mplane = (size_t)(c->cfg.ny * c->nw32) * 4;
@@ -1922,6 +2098,25 @@ sf_status sf_local_stats(sf_ctx *c, const float *d_filtered, int32_t sx, int32_t
         e = sf_launch_local_x(d_filtered, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_mean, d_std,
                               nullptr, 0, st);
     return e == cudaSuccess ? SF_OK : cuda_fail(c, e, "local statistics launch");
+}
+
+sf_status sf_local_zscore(sf_ctx *c, const float *d_filtered, int32_t sx, int32_t sy, int32_t sz, float *d_z,
+                          void *stream)
+{
+    sf_status s = local_check(c, sx, sy, sz);
+    if (s != SF_OK) return s;
+    if (!d_filtered || !d_z) return fail(c, SF_EINVAL, "NULL buffer");
+    DeviceGuard dg(c->device);
+    if ((s = local_scratch(c)) != SF_OK) return s;
+    const sf_config &g = c->cfg;
+    const size_t cube = align_up((size_t)c->nvox * sizeof(float), 256) / sizeof(float);
+    float *P = c->lscratch + cube, *Q = c->lscratch + 2 * cube;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = sf_launch_local_yz(d_filtered, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
+    if (e == cudaSuccess)
+        e = sf_launch_local_x(d_filtered, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_z, nullptr,
+                              nullptr, 3, st);
+    return e == cudaSuccess ? SF_OK : cuda_fail(c, e, "local z-score launch");
 }
 
 sf_status sf_local_detect(sf_ctx *c, const void *d_cube, int32_t sx, int32_t sy, int32_t sz, uint32_t *d_mask,
@@ -2138,8 +2333,13 @@ sf_status sf_weighted_detect(sf_ctx *c, const float *d_cube, const float *d_weig
 
 sf_status sf_synchronize(sf_ctx *c, void *stream)
 {
-    sf_status s = check_live(c);
+    sf_status s = check_live(c, true);
     if (s != SF_OK) return s;
+    if (c->sectioned) {
+        for (sf_ctx *u : c->sub)
+            if (u && (s = sf_synchronize(u, stream)) != SF_OK) return fail(c, s, "section: %s", u->err.c_str());
+        return SF_OK;
+    }
     DeviceGuard dg(c->device);
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronise");

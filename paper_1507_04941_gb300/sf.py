@@ -61,6 +61,7 @@ SIGNATURES = {
     "sf_detect": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sf_detect_host": (_i32, [_vp, _vp, _vp, _vp]),
     "sf_synchronize": (_i32, [_vp, _vp]),
+    "sf_create_sectioned": (_i32, [ctypes.POINTER(Config), _i64, ctypes.POINTER(_vp)]),
     "sf_create_batch": (_i32, [ctypes.POINTER(Config), _i32, ctypes.POINTER(_i64),
                                ctypes.POINTER(_vp)]),
     "sf_detect_batch": (_i32, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -77,6 +78,7 @@ SIGNATURES = {
                                  ctypes.c_float, _vp, _vp]),
     "sf_local_stats": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp]),
     "sf_local_detect": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "sf_local_zscore": (_i32, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "sf_weighted_filter": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp]),
     "sf_weighted_detect": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "sf_profile_enable": (_i32, [_vp, _i32]),
@@ -265,6 +267,19 @@ class SourceFinder:
                                     _stream(self.device)), self._h)
         return mean, std
 
+    def local_zscore(self, filtered, half, out=None):
+        """Per-voxel z-score (c - mean) / std over the box of half-widths
+        half = (sx, sy, sz), 0 where std = 0 (float32, the cube's shape)."""
+        import torch
+        self._check_f32(filtered, self.shape, "filtered")
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        self._check_f32(out, self.shape, "out")
+        sx, sy, sz = (int(v) for v in half)
+        _check(lib().sf_local_zscore(self._h, _ptr(filtered), sx, sy, sz, _ptr(out),
+                                     _stream(self.device)), self._h)
+        return out
+
     def local_detect(self, cube, half, mask=None):
         """Packed mask of the detect with per-voxel local statistics over the
         box of half-widths half = (sx, sy, sz)."""
@@ -370,6 +385,65 @@ def tune_report(handle) -> str:
     buf = ctypes.create_string_buffer(1 << 16)
     _check(lib().sf_tune_report(handle, buf, len(buf)), handle)
     return buf.value.decode()
+
+
+class SectionedSourceFinder:
+    """Detect on a cube held in host memory, section by section along x, with
+    device memory bounded by the section size (wraps a sectioned sf_ctx)."""
+
+    def __init__(self, shape, bank, truncation: float = 3.0, window=(32, 32, 64), k: float = 4.0,
+                 section: int = 256, storage: str = "f32", device=None):
+        import torch
+        self.shape = tuple(int(s) for s in shape)
+        self.bank = tuple((float(a), float(b)) for a, b in bank)
+        self.window = tuple(int(w) for w in window)
+        self.storage = storage
+        self.section = int(section)
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        specs = (FilterSpec * len(self.bank))(*[FilterSpec(a, b) for a, b in self.bank])
+        self._specs = specs
+        cfg = Config(self.shape[0], self.shape[1], self.shape[2], len(self.bank), specs,
+                     float(truncation), self.window[0], self.window[1], self.window[2], float(k),
+                     STORAGE[storage], 0, self.device.index if self.device.index is not None else -1)
+        h = _vp()
+        _check(lib().sf_create_sectioned(ctypes.byref(cfg), self.section, ctypes.byref(h)), None)
+        self._h = h
+
+    @property
+    def mask_shape(self):
+        return (self.shape[0], self.shape[1], -(-self.shape[2] // 32))
+
+    def detect_host(self, cube_host, mask_host=None):
+        """Host tensors in and out (pinned memory makes the copies DMA)."""
+        import torch
+        dt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.storage]
+        if tuple(cube_host.shape) != self.shape or cube_host.dtype != dt \
+                or cube_host.device.type != "cpu" or not cube_host.is_contiguous():
+            raise ValueError("cube_host must be a contiguous CPU tensor of the cube shape/dtype")
+        if mask_host is None:
+            mask_host = torch.empty(self.mask_shape, dtype=torch.int32, pin_memory=cube_host.is_pinned())
+        _check(lib().sf_detect_host(self._h, _ptr(cube_host), _ptr(mask_host), _stream(self.device)),
+               self._h)
+        return mask_host
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class BatchSourceFinder:

@@ -114,3 +114,18 @@ def test_server_invalid_arguments(libsf):
     assert lib.sf_server_destroy(None) == sf.SF_OK
     n = ctypes.c_int32()
     assert lib.sf_server_poll(None, None, None, None, 0, 0, ctypes.byref(n)) == sf.SF_EINVAL
+
+
+@pytest.mark.parametrize("section,bad", [(0, {}), (12, {}), (-8, {}), (16, dict(wx=0)),
+                                         (16, dict(bank=((float("nan"), 2.0),))),
+                                         (16, dict(filters=None)), (16, dict(truncation=0.0))])
+def test_sectioned_arguments_rejected_on_host(libsf, section, bad):
+    """A section must be a positive multiple of wx (wx = 8 here); the bank is
+    checked before any device work."""
+    from paper_1507_04941_gb300 import sf
+    lib = sf.lib()
+    cfg, _keep = _cfg(sf, **bad)
+    h = ctypes.c_void_p()
+    assert lib.sf_create_sectioned(ctypes.byref(cfg), section, ctypes.byref(h)) == sf.SF_EINVAL
+    assert not h.value
+    assert lib.sf_create_sectioned(None, 16, ctypes.byref(h)) == sf.SF_EINVAL

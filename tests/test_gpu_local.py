@@ -137,3 +137,30 @@ def test_local_detect_full_tile_sampled(dev, oracle):
     got = bits.ravel()[pick]
     diff = (got != fire.astype(bool)) & sure.astype(bool)
     assert not diff.any(), f"{int(diff.sum())} of {len(pick)} sampled certain bits differ"
+
+
+@pytest.mark.parametrize("shape,half", [((40, 36, 100), (4, 4, 8)),
+                                        ((17, 50, 31), (2, 6, 3)),      # nz odd: one z per thread
+                                        ((12, 33, 64), (0, 0, 0))])     # the voxel itself: z = 0
+def test_local_zscore_parity(dev, oracle, shape, half):
+    """z = (c - mean) / std against the oracle.  With |d mean|, |d std| below
+    1e-5 max(std, |mean|), the z error stays below
+    1e-5 max(std, |mean|) / std (1 + |z|), doubled for the final rounding."""
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder
+    cube = _cube(shape, seed=46)
+    with SourceFinder(shape, ((1.5, 2.0),), 3.0, (16, 16, 32), device=dev) as sf:
+        c = sf.filter(cube.to(dev), 0)
+        c += 3.0
+        z = sf.local_zscore(c, half)
+        torch.cuda.synchronize(dev)
+        cn = c.cpu().numpy().astype(np.float64)
+    rz = oracle.local_zscore(cn, half)
+    rm, rs = oracle.local_stats(cn, half)
+    got = z.cpu().numpy().astype(np.float64)
+    if half == (0, 0, 0):
+        assert (got == 0).all()
+        return
+    tol = 2e-5 * np.maximum(rs, np.abs(rm)) / rs * (1 + np.abs(rz)) + 1e-6
+    bad = np.abs(got - rz) > tol
+    assert not bad.any(), f"{int(bad.sum())} z-scores off, worst {float(np.abs(got - rz).max()):.3g}"

@@ -104,3 +104,45 @@ def test_local_detect_sampled_path_matches_whole_cube(oracle, rng):
     thr = mv + 3.0 * sv
     assert np.array_equal(fire.astype(bool), (cv > thr).any(axis=0))
     assert fire.sum() > 0 and fire.sum() < fire.size
+
+
+# ---- z-score (c - mean) / std over the same box ----
+
+def test_zscore_of_a_spike_is_sqrt_n_minus_1(oracle):
+    """One voxel of height h among zeros, box of n voxels around it: mean
+    h/n, population variance h^2 (n - 1) / n^2, so z at the spike is
+    (h - h/n) / (h sqrt(n - 1) / n) = sqrt(n - 1); its neighbours in the box
+    sit at -1/sqrt(n - 1)."""
+    c = np.zeros((9, 9, 13))
+    c[4, 4, 6] = 7.5
+    half = (1, 2, 3)
+    n = 3 * 5 * 7
+    z = oracle.local_zscore(c, half)
+    assert z[4, 4, 6] == pytest.approx(math.sqrt(n - 1), rel=1e-12)
+    # a neighbour whose own box is interior and holds the spike
+    assert z[4, 4, 7] == pytest.approx(-1.0 / math.sqrt(n - 1), rel=1e-12)
+    # far from the spike every box is constant 0: std 0 gives z 0
+    assert z[0, 0, 0] == 0.0
+
+
+def test_zscore_invariances(oracle, rng):
+    """z is unchanged by c -> a c + b (a > 0) and flips sign under c -> -c."""
+    c = rng.normal(size=(6, 7, 10))
+    half = (1, 2, 2)
+    z = oracle.local_zscore(c, half)
+    assert np.allclose(oracle.local_zscore(3.5 * c - 2.0, half), z, rtol=1e-10, atol=1e-10)
+    assert np.allclose(oracle.local_zscore(-c, half), -z, rtol=1e-10, atol=1e-10)
+
+
+def test_zscore_brute_force_and_sampled(oracle, rng):
+    c = rng.normal(size=(5, 6, 8)) + 4.0
+    half = (1, 1, 2)
+    z = oracle.local_zscore(c, half)
+    nx, ny, nz = c.shape
+    for x in range(nx):
+        for y in range(ny):
+            for q in range(nz):
+                blk = c[max(0, x - 1):x + 2, max(0, y - 1):y + 2, max(0, q - 2):q + 3]
+                assert z[x, y, q] == pytest.approx((c[x, y, q] - blk.mean()) / blk.std(), rel=1e-10)
+    idx = np.array([0, 17, 101, c.size - 1])
+    assert np.allclose(oracle.local_zscore(c, half, idx), z.ravel()[idx], rtol=1e-14, atol=0)
