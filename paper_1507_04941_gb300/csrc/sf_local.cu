@@ -239,6 +239,18 @@ __device__ __forceinline__ void yz_shift(float *U, const YzGeom &g, int rr0, flo
     }
 }
 
+/* one output row of the y march: the second-moment lane (sq) takes p from
+ * its partner lane; rn = 1 / (box count) */
+__device__ __forceinline__ void yz_emit(float acc, int lane, int sq, bool zok, float rn, float s, float *op)
+{
+    const float p = __shfl_sync(0xffffffffu, acc, lane & 15);
+    const float da = p * rn;
+    /* a rounded product (no contraction into an fma): for a one-voxel box q
+     * and p*p round alike and M is exactly 0 */
+    const float v = sq ? fmaxf(acc - __fmul_rn(p, da), 0.f) : s + da;
+    if (zok) *op = v;
+}
+
 /* EDGE: some staged columns lie outside the cube; the staged values are then
  * shifted in place, otherwise s is subtracted as they are read */
 template <int CH, bool EDGE>
@@ -317,7 +329,8 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
         if (b + 1 < nsteps) yz_stage<CH, EDGE>(U, g, rr0 + kRB);
         /* y sums down the ring for the outputs whose last box row arrived:
          * the step's first output is a direct sum over its box rows, the
-         * others run from it (at most 16 outputs per chain) */
+         * others run from it (at most 16 outputs per chain) in stretches
+         * where neither ring pointer wraps */
         const int rend = min(kRB, g.NR - rr0);
         const int o0 = max(0, rr0 - 2 * g.sy), o1 = rr0 + rend - 2 * g.sy;   /* outputs [o0, o1) */
         if (o1 > o0) {
@@ -328,30 +341,48 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
             /* full y boxes for every output of the step: one reciprocal */
             const bool yfull = g.ys + o0 - g.sy >= 0 && g.ys + o1 - 1 + g.sy < g.ny;
             float *op = out + (i64)o0 * g.nz;
-            for (int o = o0; o < o1; ++o) {
-                if (o == o0 || direct_y) {
-                    int sl = si + kRB + 1;   /* slot of row o */
+            for (int o = o0; o < o1;) {
+                /* direct sum of rows o .. o + 2 sy */
+                {
+                    int sl = so + (o - o0);
                     if (sl >= g.RING) sl -= g.RING;
                     const int n1 = min(cy_full, g.RING - sl);
                     acc = 0.f;
                     for (int i = 0; i < n1; ++i) acc += ring[(sl + i) * kRS + col];
                     for (int i = 0; i < cy_full - n1; ++i) acc += ring[i * kRS + col];
-                } else {
-                    /* rows o + 2 sy (slot si) in, o - 1 (slot so) out */
-                    acc += ring[si * kRS + col] - ring[so * kRS + col];
-                    if (++so == g.RING) so = 0;
                 }
-                /* the second-moment lane takes p from its partner */
-                const float p = __shfl_sync(0xffffffffu, acc, lane & 15);
-                const float rn =
-                    yfull ? rn_full : rcz * __frcp_rn((float)clipped32(g.ys + o, g.sy, g.ny));
-                const float da = p * rn;
-                /* a rounded product (no contraction into an fma): for a
-                 * one-voxel box q and p*p round alike and M is exactly 0 */
-                const float v = sq ? fmaxf(acc - __fmul_rn(p, da), 0.f) : s + da;
-                if (zok) *op = v;
+                yz_emit(acc, lane, sq, zok, yfull ? rn_full : rcz * __frcp_rn((float)clipped32(g.ys + o, g.sy, g.ny)),
+                        s, op);
                 op += g.nz;
-                if (++si == g.RING) si = 0;
+                ++o;
+                if (direct_y) continue;
+                /* rows o + 2 sy in (slot a), o - 1 out (slot c) */
+                int a = si + (o - o0), c = so + (o - 1 - o0);
+                if (a >= g.RING) a -= g.RING;
+                if (c >= g.RING) c -= g.RING;
+                while (o < o1) {
+                    const int m = min(o1 - o, min(g.RING - a, g.RING - c));
+                    const float *pin = ring + a * kRS + col, *pout = ring + c * kRS + col;
+                    if (yfull) {
+                        for (int i = 0; i < m; ++i) {
+                            acc += pin[i * kRS] - pout[i * kRS];
+                            yz_emit(acc, lane, sq, zok, rn_full, s, op);
+                            op += g.nz;
+                        }
+                    } else {
+                        for (int i = 0; i < m; ++i) {
+                            acc += pin[i * kRS] - pout[i * kRS];
+                            yz_emit(acc, lane, sq, zok,
+                                    rcz * __frcp_rn((float)clipped32(g.ys + o + i, g.sy, g.ny)), s, op);
+                            op += g.nz;
+                        }
+                    }
+                    o += m;
+                    a += m;
+                    c += m;
+                    if (a == g.RING) a = 0;
+                    if (c == g.RING) c = 0;
+                }
             }
         }
         if (b + 1 < nsteps) {
