@@ -1326,12 +1326,21 @@ sf_yz_filter(const __grid_constant__ sf_fargs a, const __grid_constant__ sfd_tap
     const int row = (warp % RG) * 8 + (lane & 7);
     const int chunk = (warp / RG) * 4 + (lane >> 3);
     float c[SFD_NZF][SFD_P];
+#if SFD_X2
+#define SFF_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                \
+    if constexpr (RY > 0) {                                                     \
+        sfd_yfilter2<IDX, RY>(slab, U, t);                                      \
+        __syncthreads();                                                        \
+    }                                                                           \
+    sfd_zfilter2<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(slab, U, row, chunk, c, t);
+#else
 #define SFF_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3)                                \
     if constexpr (RY > 0) {                                                     \
         sfd_yfilter<IDX, RY>(slab, U, t);                                       \
         __syncthreads();                                                        \
     }                                                                           \
     sfd_zfilter<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(slab, U, row, chunk, c, t);
+#endif
     SFD_SOURCES(SFF_RUN)
 #undef SFF_RUN
     const i64 y = y0 + row, zb = z0 + 8 * chunk;

@@ -539,6 +539,7 @@ sf_status build_filter(sf_ctx *c, int fi, Launch *L)
     const size_t u_bytes = f.rxy > 0 ? (size_t)sh.WY * sh.UROW * 4 : 0;
     std::string p = "#define SF_KERNEL_FILTER 1\n" + yz_prelude(c, sh, srcs);
     p += "#define SFD_P 8\n";
+    p += std::string("#define SFD_X2 ") + (env_int("SF_NO_X2", 0) ? "0" : "1") + "\n";
     p += "#define SFD_OFF_U " + std::to_string(slab_bytes) + "\n";
     std::string err;
     sf_status s = jit_kernel(p, "sf_yz_filter", c->device, &L->kernel, err);
