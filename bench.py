@@ -277,13 +277,16 @@ def run_ours(args):
                       "tflops": round(st["tflops"], 2),
                       "alu_frac": round(st["tflops"] / alu_peak, 4)}
 
-    # precision form: the same workload with FP16 / BF16 storage (FP32 arithmetic)
+    # precision form: the same workload with FP16 / BF16 storage (FP32 arithmetic),
+    # and FP32 storage with the window moments merged in FP64
     forms = {}
     if not args.no_forms and storage == "f32":
-        for st_name, st_dt in (("f16", torch.float16), ("bf16", torch.bfloat16)):
+        for st_name, st_dt in (("f16", torch.float16), ("bf16", torch.bfloat16),
+                               ("f32_stats_fp64", torch.float32)):
             cq = cube.to(st_dt).contiguous()
-            sq = SourceFinder(w.shape, w.bank, w.truncation, w.window, w.k, storage=st_name,
-                              device=dev)
+            sq = SourceFinder(w.shape, w.bank, w.truncation, w.window, w.k,
+                              storage=st_name if st_dt != torch.float32 else "f32", device=dev,
+                              stats_fp64=st_dt == torch.float32)
             for _ in range(3):
                 sq.detect(cq, mask)
             torch.cuda.synchronize(dev)
@@ -299,7 +302,7 @@ def run_ours(args):
             torch.cuda.synchronize(dev)
             msf = f0.elapsed_time(f1) / n_f
             pq = sq.profile_read()
-            algq = _algorithmic(sq, w, 2)
+            algq = _algorithmic(sq, w, 4 if st_dt == torch.float32 else 2)
             xq = pq[0][0] / n_f
             wq = pq[1][0] / n_f
             forms[st_name] = {

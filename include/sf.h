@@ -75,7 +75,8 @@ typedef struct sf_config {
     int32_t wx, wy, wz;            /* statistics window (>= 1 each) */
     float k;                       /* threshold multiplier */
     int32_t storage;               /* sf_dtype of the cube and the x-filtered scratch */
-    int32_t stats_fp64;            /* reserved, must be 0 */
+    int32_t stats_fp64;            /* window statistics: 0 merges the per-thread FP32 partial
+                                    * moments in FP32, 1 in FP64 (Chan's pairwise merge) */
     int32_t device;                /* CUDA device ordinal, -1 = current device */
 } sf_config;
 

@@ -743,18 +743,28 @@ __device__ __forceinline__ int sfw_la(int lane)
 constexpr int SFW_SLAB_STRIDE = (SFD_OFF_SLAB1 - SFD_OFF_SLAB0) / (int)sizeof(sfd_t);
 constexpr unsigned long long SFW_TIMEOUT_NS = 2000000000ull;
 
-struct sfd_mom { float n, mean, m2; };
+/* the type of the moment merge: FP32, or FP64 for the combine of the
+ * per-thread FP32 partial sums (configuration stats_fp64) */
+#ifndef SFD_STATS64
+#define SFD_STATS64 0
+#endif
+#if SFD_STATS64
+typedef double sfd_st;
+#else
+typedef float sfd_st;
+#endif
+struct sfd_mom { sfd_st n, mean, m2; };
 
 __device__ __forceinline__ sfd_mom sfd_merge(sfd_mom a, sfd_mom b)
 {
-    if (b.n == 0.f) return a;
-    if (a.n == 0.f) return b;
-    const float n = a.n + b.n;
-    const float d = b.mean - a.mean;
-    const float wb = b.n / n;
+    if (b.n == 0) return a;
+    if (a.n == 0) return b;
+    const sfd_st n = a.n + b.n;
+    const sfd_st d = b.mean - a.mean;
+    const sfd_st wb = b.n / n;
     sfd_mom r;
     r.n = n;
-    r.mean = fmaf(d, wb, a.mean);
+    r.mean = fma(d, wb, a.mean);
     r.m2 = a.m2 + b.m2 + d * d * a.n * wb;
     return r;
 }
@@ -791,7 +801,7 @@ struct sfw_state {
     float *U;
     float *pmax;    /* [WX][NWARP][NZF] */
     u32 *mask;      /* [WX][WY][NW] */
-    float *red;     /* [NWARP][NZF][3] */
+    sfd_st *red;    /* [NWARP][NZF][3] */
     float *thr;     /* [NZF] */
     u32 *flags;     /* [2] planes flagged for pass 2 (bit p) */
     u32 bar;        /* two mbarriers, 8 bytes apart */
@@ -1011,10 +1021,34 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
             for (int f = 0; f < NZ; ++f) {
                 s1[f] += f2_lo(s1p[f]) + f2_hi(s1p[f]);
                 s2[f] += f2_lo(s2p[f]) + f2_hi(s2p[f]);
-                sfd_mom m{0.f, 0.f, 0.f};
+                sfd_mom m{0, 0, 0};
+#if SFD_STATS64
+                {
+                    /* FP64 combine: the thread's FP32 sums about its own shift
+                     * K are moved to the warp's shift R (lane 0's K),
+                     *   sum (c - R)   = s1 + n (K - R),
+                     *   sum (c - R)^2 = s2 + (K - R)(2 s1 + n (K - R)),
+                     * summed over the warp in FP64, then turned into moments */
+                    const float R = __shfl_sync(0xffffffffu, K[f], 0);
+                    const double n = (double)cnt, dk = (double)K[f] - (double)R;
+                    double t1 = (double)s1[f] + n * dk;
+                    double t2 = (double)s2[f] + dk * (2.0 * (double)s1[f] + n * dk);
+                    float nw = (float)cnt;
+#pragma unroll
+                    for (int off = 1; off < 32; off <<= 1) {
+                        t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+                        t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+                        nw += __shfl_xor_sync(0xffffffffu, nw, off);
+                    }
+                    if (nw > 0.f) {
+                        const double mu = t1 / (double)nw;
+                        m = sfd_mom{(double)nw, (double)R + mu, fmax(t2 - t1 * mu, 0.0)};
+                    }
+                }
+#else
                 if (cnt > 0) {
-                    const float n = (float)cnt, mu = s1[f] / n;
-                    m = sfd_mom{n, K[f] + mu, fmaxf(s2[f] - s1[f] * mu, 0.f)};
+                    const sfd_st n = (sfd_st)cnt, mu = (sfd_st)s1[f] / n;
+                    m = sfd_mom{n, (sfd_st)K[f] + mu, fmax((sfd_st)s2[f] - (sfd_st)s1[f] * mu, (sfd_st)0)};
                 }
 #pragma unroll
                 for (int off = 1; off < 32; off <<= 1) {
@@ -1024,25 +1058,27 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
                     o.m2 = __shfl_xor_sync(0xffffffffu, m.m2, off);
                     m = (lane & off) ? sfd_merge(o, m) : sfd_merge(m, o);
                 }
+#endif
                 if (lane == 0) {
-                    float *w = S.red + (warp * SFD_NZF + f) * 3;
+                    sfd_st *w = S.red + (warp * SFD_NZF + f) * 3;
                     w[0] = m.n; w[1] = m.mean; w[2] = m.m2;
                 }
             }
             __syncthreads();
             if (threadIdx.x < NZ) {
                 const int f = threadIdx.x;
-                sfd_mom m{0.f, 0.f, 0.f};
+                sfd_mom m{0, 0, 0};
                 for (int w = 0; w < SFD_NWARP; ++w) {
-                    const float *q = S.red + (w * SFD_NZF + f) * 3;
+                    const sfd_st *q = S.red + (w * SFD_NZF + f) * 3;
                     m = sfd_merge(m, sfd_mom{q[0], q[1], q[2]});
                 }
-                const float sd = m.n > 0.f ? sqrtf(m.m2 / m.n) : 0.f;
-                S.thr[f] = fmaf(a.k, sd, m.mean);
+                const sfd_st sd = m.n > 0 ? sqrt(m.m2 / m.n) : (sfd_st)0;
+                /* the threshold in the merge's precision, rounded once */
+                S.thr[f] = (float)fma((sfd_st)a.k, sd, m.mean);
                 if (a.mean != nullptr) {
                     const i64 o = (i64)a.fidx[IDX][f] * a.nwin + S.wid;
-                    a.mean[o] = m.mean;
-                    a.stdv[o] = sd;
+                    a.mean[o] = (float)m.mean;
+                    a.stdv[o] = (float)sd;
                 }
             }
             __syncthreads();
@@ -1111,7 +1147,7 @@ __device__ __forceinline__ void sfw_init(sfw_state &S, unsigned char *raw, bool 
     S.U = reinterpret_cast<float *>(sm + SFD_OFF_U);
     S.pmax = reinterpret_cast<float *>(sm + SFD_OFF_PMAX);
     S.mask = reinterpret_cast<u32 *>(sm + SFD_OFF_MASK);
-    S.red = reinterpret_cast<float *>(sm + SFD_OFF_RED);
+    S.red = reinterpret_cast<sfd_st *>(sm + SFD_OFF_RED);
     S.thr = reinterpret_cast<float *>(sm + SFD_OFF_THR);
     S.flags = reinterpret_cast<u32 *>(sm + SFD_OFF_FLAGS);
     S.bar = sf_smem_addr(sm + SFD_OFF_MBAR);

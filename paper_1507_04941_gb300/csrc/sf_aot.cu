@@ -10,31 +10,36 @@ namespace {
 
 typedef long long i64;
 
+/* moments of a set of values; T = float, or double for the FP64 combine of
+ * the per-thread FP32 partial sums */
+template <class T>
 struct Mom {
-    float n, mean, m2;
+    T n, mean, m2;
 };
 
-__device__ __forceinline__ Mom merge(Mom a, Mom b)
+template <class T>
+__device__ __forceinline__ Mom<T> merge(Mom<T> a, Mom<T> b)
 {
-    if (b.n == 0.f) return a;
-    if (a.n == 0.f) return b;
-    const float n = a.n + b.n;
-    const float d = b.mean - a.mean;
-    const float wb = b.n / n;
-    return Mom{n, fmaf(d, wb, a.mean), a.m2 + b.m2 + d * d * a.n * wb};
+    if (b.n == 0) return a;
+    if (a.n == 0) return b;
+    const T n = a.n + b.n;
+    const T d = b.mean - a.mean;
+    const T wb = b.n / n;
+    return Mom<T>{n, fma(d, wb, a.mean), a.m2 + b.m2 + d * d * a.n * wb};
 }
 
 constexpr int kStatThreads = 256;
 
 /* Window mean and population standard deviation (Sec. 3.3): one CTA per
- * window.  Each thread sums its values shifted by its first value, the
- * per-thread moments are merged pairwise (Chan et al.) across the warp and
- * then across warps in a fixed order. */
+ * window.  Each thread sums its values shifted by its first value (FP32), the
+ * per-thread moments are merged pairwise (Chan et al.) in T across the warp
+ * and then across warps in a fixed order. */
+template <class T>
 __global__ void __launch_bounds__(kStatThreads)
 sf_window_stats_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int wx, int wy, int wz,
                        int nwy, int nwz, float *__restrict__ mean, float *__restrict__ stdv)
 {
-    __shared__ float red[kStatThreads / 32][3];
+    __shared__ T red[kStatThreads / 32][3];
     const int w = blockIdx.x;
     const int a = w / (nwy * nwz), b = (w / nwz) % nwy, e = w % nwz;
     const i64 x0 = (i64)a * wx, y0 = (i64)b * wy, z0 = (i64)e * wz;
@@ -56,16 +61,16 @@ sf_window_stats_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int 
             cnt += 1.f;
         }
     }
-    Mom m{0.f, 0.f, 0.f};
+    Mom<T> m{0, 0, 0};
     if (cnt > 0.f) {
-        const float mu = s1 / cnt;
-        m = Mom{cnt, K + mu, fmaxf(s2 - s1 * mu, 0.f)};
+        const T mu = (T)s1 / (T)cnt;
+        m = Mom<T>{(T)cnt, (T)K + mu, fmax((T)s2 - (T)s1 * mu, (T)0)};
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        Mom o{__shfl_xor_sync(0xffffffffu, m.n, off), __shfl_xor_sync(0xffffffffu, m.mean, off),
-              __shfl_xor_sync(0xffffffffu, m.m2, off)};
+        Mom<T> o{__shfl_xor_sync(0xffffffffu, m.n, off), __shfl_xor_sync(0xffffffffu, m.mean, off),
+                 __shfl_xor_sync(0xffffffffu, m.m2, off)};
         m = (lane & off) ? merge(o, m) : merge(m, o);
     }
     if (lane == 0) {
@@ -75,10 +80,10 @@ sf_window_stats_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        Mom t{0.f, 0.f, 0.f};
-        for (int q = 0; q < kStatThreads / 32; ++q) t = merge(t, Mom{red[q][0], red[q][1], red[q][2]});
-        mean[w] = t.mean;
-        stdv[w] = t.n > 0.f ? sqrtf(t.m2 / t.n) : 0.f;
+        Mom<T> t{0, 0, 0};
+        for (int q = 0; q < kStatThreads / 32; ++q) t = merge(t, Mom<T>{red[q][0], red[q][1], red[q][2]});
+        mean[w] = (float)t.mean;
+        stdv[w] = (float)(t.n > 0 ? sqrt(t.m2 / t.n) : (T)0);
     }
 }
 
@@ -117,12 +122,16 @@ sf_threshold_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int wx,
 }  // namespace
 
 cudaError_t sf_launch_stats(const float *c, long long nx, long long ny, long long nz, int wx, int wy,
-                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv,
+                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv, int fp64,
                             cudaStream_t st)
 {
     const long long nwin = (long long)nwx * nwy * nwz;
-    sf_window_stats_kernel<<<(unsigned)nwin, kStatThreads, 0, st>>>(c, nx, ny, nz, wx, wy, wz, nwy,
-                                                                     nwz, mean, stdv);
+    if (fp64)
+        sf_window_stats_kernel<double><<<(unsigned)nwin, kStatThreads, 0, st>>>(c, nx, ny, nz, wx, wy, wz, nwy,
+                                                                                 nwz, mean, stdv);
+    else
+        sf_window_stats_kernel<float><<<(unsigned)nwin, kStatThreads, 0, st>>>(c, nx, ny, nz, wx, wy, wz, nwy,
+                                                                               nwz, mean, stdv);
     return cudaGetLastError();
 }
 

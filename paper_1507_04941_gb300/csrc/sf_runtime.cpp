@@ -41,7 +41,7 @@ extern "C" const char *sf_embedded_abi_source;      /* sf_kernel_abi.h (generate
 
 /* AOT kernels (sf_aot.cu) */
 cudaError_t sf_launch_stats(const float *c, long long nx, long long ny, long long nz, int wx, int wy,
-                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv,
+                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv, int fp64,
                             cudaStream_t st);
 size_t sf_local_yz_smem(int sy, int sz);
 cudaError_t sf_launch_w_product(const float *d, const float *w, float *p, long long n, cudaStream_t st);
@@ -694,7 +694,7 @@ bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, 
     wp.off_mk = off;
     off += align_up((size_t)g.wx * g.wy * nw * 4, 16);
     wp.off_rd = off;
-    off += align_up((size_t)nwarp * wp.nzf * 3 * 4, 16);
+    off += align_up((size_t)nwarp * wp.nzf * 3 * (c->cfg.stats_fp64 ? 8 : 4), 16);
     wp.off_th = off;
     off += align_up((size_t)wp.nzf * 4, 16);
     wp.off_fl = off;
@@ -722,6 +722,7 @@ bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, 
     p += "#define SFD_OFF_FLAGS " + std::to_string(wp.off_fl) + "\n";
     p += "#define SFD_OFF_MBAR " + std::to_string(wp.off_mb) + "\n";
     if (weighted >= 0) p += "#define SFD_WEIGHTED 1\n";
+    if (c->cfg.stats_fp64) p += "#define SFD_STATS64 1\n";
     wp.prelude = p;
     wp.taps = yz_taps(c, sh, wp.srcs);
     if (weighted == 1) {
@@ -1249,7 +1250,7 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
     if (!std::isfinite(g.k)) return fail(nullptr, SF_EINVAL, "k must be finite");
     if (g.storage != SF_F32 && g.storage != SF_F16 && g.storage != SF_BF16)
         return fail(nullptr, SF_EINVAL, "unknown storage dtype %d", g.storage);
-    if (g.stats_fp64 != 0) return fail(nullptr, SF_EINVAL, "stats_fp64 is reserved and must be 0");
+    if (g.stats_fp64 != 0 && g.stats_fp64 != 1) return fail(nullptr, SF_EINVAL, "stats_fp64 must be 0 or 1");
     for (int i = 0; i < g.n_filters; ++i) {
         const sf_filter_spec &f = g.filters[i];
         if (!(f.sigma_xy >= 0.f) || !(f.sigma_z >= 0.f) || !std::isfinite(f.sigma_xy) ||
@@ -1614,7 +1615,7 @@ sf_status sf_stats(sf_ctx *c, const float *d_filtered, float *d_mean, float *d_s
     DeviceGuard dg(c->device);
     const sf_config &g = c->cfg;
     cudaError_t e = sf_launch_stats(d_filtered, g.nx, g.ny, g.nz, g.wx, g.wy, g.wz, c->nwx, c->nwy,
-                                    c->nwz, d_mean, d_std, (cudaStream_t)stream);
+                                    c->nwz, d_mean, d_std, c->cfg.stats_fp64, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stats launch");
     return SF_OK;
 }

@@ -134,7 +134,7 @@ class SourceFinder:
     """One planned filter bank over cubes of one shape (wraps an sf_ctx)."""
 
     def __init__(self, shape, bank, truncation: float = 3.0, window=(32, 32, 64), k: float = 4.0,
-                 storage: str = "f32", device=None):
+                 storage: str = "f32", device=None, stats_fp64: bool = False):
         import torch
         self.shape = tuple(int(s) for s in shape)
         self.bank = tuple((float(a), float(b)) for a, b in bank)
@@ -149,7 +149,8 @@ class SourceFinder:
         self._specs = specs
         cfg = Config(self.shape[0], self.shape[1], self.shape[2], len(self.bank), specs,
                      self.truncation, self.window[0], self.window[1], self.window[2], self.k,
-                     STORAGE[storage], 0, self.device.index if self.device.index is not None else -1)
+                     STORAGE[storage], 1 if stats_fp64 else 0,
+                     self.device.index if self.device.index is not None else -1)
         h = _vp()
         _check(lib().sf_create(ctypes.byref(cfg), ctypes.byref(h)), None)
         self._h = h

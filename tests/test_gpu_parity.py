@@ -79,13 +79,14 @@ def test_filter_parity_every_bank_filter(dev, oracle, shape):
 
 
 # -------------------------------------------------------------- stats ------
+@pytest.mark.parametrize("stats_fp64", [False, True])
 @pytest.mark.parametrize("window", [(32, 32, 64), (16, 16, 32), (7, 5, 13)])
-def test_stats_parity(dev, oracle, window):
+def test_stats_parity(dev, oracle, window, stats_fp64):
     import torch
     from paper_1507_04941_gb300 import SourceFinder
     shape = (70, 45, 150)
     cube = _cube(shape, seed=22)
-    with SourceFinder(shape, ((1.5, 2.0),), 3.0, window, device=dev) as sf:
+    with SourceFinder(shape, ((1.5, 2.0),), 3.0, window, device=dev, stats_fp64=stats_fp64) as sf:
         c = sf.filter(cube.to(dev), 0)
         # an offset makes the variance cancellation visible
         c += 3.0
@@ -120,12 +121,13 @@ def test_threshold_parity(dev, oracle):
 
 # ------------------------------------------------------------- detect ------
 def _detect_vs_oracle(dev, oracle, shape, bank, window, k=4.0, seed=30, storage="f32",
-                      cube=None, beam=None):
+                      cube=None, beam=None, stats_fp64=False):
     import torch
     from paper_1507_04941_gb300 import SourceFinder, words_to_bits
     if cube is None:
         cube = _cube(shape, seed=seed, n_sources=12, peak=(0.5, 5.0), beam=beam)
-    with SourceFinder(shape, bank, 3.0, window, k=k, storage=storage, device=dev) as sf:
+    with SourceFinder(shape, bank, 3.0, window, k=k, storage=storage, device=dev,
+                      stats_fp64=stats_fp64) as sf:
         mask, mean, std = sf.detect(cube.to(dev), stats=True)
         torch.cuda.synchronize(dev)
         got = words_to_bits(mask.cpu().numpy(), shape[2])
@@ -154,6 +156,13 @@ def test_detect_tiny_workload(dev, oracle):
 @pytest.mark.parametrize("shape", [(72, 50, 200), (96, 64, 128), (40, 33, 70)])
 def test_detect_bank6_ragged(dev, oracle, shape):
     _detect_vs_oracle(dev, oracle, shape, BANK6, (32, 32, 64), beam=1.5)
+
+
+@pytest.mark.parametrize("shape,window", [((72, 50, 200), (32, 32, 64)), ((40, 33, 70), (16, 24, 48))])
+def test_detect_stats_fp64(dev, oracle, shape, window):
+    """FP64 combine of the window moments (fused kernel, and the composed
+    path for the 16x24x48 windows): the same masks and statistics bounds."""
+    _detect_vs_oracle(dev, oracle, shape, BANK6, window, beam=1.5, stats_fp64=True)
 
 
 @pytest.mark.parametrize("window", [(16, 24, 48), (8, 8, 8), (5, 7, 33)])
