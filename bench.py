@@ -268,6 +268,21 @@ def run_ours(args):
                 "unit": "GB/s", "frac": xs["gbs"] / hbm_peak, "traffic": None}
     roof["peak_kind"] = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if roof["bound"] == "hbm" \
         else "derived"
+    # the whole step against HBM under two byte models: the separable passes
+    # materialised (x+y pass read+write per distinct sigma_xy, a z pass per
+    # filter reading t2 and writing the filtered cube, the mask) and this
+    # design's own traffic (the cube and the x-filtered cubes read, the
+    # x-filtered cubes written, the mask)
+    n_xy = len({b[0] for b in w.bank if b[0] > 0})
+    b_pass = nvox * (n_xy * 4 * sbytes + nf * 2 * sbytes + 0.125)
+    b_this = alg["x"][0] + alg["fused"][0]
+    step_models = {
+        "b_pass": {"bytes_per_step": b_pass, "achieved_gbs": b_pass / (ms_step * 1e-3) / 1e9,
+                   "frac_of_measured_hbm": b_pass / (ms_step * 1e-3) / 1e9 / hbm_peak,
+                   "roofline_ms": b_pass / (hbm_peak * 1e9) * 1e3},
+        "this_design": {"bytes_per_step": b_this, "achieved_gbs": b_this / (ms_step * 1e-3) / 1e9,
+                        "frac_of_measured_hbm": b_this / (ms_step * 1e-3) / 1e9 / hbm_peak},
+    }
     other = {}
     for key, st in stages.items():
         other[key] = {"kernel": "sf_xpass" if key == "x" else kname,
@@ -465,7 +480,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({nvox * sbytes / 2**20:.0f} MiB cube, "
                              "129 MB L2)"},
-            "roofline": roof, "kernels": other, "clocks": clocks, "storage_forms": forms,
+            "roofline": roof, "step_hbm_models": step_models, "kernels": other, "clocks": clocks, "storage_forms": forms,
             "local_stats_form": local, "weighted_form": weighted,
             "serving": serving,
             "path": "persistent (x-pass + windows in one launch)" if persistent else

@@ -36,6 +36,8 @@
  */
 #include <cuda_runtime.h>
 
+#include <cstdlib>
+
 namespace {
 
 typedef long long i64;
@@ -445,7 +447,13 @@ struct Kahan {
 
 __device__ __forceinline__ void ldv(const float *p, float *v, int V)
 {
-    if (V == 2) {
+    if (V == 4) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else if (V == 2) {
         const float2 q = *reinterpret_cast<const float2 *>(p);
         v[0] = q.x;
         v[1] = q.y;
@@ -454,29 +462,38 @@ __device__ __forceinline__ void ldv(const float *p, float *v, int V)
     }
 }
 
-/* the low 16 bits of x moved to the even bit positions */
-__device__ __forceinline__ unsigned int spread16(unsigned int x)
+/* bit i of the low 32/V bits of x moved to bit V*i (V = 2: the low 16 bits
+ * to the even positions; V = 4: the low 8 bits to every fourth) */
+template <int V>
+__device__ __forceinline__ unsigned int spread_bits(unsigned int x)
 {
-    x &= 0xffffu;
-    x = (x | (x << 8)) & 0x00ff00ffu;
-    x = (x | (x << 4)) & 0x0f0f0f0fu;
-    x = (x | (x << 2)) & 0x33333333u;
-    x = (x | (x << 1)) & 0x55555555u;
+    if (V == 2) {
+        x &= 0xffffu;
+        x = (x | (x << 8)) & 0x00ff00ffu;
+        x = (x | (x << 4)) & 0x0f0f0f0fu;
+        x = (x | (x << 2)) & 0x33333333u;
+        x = (x | (x << 1)) & 0x55555555u;
+    } else if (V == 4) {
+        x &= 0xffu;
+        x = (x | (x << 12)) & 0x000f000fu;
+        x = (x | (x << 6)) & 0x03030303u;
+        x = (x | (x << 3)) & 0x11111111u;
+    }
     return x;
 }
 
 /* MODE 0: mean / std cubes; 1: mask words set; 2: mask words OR-ed;
  * 3: z-score cube (c - mean) / std, 0 where std = 0, into `mean`.
- * V z per thread (2 when nz is even: 8-byte loads, a warp covers 64 z and
- * two mask words).  Each step's loads are issued one step ahead. */
+ * V consecutive z per thread (V-element loads; a warp covers 32 V z and V
+ * mask words).  Each step's loads are issued one step ahead. */
 template <int MODE, int V>
-__global__ void __launch_bounds__(kXThreads, 8)
+__global__ void __launch_bounds__(kXThreads, V == 4 ? 5 : 8)
     sf_local_x(const float *__restrict__ c, const float *__restrict__ A, const float *__restrict__ M, i64 nx,
                i64 ny, i64 nz, i64 nw32, int sx, int sy, int sz, float k, float *__restrict__ mean,
                float *__restrict__ stdv, unsigned int *__restrict__ mask)
 {
     /* lanes per row: 32 / V per mask word, whole warps per row */
-    const i64 words_pad = V == 2 ? (nw32 + 1) & ~1LL : nw32;
+    const i64 words_pad = (nw32 + V - 1) / V * V;
     const i64 per_row = words_pad * (32 / V);
     const i64 lane = (i64)blockIdx.x * kXThreads + threadIdx.x;
     const i64 y = lane / per_row;
@@ -588,14 +605,16 @@ __global__ void __launch_bounds__(kXThreads, 8)
                 bits[e] = __ballot_sync(0xffffffffu, valid[e] && cv[e] > fmaf(k, sd[e], mu[e]));
             unsigned int word = bits[0];
             i64 wi = lr >> 5;   /* V == 1: word of this warp */
-            if (V == 2) {
-                /* lanes 0 and 1 assemble the warp's two words: word h holds
-                 * lanes 16 h .. 16 h + 15, two bits each */
-                const int h = wl & 1;
-                word = spread16(bits[0] >> (16 * h)) | (spread16(bits[V - 1] >> (16 * h)) << 1);
-                wi = ((lr >> 5) << 1) + h;
+            if (V > 1) {
+                /* lanes 0 .. V-1 assemble the warp's V words: word h holds
+                 * lanes (32/V) h .. (32/V)(h+1) - 1, V bits each */
+                const int h = wl & (V - 1);
+                word = 0;
+#pragma unroll
+                for (int e = 0; e < V; ++e) word |= spread_bits<V>(bits[e] >> ((32 / V) * h)) << e;
+                wi = (lr >> 5) * V + h;
             }
-            if (wl < (V == 2 ? 2 : 1) && wi < nw32) {
+            if (wl < V && wi < nw32) {
                 unsigned int *w = mask + ((i64)x * ny + y) * nw32 + wi;
                 if (MODE == 2) {
                     if (word) atomicOr(w, word);   /* nothing waits on it */
@@ -648,21 +667,29 @@ cudaError_t sf_launch_local_x(const float *c, const float *A, const float *M, lo
                               float *stdv, unsigned int *mask, int mode, cudaStream_t st)
 {
     if (nx > (1LL << 30)) return cudaErrorInvalidValue;
-    const bool v2 = nz % 2 == 0;
-    const long long lanes = v2 ? ny * ((nw32 + 1) & ~1LL) * 16 : ny * nw32 * 32;
-    const dim3 grid((unsigned)((lanes + kXThreads - 1) / kXThreads), (unsigned)((nx + kXSeg - 1) / kXSeg));
-#define SF_LX(MODE, V) sf_local_x<MODE, V><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask)
-    if (v2) {
-        if (mode == 0) SF_LX(0, 2);
-        else if (mode == 1) SF_LX(1, 2);
-        else if (mode == 2) SF_LX(2, 2);
-        else SF_LX(3, 2);
-    } else {
-        if (mode == 0) SF_LX(0, 1);
-        else if (mode == 1) SF_LX(1, 1);
-        else if (mode == 2) SF_LX(2, 1);
-        else SF_LX(3, 1);
+    /* z per thread: 4 when nz is a multiple of 4 (16-byte loads), 2 when
+     * even; SF_LXV caps it (1, 2 or 4) */
+    int V = nz % 4 == 0 ? 4 : nz % 2 == 0 ? 2 : 1;
+    if (const char *e = getenv("SF_LXV")) {
+        const int cap = atoi(e);
+        if (cap == 1 || cap == 2) V = V < cap ? V : cap;
     }
+    const long long lanes = ny * ((nw32 + V - 1) / V * V) * (32 / V);
+    const dim3 grid((unsigned)((lanes + kXThreads - 1) / kXThreads), (unsigned)((nx + kXSeg - 1) / kXSeg));
+#define SF_LX(MODE, VV) sf_local_x<MODE, VV><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask)
+#define SF_LXV(VV)                     \
+    if (mode == 0) SF_LX(0, VV);       \
+    else if (mode == 1) SF_LX(1, VV);  \
+    else if (mode == 2) SF_LX(2, VV);  \
+    else SF_LX(3, VV);
+    if (V == 4) {
+        SF_LXV(4)
+    } else if (V == 2) {
+        SF_LXV(2)
+    } else {
+        SF_LXV(1)
+    }
+#undef SF_LXV
 #undef SF_LX
     return cudaGetLastError();
 }
