@@ -43,7 +43,9 @@ def _assert_stats(gm, gs, rm, rs, rel=1e-5, what=""):
                                         ((12, 33, 65), (0, 0, 0)),       # the voxel itself
                                         ((6, 40, 70), (9, 50, 90)),      # box wider than the cube
                                         ((6, 40, 520), (2, 5, 20)),      # interior z tiles
-                                        ((3, 300, 136), (1, 7, 4))])     # two y segments
+                                        ((3, 300, 136), (1, 7, 4)),      # two y segments
+                                        ((4, 120, 70), (1, 10, 3)),      # y anchors: a block + 4 rows
+                                        ((3, 90, 64), (0, 8, 2))])       # y anchors: one whole block
 def test_local_stats_parity(dev, oracle, shape, half):
     import torch
     from paper_1507_04941_gb300 import SourceFinder
