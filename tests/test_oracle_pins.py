@@ -298,3 +298,35 @@ def test_injected_source_recovered_at_centre(oracle):
     assert bits[20, 27, 50]
     # pure noise elsewhere rarely fires: far below 1% of voxels
     assert bits.mean() < 0.01
+
+
+# ------------------------------------------------- threshold statistics ----
+@pytest.mark.parametrize("k", [3.0, 4.0])
+def test_pure_noise_false_positive_rate(oracle, k):
+    """On iid N(0,1) noise with the identity filter, c > mean + k std fires
+    with probability 1 - Phi(k) per voxel (the window estimates of mean and
+    std over 65536 voxels move that by well under the binomial spread).  A
+    threshold on the variance, a flipped sign or a wrong window would miss
+    this by orders of magnitude."""
+    shape = (128, 128, 256)
+    d = _rng(4242).standard_normal(shape).astype(np.float32)
+    ref = oracle.detect(d, ((0.0, 0.0),), 3.0, (32, 32, 64), k)
+    fired = int(oracle.unpack_bits(ref["mask"], shape[2]).sum())
+    p = 0.5 * math.erfc(k / math.sqrt(2.0))
+    n = d.size
+    expect, sd = n * p, math.sqrt(n * p * (1 - p))
+    assert abs(fired - expect) < 5 * sd + 0.02 * expect, (fired, expect)
+
+
+def test_smoothed_noise_false_positive_rate(oracle):
+    """The same on noise smoothed by the (1.5, 2) filter: the filtered values
+    are Gaussian again and the window statistics follow them, so the rate is
+    still 1 - Phi(k); neighbouring voxels fire together, so the bound is
+    loose (a third of the expectation)."""
+    shape = (96, 96, 256)
+    d = _rng(4343).standard_normal(shape).astype(np.float32)
+    k = 3.0
+    ref = oracle.detect(d, ((1.5, 2.0),), 3.0, (32, 32, 64), k)
+    fired = int(oracle.unpack_bits(ref["mask"], shape[2]).sum())
+    expect = d.size * 0.5 * math.erfc(k / math.sqrt(2.0))
+    assert abs(fired - expect) < expect / 3, (fired, expect)
