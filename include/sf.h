@@ -78,6 +78,9 @@ typedef struct sf_config {
     int32_t stats_fp64;            /* window statistics: 0 merges the per-thread FP32 partial
                                     * moments in FP32, 1 in FP64 (Chan's pairwise merge) */
     int32_t device;                /* CUDA device ordinal, -1 = current device */
+    int32_t std_ddof;              /* standard deviation: squared deviations over n - std_ddof;
+                                    * 0 population (the default), 1 sample; std = 0 when
+                                    * n <= std_ddof.  Applies to every statistic. */
 } sf_config;
 
 /* Create a context: copies cfg, computes the taps (Sec. 2.1: sampled Gaussian

@@ -75,32 +75,33 @@ def _load():
                                                _dp, ctypes.c_int, _dp, ctypes.c_int,
                                                _i64, _i64, _i64]
         lib.or_filter_direct_voxel.restype = ctypes.c_double
-        lib.or_moments.argtypes = [_dp, _i64, _dp, _dp]
+        lib.or_moments.argtypes = [_dp, _i64, ctypes.c_int, _dp, _dp]
         lib.or_moments.restype = None
         lib.or_window_stats.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int,
-                                        ctypes.c_int, _dp, _dp]
+                                        ctypes.c_int, ctypes.c_int, _dp, _dp]
         lib.or_window_stats.restype = ctypes.c_int
         lib.or_threshold.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _dp, _dp, ctypes.c_double,
                                      ctypes.c_double, _u32p, _u32p]
         lib.or_threshold.restype = None
         lib.or_detect_window.argtypes = [_fp, _i64, _i64, _i64, ctypes.c_int, _ip, _dp, _ip,
-                                         _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double, ctypes.c_double, _i64, _i64, _i64,
                                          _dp, _dp, _u8p, _u8p, _dp, _dp]
         lib.or_detect_window.restype = ctypes.c_int
         lib.or_detect.argtypes = [_fp, _i64, _i64, _i64, ctypes.c_int, _ip, _dp, _ip, _dp,
-                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                   ctypes.c_double, _u32p, _u32p, _dp, _dp, ctypes.c_int]
         lib.or_detect.restype = ctypes.c_int
         lib.or_detect_windows.argtypes = [_fp, _i64, _i64, _i64, ctypes.c_int, _ip, _dp, _ip, _dp,
-                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double,
                                           ctypes.c_double, _i64,
                                           ctypes.POINTER(ctypes.c_int64),
                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
         lib.or_detect_windows.restype = ctypes.c_int
         lib.or_local_stats.argtypes = [_dp, _i64, _i64, _i64, ctypes.c_int, ctypes.c_int,
-                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _i64, _dp,
+                                       ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _i64, _dp,
                                        _dp, ctypes.c_int]
         lib.or_local_stats.restype = ctypes.c_int
         lib.or_weighted_filter_box.argtypes = [_fp, _fp, _i64, _i64, _i64, _dp, ctypes.c_int, _dp,
@@ -175,11 +176,12 @@ def filter_direct_voxel(d, sigma_xy: float, sigma_z: float, truncation: float,
 
 
 # --------------------------------------------------------------- stats -------
-def moments(values) -> tuple[float, float]:
+def moments(values, ddof: int = 0) -> tuple[float, float]:
+    """Mean and std (squared deviations over n - ddof: 0 population, 1 sample)."""
     v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).ravel())
     m = ctypes.c_double()
     s = ctypes.c_double()
-    _load().or_moments(_ptr(v, _dp), v.size, ctypes.byref(m), ctypes.byref(s))
+    _load().or_moments(_ptr(v, _dp), v.size, int(ddof), ctypes.byref(m), ctypes.byref(s))
     return m.value, s.value
 
 
@@ -187,15 +189,16 @@ def window_grid(shape, window) -> tuple[int, int, int]:
     return tuple(-(-int(n) // int(w)) for n, w in zip(shape, window))
 
 
-def window_stats(c, window) -> tuple[np.ndarray, np.ndarray]:
-    """Mean and population std per window of a filtered cube, [nwx][nwy][nwz]."""
+def window_stats(c, window, ddof: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Mean and std per window of a filtered cube, [nwx][nwy][nwz] (ddof 0:
+    population std, 1: sample std)."""
     c = np.ascontiguousarray(np.asarray(c), dtype=np.float64)
     nx, ny, nz = c.shape
     wx, wy, wz = window
     grid = window_grid(c.shape, window)
     mean = np.empty(grid, dtype=np.float64)
     std = np.empty(grid, dtype=np.float64)
-    if _load().or_window_stats(_ptr(c, _dp), nx, ny, nz, wx, wy, wz,
+    if _load().or_window_stats(_ptr(c, _dp), nx, ny, nz, wx, wy, wz, int(ddof),
                                _ptr(mean, _dp), _ptr(std, _dp)) != 0:
         raise MemoryError("oracle window_stats: out of memory")
     return mean, std
@@ -235,7 +238,7 @@ def _bank_arrays(bank, truncation):
             np.array(rz, dtype=np.int32), np.concatenate(gz))
 
 
-def detect_window(d, bank, truncation, window, k, widx, band_rel: float = 1e-4):
+def detect_window(d, bank, truncation, window, k, widx, band_rel: float = 1e-4, ddof: int = 0):
     """Whole method on one window (a, b, e); returns a dict of float64/uint8 arrays.
 
     Keys: mean[f], std[f], thr[f], fire/sure [window voxels as x,y,z box], c[f][box].
@@ -259,7 +262,7 @@ def detect_window(d, bank, truncation, window, k, widx, band_rel: float = 1e-4):
     sure = np.empty(n, dtype=np.uint8)
     cv = np.empty((nf, n))
     rc = _load().or_detect_window(_ptr(d, _fp), nx, ny, nz, nf, _ptr(rxy, _ip), _ptr(gxy, _dp),
-                                  _ptr(rz, _ip), _ptr(gz, _dp), wx, wy, wz, float(k),
+                                  _ptr(rz, _ip), _ptr(gz, _dp), wx, wy, wz, int(ddof), float(k),
                                   float(band_rel), a, b, e, _ptr(mean, _dp), _ptr(std, _dp),
                                   _ptr(fire, _u8p), _ptr(sure, _u8p), _ptr(cv, _dp),
                                   _ptr(thr, _dp))
@@ -271,7 +274,8 @@ def detect_window(d, bank, truncation, window, k, widx, band_rel: float = 1e-4):
             "origin": (a * wx, b * wy, e * wz)}
 
 
-def detect(d, bank, truncation, window, k, band_rel: float = 1e-4, nthreads: int = 0):
+def detect(d, bank, truncation, window, k, band_rel: float = 1e-4, nthreads: int = 0,
+           ddof: int = 0):
     """Whole method on the whole cube.
 
     Returns dict: mask, sure (packed uint32 [nx][ny][ceil(nz/32)]), mean, std
@@ -288,7 +292,7 @@ def detect(d, bank, truncation, window, k, band_rel: float = 1e-4, nthreads: int
     mean = np.empty((nf,) + grid)
     std = np.empty((nf,) + grid)
     used = _load().or_detect(_ptr(d, _fp), nx, ny, nz, nf, _ptr(rxy, _ip), _ptr(gxy, _dp),
-                             _ptr(rz, _ip), _ptr(gz, _dp), wx, wy, wz, float(k),
+                             _ptr(rz, _ip), _ptr(gz, _dp), wx, wy, wz, int(ddof), float(k),
                              float(band_rel), _ptr(mask, _u32p), _ptr(sure, _u32p),
                              _ptr(mean, _dp), _ptr(std, _dp), int(nthreads))
     if used < 0:
@@ -297,7 +301,7 @@ def detect(d, bank, truncation, window, k, band_rel: float = 1e-4, nthreads: int
 
 
 def detect_windows(d, bank, truncation, window, k, widx, band_rel: float = 1e-4,
-                   nthreads: int = 0):
+                   nthreads: int = 0, ddof: int = 0):
     """Whole method on a list of windows (n x 3 indices), in parallel.
 
     Returns (fired voxels per window, OpenMP threads used).
@@ -310,7 +314,7 @@ def detect_windows(d, bank, truncation, window, k, widx, band_rel: float = 1e-4,
     fired = np.zeros(idx.shape[0], dtype=np.int64)
     used = _load().or_detect_windows(_ptr(d, _fp), nx, ny, nz, len(bank), _ptr(rxy, _ip),
                                      _ptr(gxy, _dp), _ptr(rz, _ip), _ptr(gz, _dp), wx, wy, wz,
-                                     float(k), float(band_rel), idx.shape[0],
+                                     int(ddof), float(k), float(band_rel), idx.shape[0],
                                      _ptr(idx, ctypes.POINTER(ctypes.c_int64)),
                                      _ptr(fired, ctypes.POINTER(ctypes.c_int64)), int(nthreads))
     if used < 0:
@@ -339,7 +343,7 @@ def unpack_bits(words, nz: int) -> np.ndarray:
 
 
 # ------------------------------------------------- per-voxel local statistics
-def local_stats(c, half, idx=None, nthreads: int = 0) -> tuple[np.ndarray, np.ndarray]:
+def local_stats(c, half, idx=None, nthreads: int = 0, ddof: int = 0) -> tuple[np.ndarray, np.ndarray]:
     """Mean and population std of the filtered cube c over the box of
     half-widths half = (sx, sy, sz) around each voxel, clipped to the cube
     (Sec. 3.3).  idx: flat voxel indices to evaluate (default: all voxels,
@@ -352,24 +356,24 @@ def local_stats(c, half, idx=None, nthreads: int = 0) -> tuple[np.ndarray, np.nd
     if idx is None:
         mean = np.empty(c.shape, dtype=np.float64)
         std = np.empty(c.shape, dtype=np.float64)
-        _load().or_local_stats(_ptr(c, _dp), nx, ny, nz, sx, sy, sz, None, 0,
+        _load().or_local_stats(_ptr(c, _dp), nx, ny, nz, sx, sy, sz, int(ddof), None, 0,
                                _ptr(mean, _dp), _ptr(std, _dp), int(nthreads))
         return mean, std
     idx = np.ascontiguousarray(np.asarray(idx, dtype=np.int64).ravel())
     mean = np.empty(idx.shape, dtype=np.float64)
     std = np.empty(idx.shape, dtype=np.float64)
-    _load().or_local_stats(_ptr(c, _dp), nx, ny, nz, sx, sy, sz,
+    _load().or_local_stats(_ptr(c, _dp), nx, ny, nz, sx, sy, sz, int(ddof),
                            _ptr(idx, ctypes.POINTER(ctypes.c_int64)), idx.size,
                            _ptr(mean, _dp), _ptr(std, _dp), int(nthreads))
     return mean, std
 
 
-def local_zscore(c, half, idx=None) -> np.ndarray:
+def local_zscore(c, half, idx=None, ddof: int = 0) -> np.ndarray:
     """Per-voxel z-score (c - mean) / std over the clipped box of half-widths
     half (Sec. 3.3, the statistics the voxel selection tests against), 0
     where std = 0.  idx: flat voxel indices (default: every voxel)."""
     c = np.ascontiguousarray(np.asarray(c), dtype=np.float64)
-    mean, std = local_stats(c, half, idx)
+    mean, std = local_stats(c, half, idx, ddof=ddof)
     cv = c if idx is None else c.ravel()[np.asarray(idx, dtype=np.int64).ravel()]
     z = np.zeros_like(mean)
     ok = std > 0
@@ -377,7 +381,7 @@ def local_zscore(c, half, idx=None) -> np.ndarray:
     return z
 
 
-def local_detect(d, bank, truncation, half, k, band_rel: float = 1e-4, voxels=None):
+def local_detect(d, bank, truncation, half, k, band_rel: float = 1e-4, voxels=None, ddof: int = 0):
     """The sliding-statistics form of the method (Sec. 3.3 read per voxel):
     every filter of the bank (Eq. 2), the local mean/std of each filtered cube
     over the box `half` around the voxel, c_f > mean_f + k std_f, OR over the
@@ -403,7 +407,7 @@ def local_detect(d, bank, truncation, half, k, band_rel: float = 1e-4, voxels=No
         if nv > 64:
             c = filter_box(d, sxy, szz, truncation)
             flat = (voxels[:, 0] * ny + voxels[:, 1]) * nz + voxels[:, 2]
-            mv[f], sv[f] = local_stats(c, (sx, sy, sz), flat)
+            mv[f], sv[f] = local_stats(c, (sx, sy, sz), flat, ddof=ddof)
             cv[f] = c.ravel()[flat]
         else:
             for i, (x, y, z) in enumerate(voxels):
@@ -411,7 +415,8 @@ def local_detect(d, bank, truncation, half, k, band_rel: float = 1e-4, voxels=No
                        (max(0, z - sz), min(nz, z + sz + 1)))
                 c = filter_box(d, sxy, szz, truncation, box)
                 lx, ly, lz = x - box[0][0], y - box[1][0], z - box[2][0]
-                m, s_ = local_stats(c, (sx, sy, sz), [(lx * c.shape[1] + ly) * c.shape[2] + lz])
+                m, s_ = local_stats(c, (sx, sy, sz), [(lx * c.shape[1] + ly) * c.shape[2] + lz],
+                                    ddof=ddof)
                 mv[f, i], sv[f, i] = m[0], s_[0]
                 cv[f, i] = c[lx, ly, lz]
     thr = mv + k * sv

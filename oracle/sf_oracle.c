@@ -137,8 +137,10 @@ double or_filter_direct_voxel(const float *d, int64_t nx, int64_t ny, int64_t nz
     return s;
 }
 
-/* Population mean and standard deviation of n values, two passes. */
-void or_moments(const double *c, int64_t n, double *mean, double *stdv)
+/* Mean and standard deviation of n values, two passes: the squared
+ * deviations divided by n - ddof (ddof 0: population, 1: sample; 0 when
+ * n <= ddof). */
+void or_moments(const double *c, int64_t n, int ddof, double *mean, double *stdv)
 {
     double s = 0.0;
     for (int64_t i = 0; i < n; ++i) s += c[i];
@@ -146,7 +148,7 @@ void or_moments(const double *c, int64_t n, double *mean, double *stdv)
     double q = 0.0;
     for (int64_t i = 0; i < n; ++i) q += (c[i] - m) * (c[i] - m);
     *mean = m;
-    *stdv = sqrt(q / (double)n);
+    *stdv = n > ddof ? sqrt(q / (double)(n - ddof)) : 0.0;
 }
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -158,7 +160,7 @@ static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
  * mean/stdv are [nwx][nwy][nwz].
  */
 int or_window_stats(const double *c, int64_t nx, int64_t ny, int64_t nz,
-                    int wx, int wy, int wz, double *mean, double *stdv)
+                    int wx, int wy, int wz, int ddof, double *mean, double *stdv)
 {
     const int64_t nwx = ceil_div(nx, wx), nwy = ceil_div(ny, wy), nwz = ceil_div(nz, wz);
     double *buf = (double *)malloc(sizeof(double) * (size_t)wx * wy * wz);
@@ -172,7 +174,7 @@ int or_window_stats(const double *c, int64_t nx, int64_t ny, int64_t nz,
                         for (int64_t z = e * wz; z < nz && z < (e + 1) * wz; ++z)
                             buf[n++] = c[(x * ny + y) * nz + z];
                 const int64_t w = (a * nwy + b) * nwz + e;
-                or_moments(buf, n, &mean[w], &stdv[w]);
+                or_moments(buf, n, ddof, &mean[w], &stdv[w]);
             }
     free(buf);
     return 0;
@@ -222,7 +224,7 @@ void or_threshold(const double *c, int64_t nx, int64_t ny, int64_t nz,
 int or_detect_window(const float *d, int64_t nx, int64_t ny, int64_t nz,
                      int nf, const int *rxy, const double *gxy_all,
                      const int *rz, const double *gz_all,
-                     int wx, int wy, int wz, double k, double band_rel,
+                     int wx, int wy, int wz, int ddof, double k, double band_rel,
                      int64_t a, int64_t b, int64_t e,
                      double *mean, double *stdv, uint8_t *fire, uint8_t *sure,
                      double *cvals, double *thr)
@@ -245,7 +247,7 @@ int or_detect_window(const float *d, int64_t nx, int64_t ny, int64_t nz,
                           x0, x1, y0, y1, z0, z1, 0, c) != 0) {
             free(c); free(amb); free(big); return -1;
         }
-        or_moments(c, n, &mean[f], &stdv[f]);
+        or_moments(c, n, ddof, &mean[f], &stdv[f]);
         const double T = mean[f] + k * stdv[f];
         const double band = band_rel * stdv[f];
         if (thr) thr[f] = T;
@@ -272,7 +274,7 @@ int or_detect_window(const float *d, int64_t nx, int64_t ny, int64_t nz,
 int or_detect(const float *d, int64_t nx, int64_t ny, int64_t nz,
               int nf, const int *rxy, const double *gxy_all,
               const int *rz, const double *gz_all,
-              int wx, int wy, int wz, double k, double band_rel,
+              int wx, int wy, int wz, int ddof, double k, double band_rel,
               uint32_t *mask, uint32_t *sure_words, double *mean, double *stdv,
               int nthreads)
 {
@@ -302,7 +304,7 @@ int or_detect(const float *d, int64_t nx, int64_t ny, int64_t nz,
         double *s = (double *)malloc(sizeof(double) * (size_t)nf);
         if (!fire || !sure || !m || !s ||
             or_detect_window(d, nx, ny, nz, nf, rxy, gxy_all, rz, gz_all, wx, wy, wz,
-                             k, band_rel, a, b, e, m, s, fire, sure, NULL, NULL) != 0) {
+                             ddof, k, band_rel, a, b, e, m, s, fire, sure, NULL, NULL) != 0) {
 #ifdef _OPENMP
 #pragma omp atomic write
 #endif
@@ -353,7 +355,7 @@ int or_detect(const float *d, int64_t nx, int64_t ny, int64_t nz,
 int or_detect_windows(const float *d, int64_t nx, int64_t ny, int64_t nz,
                       int nf, const int *rxy, const double *gxy_all,
                       const int *rz, const double *gz_all,
-                      int wx, int wy, int wz, double k, double band_rel,
+                      int wx, int wy, int wz, int ddof, double k, double band_rel,
                       int64_t n, const int64_t *widx, int64_t *fired, int nthreads)
 {
     int used = 1, failed = 0;
@@ -377,7 +379,7 @@ int or_detect_windows(const float *d, int64_t nx, int64_t ny, int64_t nz,
         double *s = (double *)malloc(sizeof(double) * (size_t)nf);
         int64_t cnt = -1;
         if (fire && sure && m && s &&
-            or_detect_window(d, nx, ny, nz, nf, rxy, gxy_all, rz, gz_all, wx, wy, wz, k, band_rel,
+            or_detect_window(d, nx, ny, nz, nf, rxy, gxy_all, rz, gz_all, wx, wy, wz, ddof, k, band_rel,
                              widx[3 * i], widx[3 * i + 1], widx[3 * i + 2], m, s, fire, sure,
                              NULL, NULL) == 0) {
             const int64_t x0 = widx[3 * i] * wx, y0 = widx[3 * i + 1] * wy, z0 = widx[3 * i + 2] * wz;
@@ -409,7 +411,7 @@ int or_detect_windows(const float *d, int64_t nx, int64_t ny, int64_t nz,
  * value per evaluated voxel, in that order.  Returns the OpenMP threads used.
  */
 int or_local_stats(const double *c, int64_t nx, int64_t ny, int64_t nz, int sx, int sy, int sz,
-                   const int64_t *idx, int64_t n_idx, double *mean, double *stdv, int nthreads)
+                   int ddof, const int64_t *idx, int64_t n_idx, double *mean, double *stdv, int nthreads)
 {
     const int64_t nv = idx ? n_idx : nx * ny * nz;
     int used = 1;
@@ -449,7 +451,7 @@ int or_local_stats(const double *c, int64_t nx, int64_t ny, int64_t nz, int sx, 
                     q += d * d;
                 }
         mean[i] = m;
-        stdv[i] = sqrt(q / (double)n);
+        stdv[i] = n > ddof ? sqrt(q / (double)(n - ddof)) : 0.0;
     }
     return used;
 }

@@ -748,6 +748,9 @@ constexpr unsigned long long SFW_TIMEOUT_NS = 2000000000ull;
 #ifndef SFD_STATS64
 #define SFD_STATS64 0
 #endif
+#ifndef SFD_DDOF
+#define SFD_DDOF 0   /* std over n - SFD_DDOF (1: sample std) */
+#endif
 #if SFD_STATS64
 typedef double sfd_st;
 #else
@@ -1072,7 +1075,7 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
                     const sfd_st *q = S.red + (w * SFD_NZF + f) * 3;
                     m = sfd_merge(m, sfd_mom{q[0], q[1], q[2]});
                 }
-                const sfd_st sd = m.n > 0 ? sqrt(m.m2 / m.n) : (sfd_st)0;
+                const sfd_st sd = m.n > SFD_DDOF ? sqrt(m.m2 / (m.n - SFD_DDOF)) : (sfd_st)0;
                 /* the threshold in the merge's precision, rounded once */
                 S.thr[f] = (float)fma((sfd_st)a.k, sd, m.mean);
                 if (a.mean != nullptr) {

@@ -37,7 +37,7 @@ constexpr int kStatThreads = 256;
 template <class T>
 __global__ void __launch_bounds__(kStatThreads)
 sf_window_stats_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int wx, int wy, int wz,
-                       int nwy, int nwz, float *__restrict__ mean, float *__restrict__ stdv)
+                       int nwy, int nwz, int ddof, float *__restrict__ mean, float *__restrict__ stdv)
 {
     __shared__ T red[kStatThreads / 32][3];
     const int w = blockIdx.x;
@@ -83,7 +83,7 @@ sf_window_stats_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int 
         Mom<T> t{0, 0, 0};
         for (int q = 0; q < kStatThreads / 32; ++q) t = merge(t, Mom<T>{red[q][0], red[q][1], red[q][2]});
         mean[w] = (float)t.mean;
-        stdv[w] = (float)(t.n > 0 ? sqrt(t.m2 / t.n) : (T)0);
+        stdv[w] = (float)(t.n > ddof ? sqrt(t.m2 / (t.n - ddof)) : (T)0);
     }
 }
 
@@ -122,16 +122,16 @@ sf_threshold_kernel(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, int wx,
 }  // namespace
 
 cudaError_t sf_launch_stats(const float *c, long long nx, long long ny, long long nz, int wx, int wy,
-                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv, int fp64,
+                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv, int fp64, int ddof,
                             cudaStream_t st)
 {
     const long long nwin = (long long)nwx * nwy * nwz;
     if (fp64)
         sf_window_stats_kernel<double><<<(unsigned)nwin, kStatThreads, 0, st>>>(c, nx, ny, nz, wx, wy, wz, nwy,
-                                                                                 nwz, mean, stdv);
+                                                                                 nwz, ddof, mean, stdv);
     else
         sf_window_stats_kernel<float><<<(unsigned)nwin, kStatThreads, 0, st>>>(c, nx, ny, nz, wx, wy, wz, nwy,
-                                                                               nwz, mean, stdv);
+                                                                               nwz, ddof, mean, stdv);
     return cudaGetLastError();
 }
 

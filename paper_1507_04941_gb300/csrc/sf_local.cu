@@ -20,7 +20,7 @@
  *                Half-widths up to 2 use direct sums for every output, so that
  *                a one-voxel box gives M = 0 exactly;
  *   sf_local_x   one thread per (y, z) and x segment, marching along x with
- *                compensated (Kahan) running sums over the x box of (A - s),
+ *                compensated (Neumaier) running sums over the x box of (A - s),
  *                (A - s)^2 and M, started from a direct sum with s the
  *                segment's first A; the box statistics then follow from the
  *                parallel-axis rule
@@ -53,6 +53,10 @@ constexpr int kRB = 16;          /* rows per step */
 constexpr int kBS = 16;          /* z block and segment length */
 constexpr int kRS = kMZ + 4;     /* ring row stride: 33 quads (odd) */
 constexpr int kYRows = 256;      /* output rows per CTA at most */
+/* a running sum of squares that falls below 1/kRestart of its largest value
+ * since the chain started is recomputed directly: the rounding error of a
+ * chain of at most 16 steps is then within 2 * 16 * kRestart ulps of it */
+constexpr float kRestart = 4.f;
 
 /* staged row stride: columns up to 131 + 2 sz are read, in float4 quads; an
  * odd number of quads keeps eight rows' quads in distinct banks */
@@ -139,11 +143,27 @@ __device__ __forceinline__ void yz_segment(const float *__restrict__ u, const fl
     for (int i = 0; i < 5; ++i) ld4(ep + 4 * i, E + 4 * i);
     float o4[4];
     o4[0] = acc;
+    float mx = acc;   /* the chain's largest sum of squares since its start */
 #pragma unroll
     for (int i = 1; i < 16; ++i) {
         const float vin = E[SH - 1 + i] - s0, vout = L[i - 1] - s0;
-        if (SQ) acc = fmaf(-vout, vout, fmaf(vin, vin, acc));
-        else acc += vin - vout;
+        if (SQ) {
+            acc = fmaf(-vout, vout, fmaf(vin, vin, acc));
+            mx = fmaxf(mx, acc);
+            if (acc * kRestart < mx) {
+                /* the box has left values far above the rest: the rounding
+                 * left behind by their squares would dominate, so this output
+                 * is summed directly and the chain restarts from it */
+                acc = 0.f;
+                for (int o = 0; o <= 2 * sz; ++o) {
+                    const float d = u[j0 + i + o] - s0;
+                    acc = fmaf(d, d, acc);
+                }
+                mx = acc;
+            }
+        } else {
+            acc += vin - vout;
+        }
         o4[i & 3] = acc;
         if ((i & 3) == 3) st4(ring + j0 + i - 3, o4);
     }
@@ -277,6 +297,7 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
     float *out = (sq ? M : A) + g.plane0 + (i64)g.ys * g.nz + z;
     const int nsteps = (g.NR + kRB - 1) / kRB;
     float acc = 0.f;   /* this lane's y box sum of the current output row */
+    float mx = 0.f;    /* its largest value since the chain's start (sums of squares) */
     if (EDGE) {
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         yz_shift<CH>(U, g, 0, s);
@@ -353,6 +374,7 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
                     for (int i = 0; i < n1; ++i) acc += ring[(sl + i) * kRS + col];
                     for (int i = 0; i < cy_full - n1; ++i) acc += ring[i * kRS + col];
                 }
+                mx = acc;
                 yz_emit(acc, lane, sq, zok, yfull ? rn_full : rcz * __frcp_rn((float)clipped32(g.ys + o, g.sy, g.ny)),
                         s, op);
                 op += g.nz;
@@ -365,19 +387,24 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
                 while (o < o1) {
                     const int m = min(o1 - o, min(g.RING - a, g.RING - c));
                     const float *pin = ring + a * kRS + col, *pout = ring + c * kRS + col;
-                    if (yfull) {
-                        for (int i = 0; i < m; ++i) {
-                            acc += pin[i * kRS] - pout[i * kRS];
-                            yz_emit(acc, lane, sq, zok, rn_full, s, op);
-                            op += g.nz;
+                    for (int i = 0; i < m; ++i) {
+                        acc += pin[i * kRS] - pout[i * kRS];
+                        mx = fmaxf(mx, acc);
+                        if (sq && acc * kRestart < mx) {
+                            /* restart the sum of squares from a direct sum
+                             * over rows o+i .. o+i+2 sy (see kRestart) */
+                            int sl = c + i + 1;   /* slot of row o + i */
+                            if (sl >= g.RING) sl -= g.RING;
+                            const int n1 = min(cy_full, g.RING - sl);
+                            acc = 0.f;
+                            for (int r = 0; r < n1; ++r) acc += ring[(sl + r) * kRS + col];
+                            for (int r = 0; r < cy_full - n1; ++r) acc += ring[r * kRS + col];
+                            mx = acc;
                         }
-                    } else {
-                        for (int i = 0; i < m; ++i) {
-                            acc += pin[i * kRS] - pout[i * kRS];
-                            yz_emit(acc, lane, sq, zok,
-                                    rcz * __frcp_rn((float)clipped32(g.ys + o + i, g.sy, g.ny)), s, op);
-                            op += g.nz;
-                        }
+                        yz_emit(acc, lane, sq, zok,
+                                yfull ? rn_full : rcz * __frcp_rn((float)clipped32(g.ys + o + i, g.sy, g.ny)),
+                                s, op);
+                        op += g.nz;
                     }
                     o += m;
                     a += m;
@@ -419,9 +446,34 @@ __global__ void __launch_bounds__(kMT, 3) sf_local_yz(const float *__restrict__ 
     g.NR = g.nout + 2 * sy;
     g.zst = (int)blockIdx.x * kMZ - hz;      /* 16-byte aligned first staged column */
     g.zt0 = g.zst + sz;                      /* first output column */
-    /* the segment's shift: a value of the data near its centre */
-    const int yc = g.ys + g.nout / 2, zc = min(g.nz - 1, max(g.zt0 + kMZ / 2, 0));
-    const float s = c[g.plane0 + (i64)yc * g.nz + zc];
+    /* the segment's shift: the mean of the tile's columns on its centre row,
+     * so that the shifted sums stay near the local means and the second
+     * moments do not cancel */
+    __shared__ float sred[2 * (kMT / 32)];
+    float s;
+    {
+        const int yc = g.ys + g.nout / 2;
+        const int zq = g.zt0 + (int)(threadIdx.x & (kMZ - 1));
+        const bool in = threadIdx.x < kMZ && zq >= 0 && zq < g.nz;
+        float v = in ? c[g.plane0 + (i64)yc * g.nz + zq] : 0.f, n = in ? 1.f : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, off);
+            n += __shfl_xor_sync(0xffffffffu, n, off);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sred[threadIdx.x >> 5] = v;
+            sred[kMT / 32 + (threadIdx.x >> 5)] = n;
+        }
+        __syncthreads();
+        float sv = 0.f, sn = 0.f;
+#pragma unroll
+        for (int w = 0; w < kMT / 32; ++w) {
+            sv += sred[w];
+            sn += sred[kMT / 32 + w];
+        }
+        s = sn > 0.f ? sv / sn : 0.f;
+    }
     if (g.zst >= 0 && g.zst + g.SW <= g.nz) {
         /* interior tile: every staged value is data; subtract s on the fly */
         yz_stage<CH, false>(sm, g, 0);
@@ -434,15 +486,20 @@ __global__ void __launch_bounds__(kMT, 3) sf_local_yz(const float *__restrict__ 
 }
 
 /* compensated running sum */
-struct Kahan {
+/* compensated running sum (Neumaier): each addition's rounding error is
+ * recovered exactly by the branch-free two-sum and accumulated in comp, so a
+ * large term that enters and later leaves a small sum leaves no residue
+ * (Kahan's form assumes the sum outweighs the term and does not) */
+struct CompSum {
     float s = 0.f, comp = 0.f;
     __device__ __forceinline__ void add(float v)
     {
-        const float y = v - comp;
-        const float t = s + y;
-        comp = (t - s) - y;
+        const float t = s + v;
+        const float bp = t - s;
+        comp += (s - (t - bp)) + (v - bp);
         s = t;
     }
+    __device__ __forceinline__ float value() const { return s + comp; }
 };
 
 __device__ __forceinline__ void ldv(const float *p, float *v, int V)
@@ -487,9 +544,9 @@ __device__ __forceinline__ unsigned int spread_bits(unsigned int x)
  * V consecutive z per thread (V-element loads; a warp covers 32 V z and V
  * mask words).  Each step's loads are issued one step ahead. */
 template <int MODE, int V>
-__global__ void __launch_bounds__(kXThreads, V == 4 ? 5 : 8)
+__global__ void __launch_bounds__(kXThreads, V == 4 ? 4 : 8)
     sf_local_x(const float *__restrict__ c, const float *__restrict__ A, const float *__restrict__ M, i64 nx,
-               i64 ny, i64 nz, i64 nw32, int sx, int sy, int sz, float k, float *__restrict__ mean,
+               i64 ny, i64 nz, i64 nw32, int sx, int sy, int sz, int ddof, float k, float *__restrict__ mean,
                float *__restrict__ stdv, unsigned int *__restrict__ mask)
 {
     /* lanes per row: 32 / V per mask word, whole warps per row */
@@ -521,7 +578,7 @@ __global__ void __launch_bounds__(kXThreads, V == 4 ? 5 : 8)
      * so the running updates neither drift nor cancel */
     float s[V];
     ldv(pa + (i64)x0 * plane, s, V);
-    Kahan sa[V], sb[V], sm[V];   /* sums over the x box of A - s, (A - s)^2, M */
+    CompSum sa[V], sb[V], sm[V];   /* sums over the x box of A - s, (A - s)^2, M */
     {
         const int lo = max(x0 - sx, 0), hi = min(x0 + sx, nxi - 1);
         for (int xi = lo; xi <= hi; ++xi) {
@@ -580,12 +637,19 @@ __global__ void __launch_bounds__(kXThreads, V == 4 ? 5 : 8)
                 mu[e] = a1[e];
                 m2 = m1[e];
             } else {
-                const float da = sa[e].s * rX;
+                const float Sa = sa[e].value(), Sb = sb[e].value(), Sm = sm[e].value();
+                const float da = Sa * rX;
                 mu[e] = s[e] + da;
                 /* a rounded product (no contraction into an fma) */
-                m2 = sm[e].s + nyz[e] * fmaxf(sb[e].s - __fmul_rn(sa[e].s, da), 0.f);
+                m2 = Sm + nyz[e] * fmaxf(Sb - __fmul_rn(Sa, da), 0.f);
             }
-            sd[e] = sqrtf(m2 * rX * rnyz[e]);
+            if (ddof == 0) {
+                sd[e] = sqrtf(m2 * rX * rnyz[e]);
+            } else {
+                /* sample std: over n - 1 */
+                const float nn = (float)X * nyz[e] - 1.f;
+                sd[e] = nn > 0.f ? sqrtf(m2 / nn) : 0.f;
+            }
         }
         if (MODE == 0) {
 #pragma unroll
@@ -643,6 +707,12 @@ cudaError_t sf_launch_local_yz(const float *c, float *A, float *M, long long nx,
                                int sz, cudaStream_t st)
 {
     if (ny > (1LL << 30) || nz > (1LL << 30)) return cudaErrorInvalidValue;
+    if (sy == 0 && sz == 0) {
+        /* the y-z box is the voxel: A = c and M = 0 exactly */
+        const size_t bytes = (size_t)(nx * ny * nz) * sizeof(float);
+        cudaError_t e = cudaMemcpyAsync(A, c, bytes, cudaMemcpyDeviceToDevice, st);
+        return e == cudaSuccess ? cudaMemsetAsync(M, 0, bytes, st) : e;
+    }
     const size_t smem = sf_local_yz_smem(sy, sz);
     /* y segments of at most kYRows rows, split evenly */
     const long long nseg = (ny + kYRows - 1) / kYRows;
@@ -664,19 +734,21 @@ cudaError_t sf_launch_local_yz(const float *c, float *A, float *M, long long nx,
 
 cudaError_t sf_launch_local_x(const float *c, const float *A, const float *M, long long nx, long long ny,
                               long long nz, long long nw32, int sx, int sy, int sz, float k, float *mean,
-                              float *stdv, unsigned int *mask, int mode, cudaStream_t st)
+                              float *stdv, unsigned int *mask, int mode, int ddof, cudaStream_t st)
 {
     if (nx > (1LL << 30)) return cudaErrorInvalidValue;
-    /* z per thread: 4 when nz is a multiple of 4 (16-byte loads), 2 when
-     * even; SF_LXV caps it (1, 2 or 4) */
-    int V = nz % 4 == 0 ? 4 : nz % 2 == 0 ? 2 : 1;
+    /* z per thread: 2 when nz is even (8-byte loads), else 1; SF_LXV = 4
+     * takes four where nz allows (16-byte loads, 120 registers: measured
+     * slower with the compensated sums), SF_LXV = 1 one */
+    int V = nz % 2 == 0 ? 2 : 1;
     if (const char *e = getenv("SF_LXV")) {
-        const int cap = atoi(e);
-        if (cap == 1 || cap == 2) V = V < cap ? V : cap;
+        const int want = atoi(e);
+        if (want == 4 && nz % 4 == 0) V = 4;
+        else if (want == 1) V = 1;
     }
     const long long lanes = ny * ((nw32 + V - 1) / V * V) * (32 / V);
     const dim3 grid((unsigned)((lanes + kXThreads - 1) / kXThreads), (unsigned)((nx + kXSeg - 1) / kXSeg));
-#define SF_LX(MODE, VV) sf_local_x<MODE, VV><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, k, mean, stdv, mask)
+#define SF_LX(MODE, VV) sf_local_x<MODE, VV><<<grid, kXThreads, 0, st>>>(c, A, M, nx, ny, nz, nw32, sx, sy, sz, ddof, k, mean, stdv, mask)
 #define SF_LXV(VV)                     \
     if (mode == 0) SF_LX(0, VV);       \
     else if (mode == 1) SF_LX(1, VV);  \

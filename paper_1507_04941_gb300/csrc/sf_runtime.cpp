@@ -41,7 +41,7 @@ extern "C" const char *sf_embedded_abi_source;      /* sf_kernel_abi.h (generate
 
 /* AOT kernels (sf_aot.cu) */
 cudaError_t sf_launch_stats(const float *c, long long nx, long long ny, long long nz, int wx, int wy,
-                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv, int fp64,
+                            int wz, int nwx, int nwy, int nwz, float *mean, float *stdv, int fp64, int ddof,
                             cudaStream_t st);
 size_t sf_local_yz_smem(int sy, int sz);
 cudaError_t sf_launch_w_product(const float *d, const float *w, float *p, long long n, cudaStream_t st);
@@ -50,7 +50,7 @@ cudaError_t sf_launch_local_yz(const float *c, float *P, float *Q, long long nx,
                                int sz, cudaStream_t st);
 cudaError_t sf_launch_local_x(const float *c, const float *P, const float *Q, long long nx, long long ny,
                               long long nz, long long nw32, int sx, int sy, int sz, float k, float *mean,
-                              float *stdv, unsigned int *mask, int mode, cudaStream_t st);
+                              float *stdv, unsigned int *mask, int mode, int ddof, cudaStream_t st);
 cudaError_t sf_launch_threshold(const float *c, long long nx, long long ny, long long nz, int wx,
                                 int wy, int wz, int nwy, int nwz, const float *mean,
                                 const float *stdv, float k, unsigned int *mask, int accumulate,
@@ -723,6 +723,7 @@ bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, 
     p += "#define SFD_OFF_MBAR " + std::to_string(wp.off_mb) + "\n";
     if (weighted >= 0) p += "#define SFD_WEIGHTED 1\n";
     if (c->cfg.stats_fp64) p += "#define SFD_STATS64 1\n";
+    if (c->cfg.std_ddof) p += "#define SFD_DDOF 1\n";
     wp.prelude = p;
     wp.taps = yz_taps(c, sh, wp.srcs);
     if (weighted == 1) {
@@ -1251,6 +1252,7 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
     if (g.storage != SF_F32 && g.storage != SF_F16 && g.storage != SF_BF16)
         return fail(nullptr, SF_EINVAL, "unknown storage dtype %d", g.storage);
     if (g.stats_fp64 != 0 && g.stats_fp64 != 1) return fail(nullptr, SF_EINVAL, "stats_fp64 must be 0 or 1");
+    if (g.std_ddof != 0 && g.std_ddof != 1) return fail(nullptr, SF_EINVAL, "std_ddof must be 0 or 1");
     for (int i = 0; i < g.n_filters; ++i) {
         const sf_filter_spec &f = g.filters[i];
         if (!(f.sigma_xy >= 0.f) || !(f.sigma_z >= 0.f) || !std::isfinite(f.sigma_xy) ||
@@ -1615,7 +1617,8 @@ sf_status sf_stats(sf_ctx *c, const float *d_filtered, float *d_mean, float *d_s
     DeviceGuard dg(c->device);
     const sf_config &g = c->cfg;
     cudaError_t e = sf_launch_stats(d_filtered, g.nx, g.ny, g.nz, g.wx, g.wy, g.wz, c->nwx, c->nwy,
-                                    c->nwz, d_mean, d_std, c->cfg.stats_fp64, (cudaStream_t)stream);
+                                    c->nwz, d_mean, d_std, c->cfg.stats_fp64, c->cfg.std_ddof,
+                                    (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stats launch");
     return SF_OK;
 }
@@ -2098,7 +2101,7 @@ sf_status sf_local_stats(sf_ctx *c, const float *d_filtered, int32_t sx, int32_t
     cudaError_t e = sf_launch_local_yz(d_filtered, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
     if (e == cudaSuccess)
         e = sf_launch_local_x(d_filtered, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_mean, d_std,
-                              nullptr, 0, st);
+                              nullptr, 0, g.std_ddof, st);
     return e == cudaSuccess ? SF_OK : cuda_fail(c, e, "local statistics launch");
 }
 
@@ -2117,7 +2120,7 @@ sf_status sf_local_zscore(sf_ctx *c, const float *d_filtered, int32_t sx, int32_
     cudaError_t e = sf_launch_local_yz(d_filtered, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
     if (e == cudaSuccess)
         e = sf_launch_local_x(d_filtered, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_z, nullptr,
-                              nullptr, 3, st);
+                              nullptr, 3, g.std_ddof, st);
     return e == cudaSuccess ? SF_OK : cuda_fail(c, e, "local z-score launch");
 }
 
@@ -2138,7 +2141,7 @@ sf_status sf_local_detect(sf_ctx *c, const void *d_cube, int32_t sx, int32_t sy,
         cudaError_t e = sf_launch_local_yz(F, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
         if (e == cudaSuccess)
             e = sf_launch_local_x(F, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, nullptr, nullptr, d_mask,
-                                  f == 0 ? 1 : 2, st);
+                                  f == 0 ? 1 : 2, g.std_ddof, st);
         if (e != cudaSuccess) return cuda_fail(c, e, "local detect launch");
     }
     return SF_OK;

@@ -37,7 +37,8 @@ class Config(ctypes.Structure):
                 ("n_filters", ctypes.c_int32), ("filters", ctypes.POINTER(FilterSpec)),
                 ("truncation", ctypes.c_float), ("wx", ctypes.c_int32), ("wy", ctypes.c_int32),
                 ("wz", ctypes.c_int32), ("k", ctypes.c_float), ("storage", ctypes.c_int32),
-                ("stats_fp64", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("stats_fp64", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("std_ddof", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -134,7 +135,7 @@ class SourceFinder:
     """One planned filter bank over cubes of one shape (wraps an sf_ctx)."""
 
     def __init__(self, shape, bank, truncation: float = 3.0, window=(32, 32, 64), k: float = 4.0,
-                 storage: str = "f32", device=None, stats_fp64: bool = False):
+                 storage: str = "f32", device=None, stats_fp64: bool = False, std_ddof: int = 0):
         import torch
         self.shape = tuple(int(s) for s in shape)
         self.bank = tuple((float(a), float(b)) for a, b in bank)
@@ -150,7 +151,7 @@ class SourceFinder:
         cfg = Config(self.shape[0], self.shape[1], self.shape[2], len(self.bank), specs,
                      self.truncation, self.window[0], self.window[1], self.window[2], self.k,
                      STORAGE[storage], 1 if stats_fp64 else 0,
-                     self.device.index if self.device.index is not None else -1)
+                     self.device.index if self.device.index is not None else -1, int(std_ddof))
         h = _vp()
         _check(lib().sf_create(ctypes.byref(cfg), ctypes.byref(h)), None)
         self._h = h

@@ -67,7 +67,7 @@ def _cfg(sf, **kw):
 
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(nz=-3), dict(n_filters=0), dict(truncation=0.0),
-                                 dict(wx=0), dict(storage=7), dict(stats_fp64=2),
+                                 dict(wx=0), dict(storage=7), dict(stats_fp64=2), dict(std_ddof=2),
                                  dict(bank=((-1.0, 2.0),)), dict(bank=((1.0, 40.0),)),
                                  dict(filters=None)])
 def test_invalid_config_rejected_on_host(libsf, bad):

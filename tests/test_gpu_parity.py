@@ -121,18 +121,18 @@ def test_threshold_parity(dev, oracle):
 
 # ------------------------------------------------------------- detect ------
 def _detect_vs_oracle(dev, oracle, shape, bank, window, k=4.0, seed=30, storage="f32",
-                      cube=None, beam=None, stats_fp64=False):
+                      cube=None, beam=None, stats_fp64=False, std_ddof=0):
     import torch
     from paper_1507_04941_gb300 import SourceFinder, words_to_bits
     if cube is None:
         cube = _cube(shape, seed=seed, n_sources=12, peak=(0.5, 5.0), beam=beam)
     with SourceFinder(shape, bank, 3.0, window, k=k, storage=storage, device=dev,
-                      stats_fp64=stats_fp64) as sf:
+                      stats_fp64=stats_fp64, std_ddof=std_ddof) as sf:
         mask, mean, std = sf.detect(cube.to(dev), stats=True)
         torch.cuda.synchronize(dev)
         got = words_to_bits(mask.cpu().numpy(), shape[2])
         gm, gs = mean.cpu().numpy(), std.cpu().numpy()
-    ref = oracle.detect(cube.numpy(), bank, 3.0, window, k)
+    ref = oracle.detect(cube.numpy(), bank, 3.0, window, k, ddof=std_ddof)
     want = oracle.unpack_bits(ref["mask"], shape[2])
     sure = oracle.unpack_bits(ref["sure"], shape[2])
     _assert_mask(got, want, sure, f"detect {shape} {window}")
@@ -163,6 +163,26 @@ def test_detect_stats_fp64(dev, oracle, shape, window):
     """FP64 combine of the window moments (fused kernel, and the composed
     path for the 16x24x48 windows): the same masks and statistics bounds."""
     _detect_vs_oracle(dev, oracle, shape, BANK6, window, beam=1.5, stats_fp64=True)
+
+
+@pytest.mark.parametrize("shape,window", [((72, 50, 200), (32, 32, 64)), ((40, 33, 70), (8, 8, 8))])
+def test_detect_sample_std(dev, oracle, shape, window):
+    """std_ddof = 1 (squared deviations over n - 1) in the fused kernel and in
+    the composed path (8x8x8 windows), against the oracle with ddof = 1."""
+    _detect_vs_oracle(dev, oracle, shape, BANK6, window, beam=1.5, std_ddof=1)
+
+
+def test_stats_sample_std(dev, oracle):
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder
+    shape, window = (70, 45, 150), (16, 16, 32)
+    cube = _cube(shape, seed=24)
+    with SourceFinder(shape, ((1.5, 2.0),), 3.0, window, device=dev, std_ddof=1) as sf:
+        c = sf.filter(cube.to(dev), 0)
+        mean, std = sf.stats(c)
+        torch.cuda.synchronize(dev)
+        rm, rs = oracle.window_stats(c.cpu().numpy().astype(np.float64), window, ddof=1)
+        _assert_stats(mean.cpu().numpy(), std.cpu().numpy(), rm, rs, what="sample std")
 
 
 @pytest.mark.parametrize("window", [(16, 24, 48), (8, 8, 8), (5, 7, 33)])

@@ -146,3 +146,17 @@ def test_zscore_brute_force_and_sampled(oracle, rng):
                 assert z[x, y, q] == pytest.approx((c[x, y, q] - blk.mean()) / blk.std(), rel=1e-10)
     idx = np.array([0, 17, 101, c.size - 1])
     assert np.allclose(oracle.local_zscore(c, half, idx), z.ravel()[idx], rtol=1e-14, atol=0)
+
+
+def test_local_sample_std_flag(oracle, rng):
+    """ddof = 1 in the local statistics: numpy's std(ddof=1) of the clipped box."""
+    c = rng.normal(size=(5, 6, 9)) + 2.0
+    half = (1, 2, 3)
+    m, s = oracle.local_stats(c, half, ddof=1)
+    for x in range(5):
+        for y in range(6):
+            for z in range(9):
+                blk = c[max(0, x - 1):x + 2, max(0, y - 2):y + 3, max(0, z - 3):z + 4]
+                assert s[x, y, z] == pytest.approx(blk.std(ddof=1), rel=1e-12)
+    _, s0 = oracle.local_stats(c, (0, 0, 0), ddof=1)
+    assert (s0 == 0).all()

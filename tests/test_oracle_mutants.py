@@ -26,7 +26,9 @@ MUTANTS = {
         "if (x < 0 || y < 0 || z < 0 || x >= nx || y >= ny || z >= nz) return 0.0;",
         "if (x < 0) x = 0; if (y < 0) y = 0; if (z < 0) z = 0;"
         " if (x >= nx) x = nx - 1; if (y >= ny) y = ny - 1; if (z >= nz) z = nz - 1;"),
-    "sample_std": ("*stdv = sqrt(q / (double)n);", "*stdv = sqrt(q / (double)(n > 1 ? n - 1 : 1));"),
+    "sample_std": ("*stdv = n > ddof ? sqrt(q / (double)(n - ddof)) : 0.0;",
+                   "*stdv = n > 1 ? sqrt(q / (double)(n - 1)) : 0.0;"),
+    "ddof_ignored": ("*stdv = n > ddof ? sqrt(q / (double)(n - ddof)) : 0.0;", "*stdv = sqrt(q / (double)n);"),
     "threshold_not_strict": ("if (v > T) mask[word] |= bit;", "if (v >= T) mask[word] |= bit;"),
     "bit_order_reversed": ("const uint32_t bit = 1u << (z % 32);\n                if (v > T)",
                            "const uint32_t bit = 1u << (31 - z % 32);\n                if (v > T)"),
@@ -43,8 +45,10 @@ LOCAL_MUTANTS = {
                                 "x1 = x + sx >= nx ? nx - 2 : x + sx;"),
     "local_y_uses_z_half_width": ("y0 = y - sy < 0 ? 0 : y - sy, y1 = y + sy >= ny ? ny - 1 : y + sy;",
                                   "y0 = y - sz < 0 ? 0 : y - sz, y1 = y + sz >= ny ? ny - 1 : y + sz;"),
-    "local_sample_std": ("stdv[i] = sqrt(q / (double)n);",
-                         "stdv[i] = sqrt(q / (double)(n > 1 ? n - 1 : 1));"),
+    "local_sample_std": ("stdv[i] = n > ddof ? sqrt(q / (double)(n - ddof)) : 0.0;",
+                         "stdv[i] = n > 1 ? sqrt(q / (double)(n - 1)) : 0.0;"),
+    "local_ddof_ignored": ("stdv[i] = n > ddof ? sqrt(q / (double)(n - ddof)) : 0.0;",
+                           "stdv[i] = sqrt(q / (double)n);"),
 }
 
 

@@ -330,3 +330,42 @@ def test_smoothed_noise_false_positive_rate(oracle):
     fired = int(oracle.unpack_bits(ref["mask"], shape[2]).sum())
     expect = d.size * 0.5 * math.erfc(k / math.sqrt(2.0))
     assert abs(fired - expect) < expect / 3, (fired, expect)
+
+
+# ------------------------------------------------- std normaliser (ddof) ----
+def test_sample_std_flag_equals_numpy(oracle):
+    """ddof = 1 divides the squared deviations by n - 1 (numpy's ddof): per
+    window, tail windows included, and through the detect path's statistics;
+    a window of one voxel has std 0."""
+    c = _rng(77).normal(size=(7, 9, 20)) * 2.0 + 1.0
+    window = (3, 4, 8)
+    m1, s1 = oracle.window_stats(c, window, ddof=1)
+    for a in range(m1.shape[0]):
+        for b in range(m1.shape[1]):
+            for e in range(m1.shape[2]):
+                blk = c[3 * a:3 * a + 3, 4 * b:4 * b + 4, 8 * e:8 * e + 8]
+                assert m1[a, b, e] == pytest.approx(blk.mean(), rel=1e-13)
+                assert s1[a, b, e] == pytest.approx(blk.std(ddof=1), rel=1e-13)
+    m, s = oracle.moments([3.5], ddof=1)
+    assert (m, s) == (3.5, 0.0)
+    d = c.astype(np.float32)
+    r0 = oracle.detect(d, ((0.0, 0.0),), 3.0, window, 1.0)
+    r1 = oracle.detect(d, ((0.0, 0.0),), 3.0, window, 1.0, ddof=1)
+    m0, s0 = oracle.window_stats(d.astype(np.float64), window)
+    np.testing.assert_allclose(r1["std"][0], s0 * np.sqrt(_counts(d.shape, window) / (_counts(d.shape, window) - 1)),
+                               rtol=1e-12)
+    assert oracle.unpack_bits(r1["mask"], 20).sum() < oracle.unpack_bits(r0["mask"], 20).sum()
+
+
+def _counts(shape, window):
+    n = np.ones(oracle_grid(shape, window))
+    for ax, (N, w) in enumerate(zip(shape, window)):
+        ext = np.array([min(w, N - i * w) for i in range(-(-N // w))], dtype=float)
+        sh = [1, 1, 1]
+        sh[ax] = -1
+        n = n * ext.reshape(sh)
+    return n
+
+
+def oracle_grid(shape, window):
+    return tuple(-(-N // w) for N, w in zip(shape, window))
