@@ -3,22 +3,26 @@
  * standard deviation of each voxel come from a user-specified range of the
  * filtered data around it), read as the box [x-sx, x+sx] x [y-sy, y+sy] x
  * [z-sz, z+sz] clipped to the cube, with n the number of voxels of the clipped
- * box; population statistics.  The box sums are separable, as in the paper's
- * three directional sums:
+ * box; population statistics (sample statistics, over n - 1, on request).
+ * The box sums are separable, as in the paper's three directional sums:
  *
  *   sf_local_yz  one CTA per (x, 128-column z tile, y segment of up to 256
  *                rows) marching along y in steps of 16 rows.  Each step
  *                stages 16 rows of the tile with their z halo (cp.async, zeros
  *                outside the cube), forms the z box sums of (c - s) and
- *                (c - s)^2 of every row (s: one value of the data near the
- *                segment's centre) as running sums over 16-column segments
- *                started from 16-column block sums, and pushes them into a
- *                ring of the last 2 sy + 17 rows.  The y box sums run down
- *                the ring, one thread per column, restarted from a direct sum
- *                every 16 rows.  Each voxel's y-z box mean A and second central
- *                moment M = sum (c - A)^2 are written as two float32 cubes.
- *                Half-widths up to 2 use direct sums for every output, so that
- *                a one-voxel box gives M = 0 exactly;
+ *                (c - s)^2 of every row (s: the mean of the tile's centre
+ *                row) as running sums over 16-column segments started from
+ *                16-column block sums, and pushes them into a ring of the
+ *                last 2 sy + 17 rows.  The y box sums run down the ring, two
+ *                lanes per column (one per sum), restarted from a direct sum
+ *                at every step of 16 rows.  A sum of squares that falls below
+ *                a quarter of its largest value since its chain started is
+ *                recomputed directly (the rounding left by large values that
+ *                entered and left would otherwise dominate).  Each voxel's y-z
+ *                box mean A and second central moment M = sum (c - A)^2 are
+ *                written as two float32 cubes.  Half-widths up to 2 use
+ *                direct sums for every output; a one-voxel y-z box is a copy
+ *                (A = c, M = 0);
  *   sf_local_x   one thread per (y, z) and x segment, marching along x with
  *                compensated (Neumaier) running sums over the x box of (A - s),
  *                (A - s)^2 and M, started from a direct sum with s the
@@ -29,10 +33,12 @@
  *                (X planes of n_yz voxels each), var = M2 / (X n_yz); either
  *                the mean / std cubes are written or the selection
  *                c > mean + k std is packed into the mask words by a warp
- *                ballot (one warp = 32 consecutive z of one row), OR-ed into
+ *                ballot (V z per thread, V mask words per warp), OR-ed into
  *                the words already there when the mask accumulates a bank.
- * Shifting by a value of the data keeps the second moments from cancelling
- * when the local mean is large against the local spread.
+ * Shifting by values of the data keeps the second moments from cancelling
+ * when the local mean is large against the local spread.  The FP32 sums still
+ * lose precision where the box's spread is small against the distance from
+ * its mean to the shift (boxes one voxel wide on smooth data).
  */
 #include <cuda_runtime.h>
 
