@@ -53,3 +53,41 @@ def test_sectioned_context_refuses_device_entry_points(dev):
         assert sf.lib().sf_detect(ss._h, None, None, None, None, None) == sf.SF_EINVAL
         n = ctypes.c_int64()
         assert sf.lib().sf_mask_words(ss._h, ctypes.byref(n)) in (sf.SF_EINVAL, sf.SF_OK)
+
+
+def test_sections_fp16_storage(dev):
+    """16-bit storage: the sections hold the cube in FP16 like the context."""
+    import torch
+    from paper_1507_04941_gb300 import SectionedSourceFinder, SourceFinder, synth
+    shape = (150, 40, 96)
+    cube = synth.make_cube(shape, 52, 12, (1.0, 5.0), None).to(torch.float16)
+    window = (16, 16, 32)
+    with SourceFinder(shape, BANK, 3.0, window, k=3.0, storage="f16", device=dev) as sf:
+        want = sf.detect(cube.to(dev))
+        torch.cuda.synchronize(dev)
+        want = want.cpu().numpy()
+    with SectionedSourceFinder(shape, BANK, 3.0, window, k=3.0, section=48, storage="f16",
+                               device=dev) as ss:
+        got = ss.detect_host(cube.contiguous().pin_memory()).numpy()
+    assert want.any()
+    np.testing.assert_array_equal(got, want)
+
+
+def test_sections_tile_workload(dev):
+    """The bench's tile workload (512x512x1024, six filters, 32x32x64 windows)
+    in 128-plane sections: bit-identical to the whole-cube detect."""
+    import torch
+    from paper_1507_04941_gb300 import SectionedSourceFinder, SourceFinder, synth
+    w = synth.TILE
+    cube = synth.make(w, device=dev)
+    with SourceFinder(w.shape, w.bank, w.truncation, w.window, w.k, device=dev) as sf:
+        want = sf.detect(cube)
+        torch.cuda.synchronize(dev)
+        want = want.cpu().numpy()
+    h_cube = cube.cpu().pin_memory()
+    del cube
+    with SectionedSourceFinder(w.shape, w.bank, w.truncation, w.window, w.k, section=128,
+                               device=dev) as ss:
+        got = ss.detect_host(h_cube).numpy()
+    assert want.any()
+    np.testing.assert_array_equal(got, want)
