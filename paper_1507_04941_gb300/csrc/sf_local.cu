@@ -15,8 +15,8 @@
  *                16-column block sums, and pushes them into a ring of the
  *                last 2 sy + 17 rows.  The y box sums run down the ring, two
  *                lanes per column (one per sum), restarted from a direct sum
- *                at every step of 16 rows.  A sum of squares that falls below
- *                a quarter of its largest value since its chain started is
+ *                at every step of 16 rows.  A sum of squares whose chain has
+ *                carried a total above kBudget times its current value is
  *                recomputed directly (the rounding left by large values that
  *                entered and left would otherwise dominate).  Each voxel's y-z
  *                box mean A and second central moment M = sum (c - A)^2 are
@@ -59,10 +59,12 @@ constexpr int kRB = 16;          /* rows per step */
 constexpr int kBS = 16;          /* z block and segment length */
 constexpr int kRS = kMZ + 4;     /* ring row stride: 33 quads (odd) */
 constexpr int kYRows = 256;      /* output rows per CTA at most */
-/* a running sum of squares that falls below 1/kRestart of its largest value
- * since the chain started is recomputed directly: the rounding error of a
- * chain of at most 16 steps is then within 2 * 16 * kRestart ulps of it */
-constexpr float kRestart = 4.f;
+/* a running sum of squares carries a rounding error within 2 ulps of the
+ * total of its values along the chain; when that total exceeds kBudget times
+ * the current value (large values entered and left), the output is summed
+ * directly and the chain restarts from it, so the error stays within
+ * 2 * kBudget ulps of the value */
+constexpr float kBudget = 64.f;
 
 /* staged row stride: columns up to 131 + 2 sz are read, in float4 quads; an
  * odd number of quads keeps eight rows' quads in distinct banks */
@@ -149,29 +151,33 @@ __device__ __forceinline__ void yz_segment(const float *__restrict__ u, const fl
     for (int i = 0; i < 5; ++i) ld4(ep + 4 * i, E + 4 * i);
     float o4[4];
     o4[0] = acc;
-    float mx = acc;   /* the chain's largest sum of squares since its start */
+    float tot = acc;   /* the total of the chain's sums of squares since its start */
+    unsigned int redo = 0u;   /* outputs whose chain total exceeds kBudget times them */
 #pragma unroll
     for (int i = 1; i < 16; ++i) {
         const float vin = E[SH - 1 + i] - s0, vout = L[i - 1] - s0;
         if (SQ) {
             acc = fmaf(-vout, vout, fmaf(vin, vin, acc));
-            mx = fmaxf(mx, acc);
-            if (acc * kRestart < mx) {
-                /* the box has left values far above the rest: the rounding
-                 * left behind by their squares would dominate, so this output
-                 * is summed directly and the chain restarts from it */
-                acc = 0.f;
-                for (int o = 0; o <= 2 * sz; ++o) {
-                    const float d = u[j0 + i + o] - s0;
-                    acc = fmaf(d, d, acc);
-                }
-                mx = acc;
-            }
+            tot += fabsf(acc);
+            redo |= (acc * kBudget < tot ? 1u : 0u) << i;
         } else {
             acc += vin - vout;
         }
         o4[i & 3] = acc;
         if ((i & 3) == 3) st4(ring + j0 + i - 3, o4);
+    }
+    if (SQ && redo) {
+        /* large values entered and left: the rounding they left would
+         * dominate, so these outputs are summed directly */
+        for (int i = 1; i < 16; ++i)
+            if (redo >> i & 1u) {
+                float q = 0.f;
+                for (int o = 0; o <= 2 * sz; ++o) {
+                    const float d = u[j0 + i + o] - s0;
+                    q = fmaf(d, d, q);
+                }
+                ring[j0 + i] = q;
+            }
     }
 }
 
@@ -303,7 +309,7 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
     float *out = (sq ? M : A) + g.plane0 + (i64)g.ys * g.nz + z;
     const int nsteps = (g.NR + kRB - 1) / kRB;
     float acc = 0.f;   /* this lane's y box sum of the current output row */
-    float mx = 0.f;    /* its largest value since the chain's start (sums of squares) */
+    float tot = 0.f;   /* the total of its values since the chain's start (sums of squares) */
     if (EDGE) {
         asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         yz_shift<CH>(U, g, 0, s);
@@ -380,9 +386,12 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
                     for (int i = 0; i < n1; ++i) acc += ring[(sl + i) * kRS + col];
                     for (int i = 0; i < cy_full - n1; ++i) acc += ring[i * kRS + col];
                 }
-                mx = acc;
-                yz_emit(acc, lane, sq, zok, yfull ? rn_full : rcz * __frcp_rn((float)clipped32(g.ys + o, g.sy, g.ny)),
-                        s, op);
+                tot = fabsf(acc);
+                {
+                    float rn = rn_full;
+                    if (!yfull) rn = rcz * __frcp_rn((float)clipped32(g.ys + o, g.sy, g.ny));
+                    yz_emit(acc, lane, sq, zok, rn, s, op);
+                }
                 op += g.nz;
                 ++o;
                 if (direct_y) continue;
@@ -393,24 +402,50 @@ __device__ __forceinline__ void yz_body(float *__restrict__ A, float *__restrict
                 while (o < o1) {
                     const int m = min(o1 - o, min(g.RING - a, g.RING - c));
                     const float *pin = ring + a * kRS + col, *pout = ring + c * kRS + col;
-                    for (int i = 0; i < m; ++i) {
-                        acc += pin[i * kRS] - pout[i * kRS];
-                        mx = fmaxf(mx, acc);
-                        if (sq && acc * kRestart < mx) {
-                            /* restart the sum of squares from a direct sum
-                             * over rows o+i .. o+i+2 sy (see kRestart) */
-                            int sl = c + i + 1;   /* slot of row o + i */
-                            if (sl >= g.RING) sl -= g.RING;
-                            const int n1 = min(cy_full, g.RING - sl);
-                            acc = 0.f;
-                            for (int r = 0; r < n1; ++r) acc += ring[(sl + r) * kRS + col];
-                            for (int r = 0; r < cy_full - n1; ++r) acc += ring[r * kRS + col];
-                            mx = acc;
+                    unsigned int redo = 0u;   /* outputs of this stretch to sum directly */
+                    float *op0 = op;
+                    if (yfull) {
+                        for (int i = 0; i < m; ++i) {
+                            acc += pin[i * kRS] - pout[i * kRS];
+                            tot += fabsf(acc);
+                            redo |= (sq && acc * kBudget < tot ? 1u : 0u) << i;
+                            yz_emit(acc, lane, sq, zok, rn_full, s, op);
+                            op += g.nz;
                         }
-                        yz_emit(acc, lane, sq, zok,
-                                yfull ? rn_full : rcz * __frcp_rn((float)clipped32(g.ys + o + i, g.sy, g.ny)),
-                                s, op);
-                        op += g.nz;
+                    } else {
+                        for (int i = 0; i < m; ++i) {
+                            acc += pin[i * kRS] - pout[i * kRS];
+                            tot += fabsf(acc);
+                            redo |= (sq && acc * kBudget < tot ? 1u : 0u) << i;
+                            yz_emit(acc, lane, sq, zok,
+                                    rcz * __frcp_rn((float)clipped32(g.ys + o + i, g.sy, g.ny)), s, op);
+                            op += g.nz;
+                        }
+                    }
+                    /* large values entered and left the sum of squares (see
+                     * kBudget): both sums of those outputs are summed directly
+                     * over rows o+i .. o+i+2 sy and written again, the warp
+                     * visiting the union of its columns' outputs in order; the
+                     * chain continues from the last output */
+                    redo = __shfl_sync(0xffffffffu, redo, (lane & 15) + 16);
+                    unsigned int todo = __reduce_or_sync(0xffffffffu, redo);
+                    while (todo) {
+                        const int i = __ffs(todo) - 1;
+                        todo &= todo - 1u;
+                        const bool mine = (redo >> i) & 1u;
+                        int sl = c + i + 1;   /* slot of row o + i */
+                        if (sl >= g.RING) sl -= g.RING;
+                        const int n1 = min(cy_full, g.RING - sl);
+                        float d = 0.f;
+                        for (int r = 0; r < n1; ++r) d += ring[(sl + r) * kRS + col];
+                        for (int r = 0; r < cy_full - n1; ++r) d += ring[r * kRS + col];
+                        float rn = rn_full;
+                        if (!yfull) rn = rcz * __frcp_rn((float)clipped32(g.ys + o + i, g.sy, g.ny));
+                        yz_emit(d, lane, sq, zok && mine, rn, s, op0 + (i64)i * g.nz);
+                        if (mine && i == m - 1) {
+                            acc = d;
+                            tot = fabsf(d);
+                        }
                     }
                     o += m;
                     a += m;
