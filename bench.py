@@ -663,9 +663,21 @@ def cpu_baseline(cube, w, budget_s: float = 15.0):
         done += len(idx)
         vox += len(idx) * w.window[0] * w.window[1] * w.window[2]
     el = time.perf_counter() - t0
+    # the same oracle on one thread, on a bounded share of the same windows
+    t1 = time.perf_counter()
+    done1 = 0
+    while done1 < min(len(all_idx), max(1, done)) and time.perf_counter() - t1 < budget_s / 5:
+        oracle.detect_windows(cube, w.bank, w.truncation, w.window, w.k, all_idx[done1:done1 + 1],
+                              nthreads=1)
+        done1 += 1
+    el1 = time.perf_counter() - t1
+    vox1 = done1 * w.window[0] * w.window[1] * w.window[2]
     return {"value": vox * len(w.bank) / el, "unit": UNIT, "cores": int(used), "kind": "oracle",
-            "sample": f"{done} of {len(all_idx)} windows (32x32x64 voxels x 6 filters each) of "
-                      f"the {w.name} cube, seeded order, {el:.1f} s on {used} host threads"}
+            "sample": f"{done} of {len(all_idx)} windows ({w.window[0]}x{w.window[1]}x{w.window[2]} "
+                      f"voxels x {len(w.bank)} filters each) of the {w.name} cube, seeded order, "
+                      f"{el:.1f} s on {used} host threads",
+            "single_thread": {"value": vox1 * len(w.bank) / el1, "unit": UNIT, "cores": 1,
+                              "sample": f"{done1} windows of the same order, {el1:.1f} s on one thread"}}
 
 
 def run_reference(args):
