@@ -471,7 +471,8 @@ def weighted_direct_voxel(d, w, sigma_xy: float, sigma_z: float, truncation: flo
                                                   _ptr(gz, _dp), rz, DEN_MODES[den], x, y, z))
 
 
-def weighted_detect(d, w, bank, truncation, window, k, den: str = "fw", band_rel: float = 1e-4):
+def weighted_detect(d, w, bank, truncation, window, k, den: str = "fw", band_rel: float = 1e-4,
+                    ddof: int = 0):
     """The method with Eq. 1 filtering: every filter of the bank weighted by w,
     window statistics (Sec. 3.3), c > mean + k std, OR over the bank.
     Returns dict(mask, sure (packed words), mean, std [nf][nwx][nwy][nwz])."""
@@ -486,7 +487,7 @@ def weighted_detect(d, w, bank, truncation, window, k, den: str = "fw", band_rel
     near_any = np.zeros(d.shape, dtype=bool)
     for f, (sxy, sz) in enumerate(bank):
         c = weighted_filter_box(d, w, sxy, sz, truncation, den)
-        m, s = window_stats(c, window)
+        m, s = window_stats(c, window, ddof=ddof)
         means[f], stds[f] = m, s
         wi = [np.arange(n) // wn for n, wn in zip(d.shape, window)]
         mb = m[np.ix_(*wi)]

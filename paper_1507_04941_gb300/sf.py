@@ -394,7 +394,7 @@ class SectionedSourceFinder:
     device memory bounded by the section size (wraps a sectioned sf_ctx)."""
 
     def __init__(self, shape, bank, truncation: float = 3.0, window=(32, 32, 64), k: float = 4.0,
-                 section: int = 256, storage: str = "f32", device=None):
+                 section: int = 256, storage: str = "f32", device=None, std_ddof: int = 0):
         import torch
         self.shape = tuple(int(s) for s in shape)
         self.bank = tuple((float(a), float(b)) for a, b in bank)
@@ -408,7 +408,8 @@ class SectionedSourceFinder:
         self._specs = specs
         cfg = Config(self.shape[0], self.shape[1], self.shape[2], len(self.bank), specs,
                      float(truncation), self.window[0], self.window[1], self.window[2], float(k),
-                     STORAGE[storage], 0, self.device.index if self.device.index is not None else -1)
+                     STORAGE[storage], 0, self.device.index if self.device.index is not None else -1,
+                     int(std_ddof))
         h = _vp()
         _check(lib().sf_create_sectioned(ctypes.byref(cfg), self.section, ctypes.byref(h)), None)
         self._h = h
@@ -452,7 +453,7 @@ class BatchSourceFinder:
     """Many cubes of different shapes, one filter bank (wraps a batched sf_ctx)."""
 
     def __init__(self, shapes, bank, truncation: float = 3.0, window=(32, 32, 64), k: float = 4.0,
-                 storage: str = "f32", device=None):
+                 storage: str = "f32", device=None, stats_fp64: bool = False, std_ddof: int = 0):
         import torch
         self.shapes = [tuple(int(v) for v in sh) for sh in shapes]
         self.bank = tuple((float(a), float(b)) for a, b in bank)
@@ -464,8 +465,8 @@ class BatchSourceFinder:
         specs = (FilterSpec * len(self.bank))(*[FilterSpec(a, b) for a, b in self.bank])
         self._specs = specs
         cfg = Config(1, 1, 1, len(self.bank), specs, float(truncation), self.window[0],
-                     self.window[1], self.window[2], float(k), STORAGE[storage], 0,
-                     self.device.index if self.device.index is not None else -1)
+                     self.window[1], self.window[2], float(k), STORAGE[storage], 1 if stats_fp64 else 0,
+                     self.device.index if self.device.index is not None else -1, int(std_ddof))
         dims = (_i64 * (3 * len(self.shapes)))(*[v for sh in self.shapes for v in sh])
         h = _vp()
         _check(lib().sf_create_batch(ctypes.byref(cfg), len(self.shapes), dims, ctypes.byref(h)),

@@ -58,6 +58,25 @@ def test_batch_equals_per_cube(dev, oracle):
     assert not ((got != want) & sure).any()
 
 
+@pytest.mark.parametrize("opts", [dict(stats_fp64=True), dict(std_ddof=1)])
+def test_batch_statistics_options(dev, opts):
+    """The statistics options reach the persistent kernel: bit-identical to
+    the per-cube path with the same options."""
+    import torch
+    from paper_1507_04941_gb300 import BatchSourceFinder, SourceFinder
+    cubes = _cubes(dev)[:3]
+    with BatchSourceFinder(SHAPES[:3], BANK6, 3.0, (32, 32, 64), device=dev, **opts) as bf:
+        masks, means, stds = bf.detect(cubes, stats=True)
+        bf.synchronize()
+        for i, cube in enumerate(cubes):
+            with SourceFinder(SHAPES[i], BANK6, 3.0, (32, 32, 64), device=dev, **opts) as sf:
+                m1, me1, sd1 = sf.detect(cube, stats=True)
+                torch.cuda.synchronize(dev)
+            assert torch.equal(masks[i], m1), f"cube {i} mask {opts}"
+            assert torch.equal(means[i], me1), f"cube {i} mean {opts}"
+            assert torch.equal(stds[i], sd1), f"cube {i} std {opts}"
+
+
 def test_batch_single_cube_and_no_spatial_filter(dev):
     import torch
     from paper_1507_04941_gb300 import BatchSourceFinder, SourceFinder, synth

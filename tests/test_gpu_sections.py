@@ -55,6 +55,23 @@ def test_sectioned_context_refuses_device_entry_points(dev):
         assert sf.lib().sf_mask_words(ss._h, ctypes.byref(n)) in (sf.SF_EINVAL, sf.SF_OK)
 
 
+def test_sections_sample_std(dev):
+    """std_ddof = 1 reaches the section contexts."""
+    import torch
+    from paper_1507_04941_gb300 import SectionedSourceFinder, SourceFinder, synth
+    shape = (130, 40, 96)
+    cube = synth.make_cube(shape, 53, 12, (1.0, 5.0), None)
+    window = (16, 16, 32)
+    with SourceFinder(shape, BANK, 3.0, window, k=3.0, device=dev, std_ddof=1) as sf:
+        want = sf.detect(cube.to(dev))
+        torch.cuda.synchronize(dev)
+        want = want.cpu().numpy()
+    with SectionedSourceFinder(shape, BANK, 3.0, window, k=3.0, section=32, device=dev,
+                               std_ddof=1) as ss:
+        got = ss.detect_host(cube.contiguous().pin_memory()).numpy()
+    np.testing.assert_array_equal(got, want)
+
+
 def test_sections_fp16_storage(dev):
     """16-bit storage: the sections hold the cube in FP16 like the context."""
     import torch

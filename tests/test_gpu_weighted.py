@@ -95,6 +95,30 @@ def test_weighted_detect_parity(dev, oracle, den):
     assert (np.abs(gs - ref["std"]) <= 1e-5 * scale).all()
 
 
+@pytest.mark.parametrize("opts", [dict(std_ddof=1), dict(stats_fp64=True)])
+def test_weighted_detect_statistics_options(dev, oracle, opts):
+    """The statistics options in the fused pair kernel (sample std against the
+    oracle with ddof = 1; the FP64 combine against the population oracle)."""
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder, words_to_bits
+    shape, window, k = (40, 36, 100), (16, 16, 32), 3.0
+    d, w = _inputs(shape, 56)
+    with SourceFinder(shape, BANK6, 3.0, window, k=k, device=dev, **opts) as sf:
+        mask, mean, std = sf.weighted_detect(d.to(dev), w.to(dev), "fw", stats=True)
+        torch.cuda.synchronize(dev)
+        got = words_to_bits(mask.cpu().numpy(), shape[2])
+        gm, gs = mean.cpu().numpy(), std.cpu().numpy()
+    ref = oracle.weighted_detect(d.numpy(), w.numpy(), BANK6, 3.0, window, k, "fw",
+                                 ddof=opts.get("std_ddof", 0))
+    want = oracle.unpack_bits(ref["mask"], shape[2])
+    sure = oracle.unpack_bits(ref["sure"], shape[2])
+    diff = (got != want) & sure
+    assert not diff.any(), f"{opts}: {int(diff.sum())} certain mask bits differ"
+    scale = np.maximum(ref["std"], np.abs(ref["mean"]))
+    assert (np.abs(gm - ref["mean"]) <= 1e-5 * scale).all()
+    assert (np.abs(gs - ref["std"]) <= 1e-5 * scale).all()
+
+
 def test_weighted_full_tile_sampled(dev, oracle):
     """The tile workload's cube with its weights at full size: Eq. 1 of two
     bank filters at sampled voxels (some in flagged channels) against the
