@@ -369,3 +369,21 @@ def _counts(shape, window):
 
 def oracle_grid(shape, window):
     return tuple(-(-N // w) for N, w in zip(shape, window))
+
+
+def test_detect_windows_counts_match_detect(oracle):
+    """The per-window fired counts of detect_windows (the CPU baseline's
+    sampled path) equal the fired bits of the whole-cube detect in those
+    windows."""
+    rng = _rng(88)
+    shape, window = (20, 18, 70), (8, 6, 32)
+    d = rng.normal(size=shape).astype(np.float32)
+    bank = ((1.0, 2.0), (0.0, 3.0))
+    full = oracle.detect(d, bank, 3.0, window, 2.5)
+    bits = oracle.unpack_bits(full["mask"], shape[2])
+    idx = [(0, 0, 0), (2, 2, 2), (1, 2, 0), (2, 0, 1)]
+    fired, _ = oracle.detect_windows(d, bank, 3.0, window, 2.5, idx)
+    for (a, b, e), n in zip(idx, fired):
+        blk = bits[a * 8:(a + 1) * 8, b * 6:(b + 1) * 6, e * 32:(e + 1) * 32]
+        assert n == int(blk.sum())
+    assert fired.sum() > 0

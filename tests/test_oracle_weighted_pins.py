@@ -106,3 +106,41 @@ def test_zero_weight_gives_zero(oracle, rng, den):
     # planes x >= 4 have no weight within their x radius of 2
     assert np.all(got[4:] == 0.0)
     assert np.any(got[:2] != 0.0)
+
+
+# ---- the weighted detect (Eq. 1 filtering + window statistics + threshold) ----
+
+def test_weighted_detect_constant_data_is_constant(oracle):
+    """Normalised convolution (den = sum f w) of a constant cube is that
+    constant everywhere, edges included: every window has the mean C and a
+    std at the rounding level (the threshold decisions are then rounding's,
+    and are not asserted)."""
+    rng = np.random.default_rng(5)
+    shape = (12, 10, 40)
+    d = np.full(shape, 2.5, dtype=np.float32)
+    w = (0.5 + rng.random(shape)).astype(np.float32)
+    ref = oracle.weighted_detect(d, w, ((1.0, 2.0), (0.0, 3.0)), 3.0, (4, 5, 16), 3.0, "fw")
+    np.testing.assert_allclose(ref["mean"], 2.5, rtol=1e-12)
+    assert np.all(ref["std"] < 1e-12)
+
+
+def test_weighted_detect_invariances(oracle):
+    """c_w is invariant under w -> a w (a > 0) and linear in d: the masks
+    stay the same, the statistics follow d."""
+    rng = np.random.default_rng(6)
+    shape = (10, 12, 48)
+    d = rng.normal(size=shape).astype(np.float32)
+    w = (0.2 + rng.random(shape)).astype(np.float32)
+    bank = ((1.0, 2.0),)
+    for den in ("fw", "w"):
+        r0 = oracle.weighted_detect(d, w, bank, 3.0, (5, 6, 16), 2.0, den)
+        r1 = oracle.weighted_detect(d, (4.0 * w).astype(np.float32), bank, 3.0, (5, 6, 16), 2.0, den)
+        r2 = oracle.weighted_detect((2.0 * d).astype(np.float32), w, bank, 3.0, (5, 6, 16), 2.0, den)
+        np.testing.assert_allclose(r1["mean"], r0["mean"], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(r1["std"], r0["std"], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(r2["mean"], 2.0 * r0["mean"], rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(r2["std"], 2.0 * r0["std"], rtol=1e-10, atol=1e-12)
+        sure = r0["sure"] & r1["sure"] & r2["sure"]
+        assert not ((r0["mask"] ^ r1["mask"]) & sure).any()
+        assert not ((r0["mask"] ^ r2["mask"]) & sure).any()
+        assert r0["mask"].any()
