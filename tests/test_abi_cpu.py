@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 
 import pytest
 
@@ -129,3 +130,21 @@ def test_sectioned_arguments_rejected_on_host(libsf, section, bad):
     assert lib.sf_create_sectioned(ctypes.byref(cfg), section, ctypes.byref(h)) == sf.SF_EINVAL
     assert not h.value
     assert lib.sf_create_sectioned(None, 16, ctypes.byref(h)) == sf.SF_EINVAL
+
+
+def test_no_fallback_without_the_library(tmp_path):
+    """Without libsf.so every entry point raises: there is no CPU path."""
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_1507_04941_gb300 import sf\n"
+        "sf.library_path = lambda: %r\n"
+        "sf._lib = None\n"
+        "try:\n"
+        "    sf.lib()\n"
+        "except RuntimeError as e:\n"
+        "    print('raised', 'not built' in str(e))\n"
+        "else:\n"
+        "    print('loaded')\n"
+    ) % (ROOT, str(tmp_path / "missing" / "libsf.so"))
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert res.stdout.strip() == "raised True", res.stdout + res.stderr
