@@ -8,6 +8,7 @@ import math
 
 import numpy as np
 import pytest
+import scipy.ndimage as ndi
 
 
 @pytest.fixture(scope="module")
@@ -160,3 +161,108 @@ def test_local_sample_std_flag(oracle, rng):
                 assert s[x, y, z] == pytest.approx(blk.std(ddof=1), rel=1e-12)
     _, s0 = oracle.local_stats(c, (0, 0, 0), ddof=1)
     assert (s0 == 0).all()
+
+
+# ---- the sliding-statistics detect: selection and OR pinned from outside ----
+
+def _box_sums(a, half):
+    """Sums of a over the clipped box of half-widths `half` around every
+    voxel, by cumulative sums along each axis (a summed-area table): no
+    per-voxel loop, nothing shared with the oracle's two-pass box."""
+    out = np.asarray(a, dtype=np.float64)
+    for axis, h in enumerate(half):
+        n = out.shape[axis]
+        s = np.concatenate([np.zeros_like(np.take(out, [0], axis=axis)),
+                            np.cumsum(out, axis=axis)], axis=axis)
+        hi = np.minimum(np.arange(n) + h + 1, n)
+        lo = np.maximum(np.arange(n) - h, 0)
+        out = np.take(s, hi, axis=axis) - np.take(s, lo, axis=axis)
+    return out
+
+
+def _independent_local_detect(d, bank, trunc, half, k):
+    """scipy Gaussian filter with zero padding, box moments from summed-area
+    tables (mean = S1/n, var = S2/n - mean^2), c > mean + k std, OR."""
+    fire = np.zeros(d.shape, dtype=bool)
+    n = _box_sums(np.ones(d.shape), half)
+    for sxy, sz in bank:
+        rxy = math.ceil(trunc * sxy) if sxy > 0 else 0
+        rz = math.ceil(trunc * sz) if sz > 0 else 0
+        c = ndi.gaussian_filter(d.astype(np.float64), sigma=(sxy, sxy, sz), mode="constant",
+                                cval=0.0, radius=(rxy, rxy, rz))
+        mean = _box_sums(c, half) / n
+        var = np.maximum(_box_sums(c * c, half) / n - mean * mean, 0.0)
+        fire |= c > mean + k * np.sqrt(var)
+    return fire
+
+
+def test_local_detect_matches_independent_pipeline(oracle):
+    """The whole sliding-statistics detect against scipy + summed-area tables
+    on a cube with sources, a three-filter bank and an asymmetric box: masks
+    equal wherever the oracle's decision is certain.  A flipped sign, a
+    dropped filter in the OR or a box taken on the wrong axis each change
+    many voxels."""
+    k = 2.5
+    from paper_1507_04941_gb300 import synth
+    d = synth.make_cube((24, 20, 56), seed=31, n_sources=5, peak=(2.0, 4.0)).numpy()
+    bank = ((0.0, 2.0), (1.5, 4.0), (1.0, 2.0))
+    half = (4, 3, 7)
+    fire, sure, cv, mv, sv = oracle.local_detect(d, bank, 3.0, half, k)
+    ref = _independent_local_detect(d, bank, 3.0, half, k).ravel()
+    sure = sure.astype(bool)
+    got = fire.astype(bool)
+    assert ref.sum() > 100
+    assert np.array_equal(got[sure], ref[sure])
+    assert (~sure).sum() <= 4
+    # the first and the last filter each select voxels no other filter
+    # selects, so an OR that drops either cannot pass
+    per_f = cv > mv + k * sv
+    for f in (0, len(bank) - 1):
+        others = np.delete(per_f, f, axis=0).any(axis=0)
+        assert (per_f[f] & ~others).any(), f
+
+
+def test_local_detect_whole_cube_box_equals_window_detect(oracle):
+    """A cube that is exactly one statistics window and a box covering the
+    whole cube from every voxel: the local statistics are the window's, so
+    the sliding-statistics detect is the window detect (Sec. 3.3 both ways)."""
+    from paper_1507_04941_gb300 import synth
+    d = synth.make_cube((16, 12, 40), seed=32, n_sources=3, peak=(2.0, 4.0)).numpy()
+    bank = ((0.0, 2.0), (1.0, 3.0))
+    k = 2.5
+    fire, sure, cv, mv, sv = oracle.local_detect(d, bank, 3.0, (16, 12, 40), k)
+    ref = oracle.detect(d, bank, 3.0, d.shape, k, nthreads=1)
+    bits = oracle.unpack_bits(ref["mask"], d.shape[2]).ravel()
+    rsure = oracle.unpack_bits(ref["sure"], d.shape[2]).ravel()
+    both = rsure & sure.astype(bool)
+    assert bits.sum() > 20
+    assert np.array_equal(fire.astype(bool)[both], bits[both])
+    for f in range(len(bank)):
+        np.testing.assert_allclose(mv[f], ref["mean"][f].ravel()[0], rtol=0, atol=1e-12)
+        np.testing.assert_allclose(sv[f], ref["std"][f].ravel()[0], rtol=1e-12)
+
+
+def test_local_detect_tie_does_not_fire(oracle):
+    """Values +1 and -1 in equal numbers, the identity filter and a box over
+    the whole cube: mean 0 and std 1 exactly, so with k = 1 the threshold is
+    exactly 1 and the strict comparison selects nothing, while c >= T would
+    select half the cube."""
+    d = np.ones((6, 4, 8), dtype=np.float32)
+    d.reshape(-1)[::2] = -1.0
+    fire, _, cv, mv, sv = oracle.local_detect(d, ((0.0, 0.0),), 3.0, (6, 4, 8), 1.0)
+    assert np.all(mv == 0.0) and np.all(sv == 1.0)
+    assert fire.sum() == 0
+
+
+@pytest.mark.parametrize("k", [3.0, 4.0])
+def test_local_detect_pure_noise_false_positive_rate(oracle, k):
+    """iid N(0, 2^2) noise, the identity filter and a 9x9x17 box: each voxel
+    is selected with probability close to 1 - Phi(k) (the box estimates
+    move it by a few percent).  With sigma 2 a threshold on the variance
+    (mean + k var) or a flipped sign misses by orders of magnitude."""
+    shape = (64, 64, 128)
+    d = (2.0 * np.random.default_rng(777).standard_normal(shape)).astype(np.float32)
+    fire, _, _, _, _ = oracle.local_detect(d, ((0.0, 0.0),), 3.0, (4, 4, 8), k)
+    fired = int(fire.sum())
+    expect = d.size * 0.5 * math.erfc(k / math.sqrt(2.0))
+    assert abs(fired - expect) < 0.3 * expect + 5 * math.sqrt(expect), (fired, expect)

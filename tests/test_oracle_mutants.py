@@ -1,9 +1,9 @@
 """The pins catch planted slips in the oracle.
 
-Each case copies the oracle, plants one plausible mistake in its C source and
-runs tests/test_oracle_pins.py against the copy (on the CPU); the pins must
-fail.  Sign flips of the symmetric taps are not mistakes in effect and are not
-planted.
+Each case copies the oracle, plants one plausible mistake in its C source (or
+in the selection and OR that its Python wrapper composes) and runs the pins of
+that part against the copy (on the CPU); the pins must fail.  Sign flips of the
+symmetric taps are not mistakes in effect and are not planted.
 """
 import os
 import shutil
@@ -62,25 +62,59 @@ WEIGHTED_MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(LOCAL_MUTANTS) + sorted(WEIGHTED_MUTANTS))
+# slips in the selection and OR that the wrapper composes for the sliding and
+# the weighted detect (oracle/__init__.py), caught by the pins of each
+PY_MUTANTS = {
+    "local_detect_sign_flipped": ("thr = mv + k * sv", "thr = mv - k * sv",
+                                  "test_oracle_local_pins.py"),
+    "local_detect_variance_not_std": ("thr = mv + k * sv", "thr = mv + k * sv * sv",
+                                      "test_oracle_local_pins.py"),
+    "local_detect_not_strict": ("fire_f = cv > thr", "fire_f = cv >= thr",
+                                "test_oracle_local_pins.py"),
+    "local_detect_drops_last_filter": ("fire = fire_f.any(axis=0)", "fire = fire_f[:-1].any(axis=0)",
+                                       "test_oracle_local_pins.py"),
+    "local_detect_drops_first_filter": ("fire = fire_f.any(axis=0)", "fire = fire_f[1:].any(axis=0)",
+                                        "test_oracle_local_pins.py"),
+    "weighted_detect_sign_flipped": ("thr = mb + k * sb", "thr = mb - k * sb",
+                                     "test_oracle_weighted_pins.py"),
+    "weighted_detect_not_strict": ("ff = c > thr", "ff = c >= thr", "test_oracle_weighted_pins.py"),
+    "weighted_detect_drops_last_filter": ("        fire |= ff\n",
+                                          "        fire |= ff if f + 1 < nf else False\n",
+                                          "test_oracle_weighted_pins.py"),
+    "weighted_detect_window_index_reversed": (
+        "wi = [np.arange(n) // wn for n, wn in zip(d.shape, window)]",
+        "wi = [np.arange(n)[::-1] // wn for n, wn in zip(d.shape, window)]",
+        "test_oracle_weighted_pins.py"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(LOCAL_MUTANTS) + sorted(WEIGHTED_MUTANTS)
+                         + sorted(PY_MUTANTS))
 def test_pins_catch_planted_slip(tmp_path, name):
     local = name in LOCAL_MUTANTS
     weighted = name in WEIGHTED_MUTANTS
-    old, new = (LOCAL_MUTANTS[name] if local else WEIGHTED_MUTANTS[name] if weighted
-                else MUTANTS[name])
-    pins = ("test_oracle_local_pins.py" if local else
-            "test_oracle_weighted_pins.py" if weighted else "test_oracle_pins.py")
+    py = name in PY_MUTANTS
+    if py:
+        old, new, pins = PY_MUTANTS[name]
+    else:
+        old, new = (LOCAL_MUTANTS[name] if local else WEIGHTED_MUTANTS[name] if weighted
+                    else MUTANTS[name])
+        pins = ("test_oracle_local_pins.py" if local else
+                "test_oracle_weighted_pins.py" if weighted else "test_oracle_pins.py")
     dst = tmp_path / "oracle_mutant"
     shutil.copytree(os.path.join(ROOT, "oracle"), dst,
                     ignore=shutil.ignore_patterns("_build", "__pycache__"))
-    src = dst / "sf_oracle.c"
+    src = dst / ("__init__.py" if py else "sf_oracle.c")
     text = src.read_text()
-    assert old in text, f"mutation site for {name} not found"
+    assert old in text and (not py or text.count(old) == 1), f"mutation site for {name} not found"
     src.write_text(text.replace(old, new, 1))
     # the mutant must compile: a build error would count as "caught" otherwise
-    cc = subprocess.run(["gcc", "-std=c99", "-fopenmp", "-fsyntax-only", str(src)],
-                        capture_output=True, text=True)
-    assert cc.returncode == 0, cc.stderr
+    if py:
+        compile(src.read_text(), str(src), "exec")
+    else:
+        cc = subprocess.run(["gcc", "-std=c99", "-fopenmp", "-fsyntax-only", str(src)],
+                            capture_output=True, text=True)
+        assert cc.returncode == 0, cc.stderr
     env = dict(os.environ, SF_ORACLE_DIR=str(dst))
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", pins)],

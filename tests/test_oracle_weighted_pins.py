@@ -144,3 +144,112 @@ def test_weighted_detect_invariances(oracle):
         assert not ((r0["mask"] ^ r1["mask"]) & sure).any()
         assert not ((r0["mask"] ^ r2["mask"]) & sure).any()
         assert r0["mask"].any()
+
+
+# ---- the weighted detect: selection and OR pinned from outside ----
+
+def _independent_weighted_detect(d, w, bank, trunc, window, k, den):
+    """scipy filters of d*w and of w (zero padding; the unit-tap box sum for
+    the printed denominator), their ratio (0 where the denominator is 0),
+    numpy window statistics by explicit slices, c > mean + k std, OR."""
+    nx, ny, nz = d.shape
+    wx, wy, wz = window
+    fire = np.zeros(d.shape, dtype=bool)
+    per_f = []
+    dw = d.astype(np.float64) * w.astype(np.float64)
+    for sxy, sz in bank:
+        rxy = math.ceil(trunc * sxy) if sxy > 0 else 0
+        rz = math.ceil(trunc * sz) if sz > 0 else 0
+        num = ndi.gaussian_filter(dw, sigma=(sxy, sxy, sz), mode="constant", cval=0.0,
+                                  radius=(rxy, rxy, rz))
+        if den == "fw":
+            dd = ndi.gaussian_filter(w.astype(np.float64), sigma=(sxy, sxy, sz), mode="constant",
+                                     cval=0.0, radius=(rxy, rxy, rz))
+        else:
+            size = (2 * rxy + 1, 2 * rxy + 1, 2 * rz + 1)
+            dd = ndi.uniform_filter(w.astype(np.float64), size=size, mode="constant",
+                                    cval=0.0) * float(np.prod(size))
+        c = np.where(dd != 0, num / np.where(dd != 0, dd, 1.0), 0.0)
+        T = np.empty_like(c)
+        for x0 in range(0, nx, wx):
+            for y0 in range(0, ny, wy):
+                for z0 in range(0, nz, wz):
+                    blk = c[x0:x0 + wx, y0:y0 + wy, z0:z0 + wz]
+                    T[x0:x0 + wx, y0:y0 + wy, z0:z0 + wz] = blk.mean() + k * blk.std()
+        per_f.append(c > T)
+        fire |= per_f[-1]
+    return fire, np.array(per_f)
+
+
+@pytest.mark.parametrize("den", ["fw", "w"])
+def test_weighted_detect_matches_independent_pipeline(oracle, den):
+    """The whole weighted detect against scipy + numpy on a cube with
+    sources, flagged (zero-weight) channels, tail windows on every axis and a
+    three-filter bank: masks equal wherever the oracle's decision is certain.
+    A flipped sign, a dropped filter in the OR or a wrong window index in the
+    broadcast of the statistics each change many voxels."""
+    from paper_1507_04941_gb300 import synth
+    shape = (22, 18, 72)
+    d = synth.make_cube(shape, seed=41, n_sources=5, peak=(2.0, 4.0)).numpy()
+    w = synth.make_weights(shape, 41).numpy()
+    bank = ((0.0, 2.0), (1.5, 4.0), (1.0, 2.0))
+    window, k = (8, 8, 32), 2.5
+    ref = oracle.weighted_detect(d, w, bank, 3.0, window, k, den)
+    fire, per_f = _independent_weighted_detect(d, w, bank, 3.0, window, k, den)
+    got = oracle.unpack_bits(ref["mask"], shape[2])
+    sure = oracle.unpack_bits(ref["sure"], shape[2])
+    assert fire.sum() > 50
+    assert np.array_equal(got[sure], fire[sure])
+    assert (~sure).sum() <= 4
+    for f in (0, len(bank) - 1):
+        others = np.delete(per_f, f, axis=0).any(axis=0)
+        assert (per_f[f] & ~others & sure).any(), f
+
+
+def test_weighted_detect_unit_weights_identity_filter_is_detect(oracle):
+    """w = 1, the normalised denominator and the identity filter give c_w = d
+    exactly (Eq. 1 with one tap), so the weighted detect is the plain
+    detect of the identity filter: same masks, same window statistics."""
+    from paper_1507_04941_gb300 import synth
+    shape = (20, 24, 70)
+    d = synth.make_cube(shape, seed=42, n_sources=4, peak=(2.0, 4.0)).numpy()
+    w = np.ones(shape, dtype=np.float32)
+    bank, window, k = ((0.0, 0.0),), (8, 8, 32), 2.5
+    got = oracle.weighted_detect(d, w, bank, 3.0, window, k, "fw")
+    ref = oracle.detect(d, bank, 3.0, window, k, nthreads=1)
+    assert np.array_equal(got["mask"], ref["mask"])
+    assert ref["mask"].any()
+    np.testing.assert_array_equal(got["mean"], ref["mean"])
+    np.testing.assert_array_equal(got["std"], ref["std"])
+
+
+@pytest.mark.parametrize("den", ["fw", "w"])
+def test_weighted_detect_tie_does_not_fire(oracle, den):
+    """Values +1 and -1 in equal numbers, w = 1, the identity filter and one
+    window over the cube: c_w = d, mean 0 and std 1 exactly, so with k = 1
+    the threshold is exactly 1 and the strict comparison selects nothing."""
+    d = np.ones((4, 6, 8), dtype=np.float32)
+    d.reshape(-1)[::2] = -1.0
+    w = np.ones_like(d)
+    ref = oracle.weighted_detect(d, w, ((0.0, 0.0),), 3.0, (4, 6, 8), 1.0, den)
+    assert ref["mean"].ravel()[0] == 0.0 and ref["std"].ravel()[0] == 1.0
+    assert not ref["mask"].any()
+
+
+@pytest.mark.parametrize("k", [3.0, 4.0])
+def test_weighted_detect_pure_noise_false_positive_rate(oracle, k):
+    """iid N(0, 2^2) noise, random positive weights and the identity filter:
+    c_w = d w / w = d, so each voxel fires with probability 1 - Phi(k) (the
+    window estimates over 65536 voxels move it by far less than the
+    binomial spread).  A flipped sign or a threshold on the variance misses
+    by orders of magnitude."""
+    shape = (128, 128, 256)
+    rng = np.random.default_rng(4545)
+    d = (2.0 * rng.standard_normal(shape)).astype(np.float32)
+    w = (0.25 + rng.random(shape)).astype(np.float32)
+    ref = oracle.weighted_detect(d, w, ((0.0, 0.0),), 3.0, (32, 32, 64), k, "fw")
+    fired = int(oracle.unpack_bits(ref["mask"], shape[2]).sum())
+    p = 0.5 * math.erfc(k / math.sqrt(2.0))
+    n = d.size
+    expect, sd = n * p, math.sqrt(n * p * (1 - p))
+    assert abs(fired - expect) < 5 * sd + 0.02 * expect, (fired, expect)
