@@ -27,11 +27,25 @@ if ROOT not in sys.path:
 METRIC = ("voxels·filters/s and % of HBM roofline (FP32 vs FP16-stored); "
           "serving p50/p99 ms")
 UNIT = "voxels·filters/s"
-SMS = 152
 FP32_LANES_PER_SM = 128
-# sf_window_detect DRAM traffic, read + write, per voxel of the cube (ncu capture
-# of the 608x256x384 tile-recipe case: 745.546 MB / 59,768,832 voxels)
-WINDOW_TRAFFIC_PER_VOXEL = 745.546e6 / 59768832
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per voxel of the
+# cube, from one ncu capture of the kernel on a smaller cube of the same recipe,
+# keyed by (kernel, storage, bank, window, sha256 prefix of the kernel source):
+# a capture holds only for the source it was taken from, so after any change
+# of the kernels the key misses and `traffic` is reported as null.
+_BANK6 = ((0.0, 2.0), (0.0, 6.0), (1.5, 2.0), (1.5, 6.0), (3.0, 2.0), (3.0, 6.0))
+DRAM_TRAFFIC_PER_VOXEL = {
+    # 608x256x384 cube: 737.254 MB read + 8.946 MB written
+    ("sf_window_detect", "f32", _BANK6, (32, 32, 64), "38878ba04d382935"):
+        (737.253632e6 + 8.946176e6) / 59768832,
+}
+
+
+def _kernel_source_hash():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1507_04941_gb300", "csrc", "kernels", "sf_kernels.cuh")
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 def _peaks():
@@ -185,6 +199,13 @@ def run_ours(args):
     if not args.no_tune:
         # the autotuner picks the launch path on this cube (outside the timed region)
         tune_rep = json.loads(sf.tune(cube, mask))
+    # measured FP32 peak (the ALU roofline's denominator), outside the timed region
+    fma_peak = None
+    try:
+        from paper_1507_04941_gb300 import fp32_peak
+        fma_peak = fp32_peak(dev.index)
+    except Exception as exc:  # noqa: BLE001 - reported, the derived peak is used
+        print(f"fp32 peak probe failed: {exc}", file=sys.stderr)
     for _ in range(max(args.warmup, 3)):
         sf.detect(cube, mask)
     torch.cuda.synchronize(dev)
@@ -241,33 +262,45 @@ def run_ours(args):
                        "tflops": fl / nl / (per_launch_ms * 1e-3) / 1e12,
                        "bytes": b / nl, "flops": fl / nl}
     sm_mhz = clocks.get("sm_mhz") or 1920.0
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    derived_peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    alu_peak, alu_kind = derived_peak, "derived"
+    if fma_peak is not None and max(fma_peak) > 0:
+        alu_peak, alu_kind = max(fma_peak), "measured"
     fused = stages.get("fused")
     xs = stages.get("x")
     dominant = "fused" if (fused and (not xs or fused["ms_per_launch"] >= xs["ms_per_launch"])) \
         else "x"
     kname = "sf_persist" if persistent else "sf_window_detect"
-    # DRAM bytes per launch from the committed ncu capture of this kernel
-    # (profiles/sf_window_detect_sf_xpass_tile-recipe-608x256x384.md): 745.5 MB
-    # for the 608x256x384 case of the same recipe, bank and windows, scaled by
-    # voxels; only for that configuration of the window kernel
-    traffic = None
-    if (kname == "sf_window_detect" and storage == "f32" and tuple(w.bank) == synth.BANK6
-            and tuple(w.window) == (32, 32, 64)):
-        traffic = WINDOW_TRAFFIC_PER_VOXEL * w.voxels
+    # DRAM bytes per launch from an ncu capture of this kernel source on a
+    # smaller cube of the same recipe, scaled by voxels (null when no capture
+    # matches the kernel source, storage, bank and window)
+    key = (kname, storage, tuple(tuple(float(v) for v in b) for b in w.bank), tuple(w.window),
+           _kernel_source_hash())
+    tpv = DRAM_TRAFFIC_PER_VOXEL.get(key)
+    traffic = tpv * w.voxels if tpv is not None else None
     if dominant == "fused":
         roof = {"kernel": kname, "bound": "alu", "achieved": fused["tflops"],
                 "peak": alu_peak, "unit": "TFLOP/s", "frac": fused["tflops"] / alu_peak,
                 "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median "
-                               "SM clock sampled during the timed region)",
+                "traffic_key": list(key[:2]) + [key[4]],
+                "peak_source": ("FP32 FMA probe (sf_fp32_peak: eight independent fma chains per "
+                                "thread, 2048 threads per SM, best of scalar and f32x2), timed "
+                                "before the timed region" if alu_kind == "measured" else
+                                f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz"),
+                "derived_peak": {"value": derived_peak,
+                                 "source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz "
+                                           "(median SM clock sampled during the timed region)",
+                                 "frac": fused["tflops"] / derived_peak},
+                "fma_probe_tflops": ({"scalar": fma_peak[0], "f32x2": fma_peak[1]}
+                                     if fma_peak is not None else None),
                 "hbm_view": {"achieved_gbs": fused["gbs"], "peak_gbs": hbm_peak,
                              "frac": fused["gbs"] / hbm_peak}}
     else:
         roof = {"kernel": "sf_xpass", "bound": "hbm", "achieved": xs["gbs"], "peak": hbm_peak,
                 "unit": "GB/s", "frac": xs["gbs"] / hbm_peak, "traffic": None}
     roof["peak_kind"] = f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if roof["bound"] == "hbm" \
-        else "derived"
+        else alu_kind
     # the whole step against HBM under two byte models: the separable passes
     # materialised (x+y pass read+write per distinct sigma_xy, a z pass per
     # filter reading t2 and writing the filtered cube, the mask) and this

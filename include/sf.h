@@ -295,6 +295,19 @@ sf_status sf_synchronize(sf_ctx *ctx, void *stream);
 sf_status sf_profile_enable(sf_ctx *ctx, int32_t enable);
 sf_status sf_profile_read(sf_ctx *ctx, double *ms, int64_t *launches, int32_t n_stages);
 
+/* Measured FP32 arithmetic peak of `device` (TFLOP/s, 2 flops per lane-FMA):
+ * the denominator of the ALU roofline of the fused window kernel, which runs
+ * its filter taps, pair sums and moments on the FP32 FMA pipe.  A probe kernel
+ * with eight independent fma chains per thread on 2048 threads per SM is
+ * timed with CUDA events (best of three after a warm-up), once with scalar
+ * fma.rn.f32 (*tflops_scalar) and once with packed fma.rn.f32x2
+ * (*tflops_pair).  Synchronous; allocates and frees one small device buffer.
+ * The paper has no counterpart: this measures the machine, not the method.
+ * Errors: SF_EINVAL for null outputs, SF_ECUDA for a CUDA failure (message
+ * from sf_fp32_peak_error()). */
+sf_status sf_fp32_peak(int32_t device, double *tflops_scalar, double *tflops_pair);
+const char *sf_fp32_peak_error(void);
+
 #ifdef __cplusplus
 }
 #endif

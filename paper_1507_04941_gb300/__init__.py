@@ -6,4 +6,4 @@ OR of all filters into a packed mask (Westerlund & Harris, Eq. 2 and
 Sec. 3.3), as CUDA kernels for sm_103a behind the C ABI of include/sf.h.
 """
 from .sf import (BatchSourceFinder, SectionedSourceFinder, Server, SfError, SourceFinder,  # noqa: F401
-                 lib, words_to_bits)
+                 fp32_peak, lib, words_to_bits)

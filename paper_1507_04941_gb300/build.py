@@ -49,14 +49,14 @@ def _sources() -> list[str]:
     return [os.path.join(CSRC, "sf_runtime.cpp"), os.path.join(CSRC, "sf_aot.cu"),
             os.path.join(CSRC, "sf_noalloc.cu"), os.path.join(CSRC, "sf_server.cpp"),
             os.path.join(CSRC, "sf_local.cu"), os.path.join(CSRC, "sf_weighted.cu"),
-            os.path.join(BUILD, "sf_embedded.cpp")]
+            os.path.join(CSRC, "sf_probe.cu"), os.path.join(BUILD, "sf_embedded.cpp")]
 
 
 def _inputs() -> list[str]:
     files = [os.path.join(CSRC, "sf_runtime.cpp"), os.path.join(CSRC, "sf_aot.cu"),
              os.path.join(CSRC, "sf_noalloc.cu"), os.path.join(CSRC, "sf_server.cpp"),
              os.path.join(CSRC, "sf_local.cu"), os.path.join(CSRC, "sf_weighted.cu"),
-             os.path.join(CSRC, "sf_kernel_abi.h"), os.path.join(CSRC, "kernels", "sf_kernels.cuh"),
+             os.path.join(CSRC, "sf_probe.cu"), os.path.join(CSRC, "sf_kernel_abi.h"), os.path.join(CSRC, "kernels", "sf_kernels.cuh"),
              os.path.join(ROOT, "include", "sf.h"), os.path.abspath(__file__)]
     return files
 
@@ -88,7 +88,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")
         return obj
 
-    with ThreadPoolExecutor(max_workers=5) as ex:
+    with ThreadPoolExecutor(max_workers=8) as ex:
         objs = list(ex.map(compile_one, _sources()))
     libdir = _cuda_lib_dir(nvcc)
     tmp = LIB + f".{os.getpid()}.tmp"

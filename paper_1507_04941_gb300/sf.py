@@ -84,6 +84,8 @@ SIGNATURES = {
     "sf_weighted_detect": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "sf_profile_enable": (_i32, [_vp, _i32]),
     "sf_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
+    "sf_fp32_peak": (_i32, [_i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "sf_fp32_peak_error": (ctypes.c_char_p, []),
 }
 
 
@@ -626,6 +628,16 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def fp32_peak(device: int = 0) -> tuple[float, float]:
+    """Measured FP32 peak of the device in TFLOP/s: (scalar fma, packed f32x2 fma)."""
+    a = ctypes.c_double()
+    b = ctypes.c_double()
+    st = lib().sf_fp32_peak(int(device), ctypes.byref(a), ctypes.byref(b))
+    if st != SF_OK:
+        raise SfError(st, lib().sf_fp32_peak_error().decode(errors="replace"))
+    return a.value, b.value
 
 
 def words_to_bits(words, nz: int) -> np.ndarray:
