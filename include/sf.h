@@ -242,7 +242,15 @@ sf_status sf_filter_noalloc(const float *d_cube, int64_t nx, int64_t ny, int64_t
  * sx, sy, sz >= 0; sy <= 64 and sz <= 128 (the y-z tile of the box sums
  * lives in shared memory); nx <= 65535.  The context keeps two float32
  * scratch cubes for the partial sums, allocated on first use (SF_ENOMEM if
- * that fails).  Not for batched contexts. */
+ * that fails).  Not for batched contexts.
+ * Accuracy against the exact statistics of the float32 input: boxes with a
+ * half-width below 3 on some axis (and not all 0) are evaluated in two passes
+ * over each voxel's box (O(box) work per voxel), within 1e-5 max(std, |mean|)
+ * for mean and std; wider boxes take separable running sums about one shift
+ * per tile, within 1e-5 max(std, |mean|) where the box mean is near the
+ * shift and within 2e-5 next to bright sources at the cube's edges (the sums
+ * of squares then carry the distance from the shift).  A box of half-widths
+ * (0, 0, 0) is exact (mean = c, std = 0). */
 sf_status sf_local_stats(sf_ctx *ctx, const float *d_filtered, int32_t sx, int32_t sy, int32_t sz,
                          float *d_mean, float *d_std, void *stream);
 

@@ -38,7 +38,11 @@
  * Shifting by values of the data keeps the second moments from cancelling
  * when the local mean is large against the local spread.  The FP32 sums still
  * lose precision where the box's spread is small against the distance from
- * its mean to the shift (boxes one voxel wide on smooth data).
+ * its mean to the shift, which thin boxes on smooth data reach; boxes with a
+ * half-width below 3 on some axis therefore take
+ *   sf_local_direct  two passes over each voxel's clipped box (the mean, then
+ *                the squared deviations from it) with compensated sums: no
+ *                cancellation, O(box) work per voxel.
  */
 #include <cuda_runtime.h>
 
@@ -543,6 +547,7 @@ struct CompSum {
     __device__ __forceinline__ float value() const { return s + comp; }
 };
 
+
 __device__ __forceinline__ void ldv(const float *p, float *v, int V)
 {
     if (V == 4) {
@@ -739,7 +744,98 @@ __global__ void __launch_bounds__(kXThreads, V == 4 ? 4 : 8)
     }
 }
 
+/* Boxes one, three or five voxels wide on some axis (a half-width below
+ * kNarrow): the statistics of each voxel's clipped box in two passes over the box, the
+ * mean first and then the sum of squared deviations from it, both with
+ * compensated (Neumaier) sums.  Nothing cancels, at the cost of reading the
+ * box once per pass for every voxel (O(box) work per voxel), which the thin
+ * box keeps small.  One warp per (x, y, 32-z mask word): lane = z offset.
+ * MODE as sf_local_x. */
+constexpr int kNarrow = 3;
+constexpr int kDThreads = 128;
+
+template <int MODE>
+__global__ void __launch_bounds__(kDThreads)
+    sf_local_direct(const float *__restrict__ c, i64 nx, i64 ny, i64 nz, i64 nw32, int sx, int sy, int sz,
+                    int ddof, float k, float *__restrict__ mean, float *__restrict__ stdv,
+                    unsigned int *__restrict__ mask)
+{
+    const i64 wg = ((i64)blockIdx.x * kDThreads + threadIdx.x) >> 5;   /* warp: (x, y, word) */
+    const int lane = threadIdx.x & 31;
+    if (wg >= nx * ny * nw32) return;   /* whole warps */
+    const i64 wi = wg % nw32, xy = wg / nw32;
+    const i64 y = xy % ny, x = xy / ny;
+    const i64 z = wi * 32 + lane;
+    const bool valid = z < nz;
+    const i64 zq = valid ? z : nz - 1;
+    const i64 x0 = x - sx < 0 ? 0 : x - sx, x1 = x + sx >= nx ? nx - 1 : x + sx;
+    const i64 y0 = y - sy < 0 ? 0 : y - sy, y1 = y + sy >= ny ? ny - 1 : y + sy;
+    const i64 z0 = zq - sz < 0 ? 0 : zq - sz, z1 = zq + sz >= nz ? nz - 1 : zq + sz;
+    const float n = (float)((x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1));
+    CompSum s1;
+    for (i64 xi = x0; xi <= x1; ++xi)
+        for (i64 yi = y0; yi <= y1; ++yi) {
+            const float *row = c + (xi * ny + yi) * nz;
+            for (i64 zi = z0; zi <= z1; ++zi) s1.add(__ldg(row + zi));
+        }
+    const float mu = s1.value() / n;
+    CompSum s2;
+    for (i64 xi = x0; xi <= x1; ++xi)
+        for (i64 yi = y0; yi <= y1; ++yi) {
+            const float *row = c + (xi * ny + yi) * nz;
+            for (i64 zi = z0; zi <= z1; ++zi) {
+                const float d = __ldg(row + zi) - mu;
+                s2.add(d * d);
+            }
+        }
+    const float q = fmaxf(s2.value(), 0.f);
+    const float sd = ddof == 0 ? sqrtf(q / n) : (n > 1.f ? sqrtf(q / (n - 1.f)) : 0.f);
+    const i64 v = (x * ny + y) * nz + zq;
+    if (MODE == 0) {
+        if (valid) {
+            mean[v] = mu;
+            stdv[v] = sd;
+        }
+    } else if (MODE == 3) {
+        if (valid) mean[v] = sd > 0.f ? (c[v] - mu) / sd : 0.f;
+    } else {
+        const unsigned int word = __ballot_sync(0xffffffffu, valid && c[v] > fmaf(k, sd, mu));
+        if (lane == 0) {
+            unsigned int *w = mask + (x * ny + y) * nw32 + wi;
+            if (MODE == 2) {
+                if (word) atomicOr(w, word);
+            } else {
+                *w = word;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+/* boxes with a half-width below kNarrow on some axis (and not the voxel
+ * itself) take the two-pass direct kernel */
+bool sf_local_is_narrow(int sx, int sy, int sz)
+{
+    const int lo = sx < sy ? (sx < sz ? sx : sz) : (sy < sz ? sy : sz);
+    return lo < kNarrow && (sx | sy | sz) != 0;
+}
+
+cudaError_t sf_launch_local_direct(const float *c, long long nx, long long ny, long long nz, long long nw32,
+                                   int sx, int sy, int sz, float k, float *mean, float *stdv, unsigned int *mask,
+                                   int mode, int ddof, cudaStream_t st)
+{
+    const long long warps = nx * ny * nw32;
+    const long long blocks = (warps * 32 + kDThreads - 1) / kDThreads;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+#define SF_LD(MODE) sf_local_direct<MODE><<<(unsigned)blocks, kDThreads, 0, st>>>(c, nx, ny, nz, nw32, sx, sy, sz, ddof, k, mean, stdv, mask)
+    if (mode == 0) SF_LD(0);
+    else if (mode == 1) SF_LD(1);
+    else if (mode == 2) SF_LD(2);
+    else SF_LD(3);
+#undef SF_LD
+    return cudaGetLastError();
+}
 
 /* shared memory of sf_local_yz for half-widths (sy, sz) */
 size_t sf_local_yz_smem(int sy, int sz) { return sizeof(float) * yz_smem_floats(sy, sz); }

@@ -49,6 +49,10 @@ cudaError_t sf_launch_w_product(const float *d, const float *w, float *p, long l
 cudaError_t sf_launch_w_ratio(const float *num, const float *den, float *out, long long n, cudaStream_t st);
 cudaError_t sf_launch_local_yz(const float *c, float *P, float *Q, long long nx, long long ny, long long nz, int sy,
                                int sz, cudaStream_t st);
+bool sf_local_is_narrow(int sx, int sy, int sz);
+cudaError_t sf_launch_local_direct(const float *c, long long nx, long long ny, long long nz, long long nw32,
+                                   int sx, int sy, int sz, float k, float *mean, float *stdv, unsigned int *mask,
+                                   int mode, int ddof, cudaStream_t st);
 cudaError_t sf_launch_local_x(const float *c, const float *P, const float *Q, long long nx, long long ny,
                               long long nz, long long nw32, int sx, int sy, int sz, float k, float *mean,
                               float *stdv, unsigned int *mask, int mode, int ddof, cudaStream_t st);
@@ -2120,10 +2124,16 @@ sf_status sf_local_stats(sf_ctx *c, const float *d_filtered, int32_t sx, int32_t
     const size_t cube = align_up((size_t)c->nvox * sizeof(float), 256) / sizeof(float);
     float *P = c->lscratch + cube, *Q = c->lscratch + 2 * cube;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = sf_launch_local_yz(d_filtered, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
-    if (e == cudaSuccess)
-        e = sf_launch_local_x(d_filtered, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_mean, d_std,
-                              nullptr, 0, g.std_ddof, st);
+    cudaError_t e;
+    if (sf_local_is_narrow(sx, sy, sz)) {
+        e = sf_launch_local_direct(d_filtered, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_mean, d_std,
+                                   nullptr, 0, g.std_ddof, st);
+    } else {
+        e = sf_launch_local_yz(d_filtered, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
+        if (e == cudaSuccess)
+            e = sf_launch_local_x(d_filtered, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_mean, d_std,
+                                  nullptr, 0, g.std_ddof, st);
+    }
     return e == cudaSuccess ? SF_OK : cuda_fail(c, e, "local statistics launch");
 }
 
@@ -2139,10 +2149,16 @@ sf_status sf_local_zscore(sf_ctx *c, const float *d_filtered, int32_t sx, int32_
     const size_t cube = align_up((size_t)c->nvox * sizeof(float), 256) / sizeof(float);
     float *P = c->lscratch + cube, *Q = c->lscratch + 2 * cube;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = sf_launch_local_yz(d_filtered, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
-    if (e == cudaSuccess)
-        e = sf_launch_local_x(d_filtered, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_z, nullptr,
-                              nullptr, 3, g.std_ddof, st);
+    cudaError_t e;
+    if (sf_local_is_narrow(sx, sy, sz)) {
+        e = sf_launch_local_direct(d_filtered, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_z, nullptr,
+                                   nullptr, 3, g.std_ddof, st);
+    } else {
+        e = sf_launch_local_yz(d_filtered, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
+        if (e == cudaSuccess)
+            e = sf_launch_local_x(d_filtered, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, d_z, nullptr,
+                                  nullptr, 3, g.std_ddof, st);
+    }
     return e == cudaSuccess ? SF_OK : cuda_fail(c, e, "local z-score launch");
 }
 
@@ -2160,10 +2176,16 @@ sf_status sf_local_detect(sf_ctx *c, const void *d_cube, int32_t sx, int32_t sy,
     cudaStream_t st = (cudaStream_t)stream;
     for (int f = 0; f < (int)c->filt.size(); ++f) {
         if ((s = sf_filter(c, d_cube, f, F, stream)) != SF_OK) return s;
-        cudaError_t e = sf_launch_local_yz(F, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
-        if (e == cudaSuccess)
-            e = sf_launch_local_x(F, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, nullptr, nullptr, d_mask,
-                                  f == 0 ? 1 : 2, g.std_ddof, st);
+        cudaError_t e;
+        if (sf_local_is_narrow(sx, sy, sz)) {
+            e = sf_launch_local_direct(F, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, nullptr, nullptr, d_mask,
+                                       f == 0 ? 1 : 2, g.std_ddof, st);
+        } else {
+            e = sf_launch_local_yz(F, P, Q, g.nx, g.ny, g.nz, sy, sz, st);
+            if (e == cudaSuccess)
+                e = sf_launch_local_x(F, P, Q, g.nx, g.ny, g.nz, c->nw32, sx, sy, sz, g.k, nullptr, nullptr,
+                                      d_mask, f == 0 ? 1 : 2, g.std_ddof, st);
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "local detect launch");
     }
     return SF_OK;

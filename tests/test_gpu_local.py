@@ -45,19 +45,24 @@ def _assert_stats(gm, gs, rm, rs, rel=1e-5, what=""):
                                         ((6, 40, 520), (2, 5, 20)),      # interior z tiles
                                         ((3, 300, 136), (1, 7, 4)),      # two y segments
                                         ((4, 120, 70), (1, 10, 3)),      # y anchors: a block + 4 rows
-                                        ((3, 90, 64), (0, 8, 2))])       # y anchors: one whole block
+                                        ((3, 90, 64), (0, 8, 2)),        # y anchors: one whole block
+                                        ((30, 40, 100), (2, 2, 2)),      # narrowest running-sum box
+                                        ((30, 40, 100), (4, 2, 9)),
+                                        ((30, 40, 100), (2, 5, 8)),
+                                        ((30, 40, 100), (0, 3, 0)),      # one-voxel-wide boxes
+                                        ((30, 40, 100), (4, 0, 0)),
+                                        ((30, 40, 100), (0, 0, 9))])
 @pytest.mark.parametrize("offset", [0.0, 3.0])
 def test_local_stats_parity(dev, oracle, shape, half, offset):
     """offset 3 makes the variance cancellation visible (|mean| >> std):
-    1e-5 max(std, |mean|).  offset 0 puts the tolerance on the std itself,
-    where boxes next to bright sources test the running sums of squares: the
-    precision contract of the running sums (FP32 sums about one shift per
-    tile, chains of at most 16 steps restarted at 4x drops) is
-    2e-5 max(std, |mean|) for boxes at least 5 voxels wide on every axis;
-    narrower boxes on this smoothed data are tested with the offset only."""
-    if offset == 0.0 and min(half) < 2 and max(half) > 0:
-        pytest.skip("box narrower than the precision contract of the running sums")
-    rel = 1e-5 if offset else 2e-5
+    1e-5 max(std, |mean|) for every box.  offset 0 puts the tolerance on the
+    std itself: boxes with a half-width below 3 on some axis (the two-pass
+    direct kernel; smooth data whose box spread is small against its
+    variation) are held to 1e-5 as well; the running sums of the wider boxes
+    (FP32 sums about one shift per tile) to 2e-5, which boxes next to bright
+    sources at the cube's edges reach (1.3e-5 measured at (4, 3, 9))."""
+    narrow = min(half) < 3 and max(half) > 0
+    rel = 1e-5 if (offset or narrow or half == (0, 0, 0)) else 2e-5
     import torch
     from paper_1507_04941_gb300 import SourceFinder
     cube = _cube(shape, seed=41)
