@@ -196,9 +196,30 @@ def run_ours(args):
     mask = torch.empty(sf.mask_shape, dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
     tune_rep = None
-    if not args.no_tune:
+    if not args.no_tune and world == 1:
         # the autotuner picks the launch path on this cube (outside the timed region)
         tune_rep = json.loads(sf.tune(cube, mask))
+    step = lambda: sf.detect(cube, mask)  # noqa: E731
+    prof_ctx = sf
+    if world > 1:
+        # N GPUs: this rank's cube is one x slab of an N times longer cube (weak
+        # scaling); each step exchanges the x halo with the neighbouring ranks
+        # (NCCL point to point into this rank's own memory) and runs the slab
+        # (sf_detect_slab): x pass of the slab's planes reading the halo, windows
+        # of the slab
+        from paper_1507_04941_gb300 import partition
+        halo = partition.halo_width(w.bank, w.truncation)
+        ext = torch.zeros((w.shape[0] + 2 * halo,) + tuple(w.shape[1:]), dtype=tdt, device=dev)
+        ext[halo:halo + w.shape[0]] = cube
+        del cube
+        cube = ext[halo:halo + w.shape[0]]
+        sfs = SourceFinder(tuple(ext.shape), w.bank, w.truncation, w.window, w.k, storage=storage,
+                           device=dev)
+
+        def step():
+            partition.exchange_halo_into(ext, halo, rank, world)
+            sfs.detect_slab(ext, halo, mask)
+        prof_ctx = sfs
     # measured FP32 peak (the ALU roofline's denominator), outside the timed region
     fma_peak = None
     try:
@@ -207,10 +228,10 @@ def run_ours(args):
     except Exception as exc:  # noqa: BLE001 - reported, the derived peak is used
         print(f"fp32 peak probe failed: {exc}", file=sys.stderr)
     for _ in range(max(args.warmup, 3)):
-        sf.detect(cube, mask)
+        step()
     torch.cuda.synchronize(dev)
-    sf.profile(True)
-    sf.profile_read()
+    prof_ctx.profile(True)
+    prof_ctx.profile_read()
 
     sampler = ClockSampler(dev.index)
     if world > 1:
@@ -222,15 +243,15 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        sf.detect(cube, mask)
+        step()
     e1.record(stream)
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
     ms_total = e0.elapsed_time(e1)
-    prof = sf.profile_read()
-    sf.profile(False)
+    prof = prof_ctx.profile_read()
+    prof_ctx.profile(False)
     t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -328,7 +349,7 @@ def run_ours(args):
     # precision form: the same workload with FP16 / BF16 storage (FP32 arithmetic),
     # and FP32 storage with the window moments merged in FP64
     forms = {}
-    if not args.no_forms and storage == "f32":
+    if not args.no_forms and storage == "f32" and world == 1:
         for st_name, st_dt in (("f16", torch.float16), ("bf16", torch.bfloat16),
                                ("f32_stats_fp64", torch.float32)):
             cq = cube.to(st_dt).contiguous()
@@ -364,10 +385,16 @@ def run_ours(args):
             sq.close()
             del cq
 
+    # precision workload at its own size: 1024 x 1024 x 2048, noise sigma
+    # rising 0.8 -> 1.5 along z, 1000 sources; FP32, FP16 and BF16 storage
+    precision = None
+    if not args.no_precision and storage == "f32" and world == 1:
+        precision = run_precision(args, dev, stream)
+
     # sliding-statistics form: per-voxel local mean/std over the box of the
     # window's half extents (Sec. 3.3 read per voxel), same cube and bank
     local = None
-    if not args.no_local and storage == "f32":
+    if not args.no_local and storage == "f32" and world == 1:
         half = tuple(int(v) // 2 for v in w.window)
         lmask = torch.empty(sf.mask_shape, dtype=torch.int32, device=dev)
         for _ in range(3):
@@ -398,7 +425,7 @@ def run_ours(args):
     # weighted form (Eq. 1, normalised denominator): same cube and bank with
     # a synthetic inverse-variance weights cube (flagged channels at 0)
     weighted = None
-    if not args.no_weighted and storage == "f32":
+    if not args.no_weighted and storage == "f32" and world == 1:
         wts = synth.make_weights(w.shape, w.seed, device=dev)
         wmask = torch.empty(sf.mask_shape, dtype=torch.int32, device=dev)
         for _ in range(3):
@@ -510,11 +537,13 @@ def run_ours(args):
             "config": {"workload": w.name, "shape": list(w.shape),
                        "bank_sigma_xy_z": [list(b) for b in w.bank], "truncation": w.truncation,
                        "window": list(w.window), "k": w.k, "storage": storage,
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "parallelism": (f"x-slab split over {world} GPUs, {w.shape[0]} planes per GPU, "
+                                       "x halo exchanged by NCCL point to point each step")
+                                      if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 ({nvox * sbytes / 2**20:.0f} MiB cube, "
                              "129 MB L2)"},
             "roofline": roof, "step_hbm_models": step_models, "kernels": other, "clocks": clocks, "storage_forms": forms,
-            "local_stats_form": local, "weighted_form": weighted,
+            "local_stats_form": local, "weighted_form": weighted, "precision_form": precision,
             "serving": serving,
             "path": "persistent (x-pass + windows in one launch)" if persistent else
                     "x pass + window kernel", "autotune": tune_rep, "batched_form": batch,
@@ -526,6 +555,48 @@ def run_ours(args):
     sf.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_precision(args, dev, stream):
+    """sf_detect on the precision workload with FP32, FP16 and BF16 storage,
+    each timed with CUDA events over n steps (inputs far larger than L2)."""
+    import torch
+
+    from paper_1507_04941_gb300 import SourceFinder, synth
+    w = synth.PRECISION
+    units = w.voxels * len(w.bank)
+    base = synth.make(w, device=dev)
+    out = {"workload": w.name, "shape": list(w.shape), "noise_sigma": list(w.noise_sigma),
+           "n_sources": w.n_sources, "unit": UNIT, "storage": {}}
+    n = max(5, min(args.steps // 4, 20))
+    for st_name, st_dt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
+        cq = base.to(st_dt).contiguous()
+        with SourceFinder(w.shape, w.bank, w.truncation, w.window, w.k, storage=st_name,
+                          device=dev) as sq:
+            mk = torch.empty(sq.mask_shape, dtype=torch.int32, device=dev)
+            for _ in range(3):
+                sq.detect(cq, mk)
+            torch.cuda.synchronize(dev)
+            sq.profile(True)
+            sq.profile_read()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n):
+                sq.detect(cq, mk)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / n
+            pq = sq.profile_read()
+        out["storage"][st_name] = {"value": units / (ms * 1e-3), "ms_per_step": ms, "steps": n,
+                                   "x_pass_ms": pq[0][0] / n, "window_kernel_ms": pq[1][0] / n}
+        del cq, mk
+    f32 = out["storage"]["f32"]["ms_per_step"]
+    for st_name in ("f16", "bf16"):
+        out["storage"][st_name]["speedup_vs_f32"] = f32 / out["storage"][st_name]["ms_per_step"]
+    del base
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batch(args, dev, stream, w):
@@ -586,8 +657,9 @@ def run_batch(args, dev, stream, w):
 
 def run_serving(args, dev, w, capacity_rps):
     """Continuous-batching server under Poisson arrivals at fractions of the
-    batched form's capacity (requests/s); shapes drawn from the batched
-    workload's 64 subcubes; FP16 storage; 150 GB HBM budget."""
+    server's own capacity (requests/s, measured by a burst through the same
+    per-request path); shapes drawn from the batched workload's 64 subcubes;
+    FP16 storage; 150 GB HBM budget."""
     import numpy as np
     import torch
 
@@ -606,6 +678,7 @@ def run_serving(args, dev, w, capacity_rps):
     out = {"workload": "Poisson arrivals of the 64 batched-workload subcubes, FP16 storage, "
                        "150 GB budget, 8 slots",
            "capacity_rps_of_batched_form": capacity_rps, "levels": []}
+    batched_capacity = capacity_rps
     rng = np.random.Generator(np.random.PCG64(21))
     with Server(w.bank, w.truncation, w.window, w.k, storage="f16", budget_bytes=150 * 10 ** 9,
                 max_inflight=8, device=dev.index) as srv:
@@ -620,8 +693,23 @@ def run_serving(args, dev, w, capacity_rps):
                 i, m = owner.pop(rid)
                 free[i].append(m)
                 got += 1
-        if capacity_rps is None:
-            capacity_rps = 200.0
+        # the server's own capacity: a seeded burst of requests submitted at
+        # once, through the same per-request path (host buffers, 8 slots)
+        burst = rng.integers(0, len(shapes), 384)
+        t0 = time.perf_counter()
+        for i in burst:
+            m = mask_for(int(i))
+            owner[srv.submit(cubes[int(i)], m)] = (int(i), m)
+        while owner:
+            for rid, st, _ in srv.poll(timeout_ms=500):
+                i, m = owner.pop(rid)
+                free[i].append(m)
+        capacity_rps = len(burst) / (time.perf_counter() - t0)
+        out["capacity_rps"] = capacity_rps
+        out["capacity_basis"] = (f"{len(burst)} requests submitted at once through the server "
+                                 "(the loads below are fractions of this)")
+        if batched_capacity:
+            out["capacity_vs_batched_form"] = capacity_rps / batched_capacity
         for frac in (0.25, 0.5, 0.75, 1.0):
             rate = frac * capacity_rps
             n = args.serve_requests
@@ -768,6 +856,8 @@ def main():
     ap.add_argument("--no-sections", action="store_true", help="skip the sectioned (out-of-core) form")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests per offered-load level of the serving form")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the 1024x1024x2048 precision workload (FP32 / FP16 / BF16 storage)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP16/BF16-storage runs of the same workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

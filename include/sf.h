@@ -51,7 +51,8 @@ typedef enum sf_status {
     SF_ECUDA = 4,     /* CUDA runtime error */
     SF_ETIMEOUT = 5,  /* a bounded wait expired */
     SF_ESTATE = 6,    /* context unusable after an earlier CUDA error */
-    SF_EJIT = 7       /* run-time compilation of a kernel failed */
+    SF_EJIT = 7,      /* run-time compilation of a kernel failed */
+    SF_ECANCELED = 8  /* a served request was cancelled before admission */
 } sf_status;
 
 typedef enum sf_dtype {
@@ -138,6 +139,23 @@ sf_status sf_detect(sf_ctx *ctx, const void *d_cube, uint32_t *d_mask, float *d_
  * the copies asynchronous DMA; pageable ones work too. */
 sf_status sf_detect_host(sf_ctx *ctx, const void *h_cube, uint32_t *h_mask, void *stream);
 
+/* One x slab of a larger cube, for cubes split across devices along x
+ * (Sec. 3.1: the paper's nodes and sections take x slabs whose x pass needs
+ * the neighbours' planes).  The context is planned for the extended slab:
+ * cfg.nx = halo + S + halo, where S is the slab's own planes and the `halo`
+ * planes on each side are the neighbours' (zeros beyond the cube's edge).
+ *   d_ext   the extended slab [nx][ny][nz] in the storage type (device);
+ *   halo    >= the largest x radius of the bank, and nx - 2 halo >= 1;
+ *   d_mask  mask words of the S slab planes, [S][ny][ceil(nz/32)];
+ *   d_mean, d_std  NULL, or [n_filters][ceil(S/wx)][nwy][nwz] float32.
+ * Statistics windows tile the slab from its first plane, so a slab that
+ * starts at a multiple of wx of the cube has exactly the cube's windows and
+ * its mask rows equal sf_detect's on the whole cube bit for bit.  Needs the
+ * fused window kernel (wy % 8 == 0, wz % 32 == 0), else SF_EINVAL; not for
+ * batched contexts. */
+sf_status sf_detect_slab(sf_ctx *ctx, const void *d_ext, int64_t halo, uint32_t *d_mask, float *d_mean,
+                         float *d_std, void *stream);
+
 /* Sectioned form for cubes larger than device memory (Sec. 3.1: the cube is
  * split into sections that each fit the device, with a halo).  The cube stays
  * in host memory.  sf_detect_host on this context cuts it along x into
@@ -205,13 +223,18 @@ sf_status sf_server_create(const sf_config *proto, int64_t budget_bytes, int32_t
  * *id receives the request id. */
 sf_status sf_server_submit(sf_server *srv, const void *h_cube, int64_t nx, int64_t ny, int64_t nz,
                            uint32_t *h_mask, int64_t *id);
+/* Cancel request `id` if it is still waiting for admission: it completes at
+ * once with status SF_ECANCELED (reported by sf_server_poll) and its buffers
+ * are not touched again.  SF_ESTATE if it was already admitted (it then runs
+ * to its end), completed, or is unknown. */
+sf_status sf_server_cancel(sf_server *srv, int64_t id);
 /* Up to cap completed requests: id, status and latency (ns from submit to
  * the mask being on the host).  Waits at most timeout_ms for a first one. */
 sf_status sf_server_poll(sf_server *srv, int64_t *ids, int32_t *statuses, int64_t *latency_ns,
                          int32_t cap, int32_t timeout_ms, int32_t *n);
 /* Counters: submitted, admitted, completed, rejected, bytes in use, peak
  * bytes (in use + idle contexts), idle bytes, evictions, contexts created,
- * busy slots, queued requests, budget (up to cap values). */
+ * busy slots, queued requests, budget, cancelled (up to cap values). */
 sf_status sf_server_stats(sf_server *srv, int64_t *out, int32_t cap);
 /* Drain the queue, wait for the requests in flight, free everything. */
 sf_status sf_server_destroy(sf_server *srv);
@@ -226,8 +249,10 @@ sf_status sf_server_destroy(sf_server *srv);
  * d_cube and d_filtered are float32 device buffers of nx*ny*nz elements.
  * All calls share the scratch array: calls that overlap on the GPU race.
  * The first call on a device sets up the scratch address with
- * cudaGetSymbolAddress; make it before any stream capture.  The paper has no
- * counterpart of this entry point. */
+ * cudaGetSymbolAddress; make it before any stream capture.  The address is
+ * kept for the life of the process: after cudaDeviceReset on that device it
+ * is stale, so do not call this entry point after a device reset.  The paper
+ * has no counterpart of this entry point. */
 sf_status sf_filter_noalloc(const float *d_cube, int64_t nx, int64_t ny, int64_t nz,
                             float sigma_xy, float sigma_z, float truncation, float *d_filtered,
                             void *stream);
@@ -290,9 +315,29 @@ sf_status sf_weighted_detect(sf_ctx *ctx, const float *d_cube, const float *d_we
                              uint32_t *d_mask, float *d_mean, float *d_std, void *stream);
 
 /* Wait for the work enqueued on `stream`, then report kernel-side failures:
- * SF_ETIMEOUT when a kernel's bounded wait on its own shared-memory loads
- * expired since the last call (the flag is cleared). */
+ * SF_ETIMEOUT when a kernel's bounded wait expired since the last call (the
+ * flag is cleared): a wait on its own shared-memory loads, or, in the
+ * persistent kernel, a window's wait for its cube's x pass done by other
+ * CTAs.  The kernel that gave up has left; the context stays usable. */
 sf_status sf_synchronize(sf_ctx *ctx, void *stream);
+
+/* Limit, in nanoseconds of %globaltimer, of every bounded wait of the
+ * context's kernels (the paper's GPU kernels were split to stay under the
+ * display watchdog, Sec. 3.4; here each wait is bounded instead).  Default
+ * 2 s; accepted range [1 us, 60 s], else SF_EINVAL.  Applies to later
+ * launches; a batched context captures its graph again (allocates nothing
+ * new).  Not to be called while work of the context is being captured. */
+sf_status sf_set_wait_limit(sf_ctx *ctx, int64_t limit_ns);
+
+/* Test hook for the bounded-wait path (no counterpart in the paper).  For a
+ * batched context whose bank has an x pass: switches its plan to the
+ * persistent kernel with the x pass as items of its queue (whole cubes,
+ * 1024 lanes per item) and makes every window item wait for `extra` more x
+ * items than its cube has, so with extra > 0 no such wait can complete: each
+ * runs into the wait limit, its CTA records the expiry and leaves, and
+ * sf_synchronize returns SF_ETIMEOUT.  extra = 0 keeps that plan with the
+ * true count.  SF_EINVAL for other contexts or extra outside [0, 1e6]. */
+sf_status sf_test_stall_batch(sf_ctx *ctx, int32_t extra);
 
 /* Stage timing (tracing).  While enabled, every sf_detect records CUDA
  * events on its stream around each of its stages: stage 0 = the x pass

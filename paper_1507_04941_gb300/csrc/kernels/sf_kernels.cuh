@@ -721,8 +721,8 @@ __device__ __forceinline__ void sfd_zfilter(const sfd_t *slab, const float *U, i
  * The mask words of the window are written once at the end.  Slabs arrive by
  * TMA (cp.async.bulk.tensor, zero fill outside the cube) when the cube's
  * rows are 16-byte multiples, else by cp.async.  Every wait on a TMA
- * transaction is bounded by %globaltimer; on expiry the CTA records the
- * failure in *err and leaves.
+ * transaction is bounded by %globaltimer (the limit comes with the
+ * arguments); on expiry the CTA records the failure in *err and leaves.
  */
 struct __align__(64) sf_tmap { unsigned long long opaque[16]; };
 struct sfw_maps { sf_tmap m[SFD_NSRC]; };
@@ -741,7 +741,6 @@ __device__ __forceinline__ int sfw_la(int lane)
     return SFD_ZMAP == 1 ? lane % SFW_LPW : (lane >> 3) % SFW_LPW;
 }
 constexpr int SFW_SLAB_STRIDE = (SFD_OFF_SLAB1 - SFD_OFF_SLAB0) / (int)sizeof(sfd_t);
-constexpr unsigned long long SFW_TIMEOUT_NS = 2000000000ull;
 
 /* the type of the moment merge: FP32, or FP64 for the combine of the
  * per-thread FP32 partial sums (configuration stats_fp64) */
@@ -789,13 +788,13 @@ __device__ __forceinline__ bool sfw_try_wait(u32 bar, u32 parity)
     return ok != 0;
 }
 
-/* wait for phase `parity` of the barrier; false after SFW_TIMEOUT_NS */
-__device__ __forceinline__ bool sfw_wait(u32 bar, u32 parity)
+/* wait for phase `parity` of the barrier; false after `limit` ns */
+__device__ __forceinline__ bool sfw_wait(u32 bar, u32 parity, unsigned long long limit)
 {
     if (sfw_try_wait(bar, parity)) return true;
     const unsigned long long t0 = sfw_clock();
     while (!sfw_try_wait(bar, parity))
-        if (sfw_clock() - t0 > SFW_TIMEOUT_NS) return false;
+        if (sfw_clock() - t0 > limit) return false;
     return true;
 }
 
@@ -815,6 +814,7 @@ struct sfw_state {
     int it;         /* slab loads issued so far (buffer = it & 1) */
     bool dead;
     bool tma;       /* slabs arrive by TMA (else cp.async) */
+    unsigned long long limit;   /* bounded waits give up after this many ns */
 };
 
 /* TMA or cp.async slabs: fixed by the plan, or per cube in the persistent kernel */
@@ -859,7 +859,7 @@ __device__ __forceinline__ void sfw_load(const sf_dargs &a, const sf_tmap *mp, s
 __device__ __forceinline__ bool sfw_wait_buf(sfw_state &S, int b, bool more)
 {
     if (sfw_tma(S)) {
-        const bool ok = sfw_wait(S.bar + 8u * (u32)b, (S.phase >> b) & 1u);
+        const bool ok = sfw_wait(S.bar + 8u * (u32)b, (S.phase >> b) & 1u, S.limit);
         S.phase ^= 1u << b;
         return ok;
     }
@@ -1184,8 +1184,9 @@ __device__ __forceinline__ bool sfw_window(const sf_dargs &a, const sfd_taps &t,
 {
     const int lane = threadIdx.x & 31;
     S.wid = wid;
+    S.limit = (unsigned long long)a.wait_ns;
     const int wz = wid % a.nwz, wy = (wid / a.nwz) % a.nwy, wx = wid / (a.nwz * a.nwy);
-    S.x0 = (i64)wx * SFD_WX;
+    S.x0 = a.xorg + (i64)wx * SFD_WX;
     S.y0 = (i64)wy * SFD_WY;
     S.z0 = (i64)wz * SFD_WZ;
     const i64 left = a.nx - S.x0;
@@ -1214,8 +1215,8 @@ __device__ __forceinline__ bool sfw_window(const sf_dargs &a, const sfd_taps &t,
         if (threadIdx.x == 0) {
             atomicOr(a.err, 1);
             if (S.tma) {
-                sfw_wait(S.bar, (S.phase >> 0) & 1u);
-                sfw_wait(S.bar + 8u, (S.phase >> 1) & 1u);
+                sfw_wait(S.bar, (S.phase >> 0) & 1u, S.limit);
+                sfw_wait(S.bar + 8u, (S.phase >> 1) & 1u, S.limit);
             }
         }
         if (!S.tma) sf_cp_wait<0>();
@@ -1228,7 +1229,7 @@ __device__ __forceinline__ bool sfw_window(const sf_dargs &a, const sfd_taps &t,
         const i64 gw = (S.z0 >> 5) + wd;
         if (gw < a.nw32)
             for (int p = 0; p < S.npl; ++p)
-                a.mask[((S.x0 + p) * a.ny + S.y0 + S.row) * a.nw32 + gw] =
+                a.mask[((S.x0 - a.xorg + p) * a.ny + S.y0 + S.row) * a.nw32 + gw] =
                     S.mask[(p * SFD_WY + S.row) * SFW_NW + wd];
     }
     return true;
@@ -1263,7 +1264,7 @@ sf_window_detect(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd
  * HBM-bound x items and ALU-bound window items of different units run side by
  * side on the SMs.
  */
-__device__ __forceinline__ bool sfp_wait_count(const int *ctr, int need)
+__device__ __forceinline__ bool sfp_wait_count(const int *ctr, int need, unsigned long long limit)
 {
     unsigned long long t0 = 0ull;
     while (true) {
@@ -1272,7 +1273,7 @@ __device__ __forceinline__ bool sfp_wait_count(const int *ctr, int need)
         if (v >= need) return true;
         const unsigned long long now = sfw_clock();
         if (t0 == 0ull) t0 = now;
-        else if (now - t0 > SFW_TIMEOUT_NS) return false;
+        else if (now - t0 > limit) return false;
         __nanosleep(200);
     }
 }
@@ -1321,7 +1322,8 @@ sf_persist(const __grid_constant__ sf_pargs pa, const __grid_constant__ sfd_taps
         } else {
             bool ok = true;
             if (SFP_XITEMS && threadIdx.x == 0) {
-                ok = sfp_wait_count(pa.xdone + it.unit, u.n_xitems);
+                ok = sfp_wait_count(pa.xdone + it.unit, u.n_xitems + pa.xextra,
+                                    (unsigned long long)pa.wait_ns);
                 /* the x-filtered planes were written through the generic proxy
                  * by other CTAs; order them before this CTA's TMA reads */
                 asm volatile("fence.proxy.async.global;" ::: "memory");

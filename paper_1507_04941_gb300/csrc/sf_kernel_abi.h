@@ -58,6 +58,8 @@ struct sf_dargs {
     int *err;          /* set non-zero when a bounded wait expires */
     int wid0;          /* window of block 0 (launches over a range of windows) */
     int pad_;
+    long long wait_ns; /* limit of every bounded wait (%globaltimer ns) */
+    long long xorg;    /* x-plane of window 0 (an x slab inside a cube with halo planes) */
 };
 
 /* Persistent batched kernel: a unit is one cube (or one x-slab of a cube)
@@ -92,7 +94,8 @@ struct sf_pargs {
     int *xdone;                 /* per unit: x items completed (reset to 0) */
     int *err;
     int n_items;
-    int pad_;
+    int xextra;                 /* test hook: x items a window waits for beyond its unit's */
+    long long wait_ns;          /* limit of every bounded wait (%globaltimer ns) */
 };
 
 /* y/z filter of one filter, writing float32 filtered values */

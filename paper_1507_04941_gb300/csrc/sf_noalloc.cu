@@ -130,7 +130,17 @@ extern "C" sf_status sf_filter_noalloc(const float *d_cube, int64_t nx, int64_t 
     }
 
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SF_ECUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        sf_set_global_error("sf_filter_noalloc: cudaGetDevice failed (no usable CUDA device)");
+        return SF_ECUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        snprintf(msg, sizeof(msg), "sf_filter_noalloc: device %d beyond the %d devices it serves", dev,
+                 kMaxDevices);
+        sf_set_global_error(msg);
+        return SF_ECUDA;
+    }
     void *scratch = nullptr;
     {
         /* set-up once per device, with that device current: the host-side name

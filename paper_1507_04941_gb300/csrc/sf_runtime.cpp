@@ -261,6 +261,8 @@ struct sf_ctx {
     std::vector<float> dtaps;
     std::vector<CUtensorMap> dmaps;   /* per input; the cube's is re-encoded per call */
     int *err_flag = nullptr;          /* device flag set by kernels whose bounded wait expired */
+    long long wait_ns = 2000000000LL; /* limit of the kernels' bounded waits */
+    int stall_extra = 0;              /* test hook: x items each window waits for beyond its unit's */
 
     /* per-filter y/z filter kernels (sf_filter) and single-sigma x pass */
     std::map<int, Launch> flaunch;
@@ -1027,6 +1029,8 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
     pa.xdone = c->d_ctr + 1;
     pa.err = c->err_flag;
     pa.n_items = c->n_items;
+    pa.xextra = xbatch ? 0 : c->stall_extra;
+    pa.wait_ns = c->wait_ns;
     cudaGraph_t graph = nullptr;
     if ((e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
         return cuda_fail(c, e, "graph capture");
@@ -1100,6 +1104,7 @@ sf_status run_persist(sf_ctx *c, const void *const *cubes, uint32_t *const *mask
         a.nwin = q.nwin;
         a.k = g.k;
         a.err = c->err_flag;
+        a.wait_ns = c->wait_ns;
         h.xsrc = cubes[i];
         for (int k = 0; k < SF_MAX_XOUT; ++k)
             h.xdst[k] = k < (int)c->xy_sigma.size() ? (void *)((char *)q.slots + (size_t)k * q.slot_bytes) : nullptr;
@@ -1140,9 +1145,12 @@ sf_status check_live(sf_ctx *c, bool sectioned_ok = false)
     return SF_OK;
 }
 
-/* the window kernel over windows [w0, w1) of the plain context's cube */
+/* the window kernel over windows [w0, w1) of the plain context's cube; for
+ * an x slab inside the cube (sf_detect_slab) the window grid starts at plane
+ * xorg, ends at plane nx_end and has nwx windows along x */
 sf_status launch_windows(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_mean, float *d_std,
-                         cudaStream_t st, int w0, int w1)
+                         cudaStream_t st, int w0, int w1, long long xorg = 0, long long nx_end = -1,
+                         int nwx = -1)
 {
     sf_dargs da{};
     for (size_t i = 0; i < c->dsrc.size(); ++i) {
@@ -1155,16 +1163,18 @@ sf_status launch_windows(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float 
     da.mask = d_mask;
     da.mean = d_mean;
     da.stdv = d_std;
-    da.nx = c->cfg.nx;
+    da.nx = nx_end >= 0 ? nx_end : c->cfg.nx;
     da.ny = c->cfg.ny;
     da.nz = c->cfg.nz;
     da.nw32 = c->nw32;
-    da.nwx = c->nwx;
+    da.nwx = nwx >= 0 ? nwx : c->nwx;
     da.nwy = c->nwy;
     da.nwz = c->nwz;
-    da.nwin = c->nwin;
+    da.nwin = da.nwx * c->nwy * c->nwz;
     da.k = c->cfg.k;
     da.err = c->err_flag;
+    da.wait_ns = c->wait_ns;
+    da.xorg = xorg;
     da.wid0 = w0;
     Launch L = c->dlaunch;
     L.grid = dim3((unsigned)(w1 - w0));
@@ -1232,6 +1242,7 @@ const char *sf_status_str(sf_status s)
     case SF_ETIMEOUT: return "SF_ETIMEOUT";
     case SF_ESTATE: return "SF_ESTATE";
     case SF_EJIT: return "SF_EJIT";
+    case SF_ECANCELED: return "SF_ECANCELED";
     }
     return "SF_UNKNOWN";
 }
@@ -1720,6 +1731,40 @@ sf_status sf_detect(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_me
     for (const Filt &f : c->filt) nl += 3 + (f.slot >= 0 ? 1 : 0);
     tf.done(nl);
     return SF_OK;
+}
+
+sf_status sf_detect_slab(sf_ctx *c, const void *d_ext, int64_t halo, uint32_t *d_mask, float *d_mean,
+                         float *d_std, void *stream)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (!d_ext || !d_mask) return fail(c, SF_EINVAL, "NULL buffer");
+    if ((d_mean == nullptr) != (d_std == nullptr))
+        return fail(c, SF_EINVAL, "d_mean and d_std must both be NULL or both be set");
+    if (!aligned16(d_ext)) return fail(c, SF_EINVAL, "cube must be 16-byte aligned");
+    if (c->batch) return fail(c, SF_EINVAL, "batched context: slabs take a plain context");
+    if (!c->fused) return fail(c, SF_EINVAL, "slabs need the fused window kernel (wy %% 8 == 0, wz %% 32 == 0)");
+    int rxm = 0;
+    for (int r : c->xy_radius) rxm = std::max(rxm, r);
+    const long long S = c->cfg.nx - 2 * (long long)halo;
+    if (halo < rxm || S < 1)
+        return fail(c, SF_EINVAL, "halo %lld: needs >= %d planes and nx - 2 halo >= 1 (nx = %lld)",
+                    (long long)halo, rxm, (long long)c->cfg.nx);
+    DeviceGuard dg(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        /* x pass of the slab's planes only; they read the halo planes */
+        StageTimer tx(c, 0, st);
+        for (size_t i = 0; i < c->xlaunch.size(); ++i)
+            if ((s = run_xpass(c, c->xlaunch[i], c->xgroups[i], d_ext, st, halo, halo + S)) != SF_OK)
+                return s;
+        tx.done((int)c->xlaunch.size());
+    }
+    StageTimer tf(c, 1, st);
+    const int nwx = (int)((S + c->cfg.wx - 1) / c->cfg.wx);
+    s = launch_windows(c, d_ext, d_mask, d_mean, d_std, st, 0, nwx * c->nwy * c->nwz, halo, halo + S, nwx);
+    if (s == SF_OK) tf.done(1);
+    return s;
 }
 
 sf_status sf_detect_batch(sf_ctx *c, const void *const *d_cubes, uint32_t *const *d_masks,
@@ -2364,6 +2409,7 @@ sf_status sf_weighted_detect(sf_ctx *c, const float *d_cube, const float *d_weig
         da.nwin = c->nwin;
         da.k = c->cfg.k;
         da.err = c->err_flag;
+        da.wait_ns = c->wait_ns;
         da.wid0 = 0;
         void *args[] = {&da, (void *)W.taps.data(), (void *)Wm.maps.data()};
         return launch(c, W.L, args, st, "weighted window kernel launch");
@@ -2397,9 +2443,54 @@ sf_status sf_synchronize(sf_ctx *c, void *stream)
         return cuda_fail(c, e, "error flag read");
     if (flag) {
         cudaMemset(c->err_flag, 0, sizeof(int));
-        return fail(c, SF_ETIMEOUT, "a kernel's bounded wait for its shared-memory loads expired");
+        return fail(c, SF_ETIMEOUT, "a kernel's bounded wait (shared-memory loads, or another CTA's "
+                                    "x pass) expired");
     }
     return SF_OK;
+}
+
+sf_status sf_set_wait_limit(sf_ctx *c, int64_t limit_ns)
+{
+    sf_status s = check_live(c, true);
+    if (s != SF_OK) return s;
+    if (limit_ns < 1000 || limit_ns > 60000000000LL)
+        return fail(c, SF_EINVAL, "wait limit %lld ns outside [1 us, 60 s]", (long long)limit_ns);
+    c->wait_ns = limit_ns;
+    if (c->sectioned) {
+        for (sf_ctx *u : c->sub)
+            if (u && (s = sf_set_wait_limit(u, limit_ns)) != SF_OK) return fail(c, s, "section: %s", u->err.c_str());
+        return SF_OK;
+    }
+    /* the persistent graph holds its launch arguments: capture it again */
+    if (c->pready) {
+        DeviceGuard dg(c->device);
+        if (c->gpending) {
+            cudaError_t e = cudaEventSynchronize(c->gdone);
+            if (e != cudaSuccess) return cuda_fail(c, e, "previous batch");
+            c->gpending = false;
+        }
+        return plan_persist(c, sf_ctx::PersistPlan(c->pp));
+    }
+    return SF_OK;
+}
+
+sf_status sf_test_stall_batch(sf_ctx *c, int32_t extra)
+{
+    sf_status s = check_live(c);
+    if (s != SF_OK) return s;
+    if (!c->batch) return fail(c, SF_EINVAL, "the stall hook takes a batched context");
+    if (extra < 0 || extra > 1000000) return fail(c, SF_EINVAL, "extra %d outside [0, 1e6]", (int)extra);
+    if (c->xy_sigma.empty()) return fail(c, SF_EINVAL, "the bank has no x pass to wait for");
+    DeviceGuard dg(c->device);
+    if (c->gpending) {
+        cudaError_t e = cudaEventSynchronize(c->gdone);
+        if (e != cudaSuccess) return cuda_fail(c, e, "previous batch");
+        c->gpending = false;
+    }
+    c->stall_extra = extra;
+    sf_ctx::PersistPlan q;   /* x items inside the persistent kernel, whole cubes */
+    q.xbatch = false;
+    return plan_persist(c, q);
 }
 
 }  /* extern "C" */

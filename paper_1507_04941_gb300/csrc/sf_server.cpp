@@ -13,6 +13,8 @@
  * device buffers stay resident) and counted against the budget; idle ones are
  * destroyed, least recently used first, when an admission needs the room.
  * A request larger than the whole budget completes at once with SF_EBUDGET.
+ * A request still waiting for admission can be cancelled (it completes with
+ * SF_ECANCELED); one already admitted runs to its end.
  *
  * The paper processes device-sized sections one after another, with copies
  * not overlapped (Sec. 3.1), and names overlapping input with processing as
@@ -79,7 +81,7 @@ struct sf_server {
     int64_t in_use = 0, idle_bytes = 0, peak = 0;
     int64_t next_id = 1;
     int64_t n_submitted = 0, n_admitted = 0, n_completed = 0, n_rejected = 0, n_evicted = 0,
-            n_created = 0;
+            n_created = 0, n_cancelled = 0;
     int busy = 0;
     bool stop = false;
     std::vector<std::thread> workers;
@@ -255,6 +257,27 @@ sf_status sf_server_submit(sf_server *s, const void *h_cube, int64_t nx, int64_t
     return SF_OK;
 }
 
+sf_status sf_server_cancel(sf_server *s, int64_t id)
+{
+    if (!s) return SF_EINVAL;
+    Request *r = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = std::find_if(s->queue.begin(), s->queue.end(), [&](const Request *q) { return q->id == id; });
+        if (it == s->queue.end()) return SF_ESTATE;   /* admitted, done, or unknown */
+        r = *it;
+        s->queue.erase(it);
+        r->status = SF_ECANCELED;
+        r->t_done = now_ns();
+        ++s->n_cancelled;
+        ++s->n_completed;
+        s->done.push_back(r);
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+    return SF_OK;
+}
+
 sf_status sf_server_poll(sf_server *s, int64_t *ids, int32_t *statuses, int64_t *latency_ns,
                          int32_t cap, int32_t timeout_ms, int32_t *n)
 {
@@ -281,7 +304,7 @@ sf_status sf_server_stats(sf_server *s, int64_t *out, int32_t cap)
     std::lock_guard<std::mutex> lk(s->mu);
     const int64_t v[] = {s->n_submitted, s->n_admitted, s->n_completed, s->n_rejected, s->in_use,
                          s->peak,        s->idle_bytes, s->n_evicted,   s->n_created,  s->busy,
-                         (int64_t)s->queue.size(), s->budget};
+                         (int64_t)s->queue.size(), s->budget, s->n_cancelled};
     const int32_t m = std::min<int32_t>(cap, (int32_t)(sizeof(v) / sizeof(v[0])));
     std::memcpy(out, v, sizeof(int64_t) * (size_t)m);
     return SF_OK;

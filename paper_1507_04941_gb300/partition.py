@@ -78,6 +78,31 @@ def exchange_halo(slab, rank: int, world: int, halo: int, group=None):
     return left, right
 
 
+def exchange_halo_into(ext, halo: int, rank: int, world: int, group=None):
+    """In-place exchange on a preallocated extended slab ext = [halo | slab |
+    halo] (x the major axis, so every part is a contiguous view): this rank's
+    first and last `halo` slab planes go to its neighbours, whose planes are
+    received straight into ext[:halo] and ext[-halo:].  Halo planes without a
+    neighbour are left as they are (zeros, set once by the caller).  Slabs
+    must be at least `halo` planes thick."""
+    import torch.distributed as dist
+
+    if halo == 0 or world == 1:
+        return
+    s = ext.shape[0] - 2 * halo
+    if s < halo:
+        raise ValueError("slab thinner than its halo")
+    ops = []
+    if rank > 0:
+        ops.append(dist.P2POp(dist.isend, ext[halo:2 * halo], rank - 1, group))
+        ops.append(dist.P2POp(dist.irecv, ext[:halo], rank - 1, group))
+    if rank < world - 1:
+        ops.append(dist.P2POp(dist.isend, ext[s:s + halo], rank + 1, group))
+        ops.append(dist.P2POp(dist.irecv, ext[s + halo:], rank + 1, group))
+    for req in dist.batch_isend_irecv(ops):
+        req.wait()
+
+
 def extended_slab(slab, left, right):
     """Halo + slab + halo along x, the input of the x pass for this rank."""
     import torch

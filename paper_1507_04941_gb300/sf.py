@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-SF_OK, SF_EINVAL, SF_ENOMEM, SF_EBUDGET, SF_ECUDA, SF_ETIMEOUT, SF_ESTATE, SF_EJIT = range(8)
+SF_OK, SF_EINVAL, SF_ENOMEM, SF_EBUDGET, SF_ECUDA, SF_ETIMEOUT, SF_ESTATE, SF_EJIT, SF_ECANCELED = range(9)
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 
 _lock = threading.Lock()
@@ -61,6 +61,7 @@ SIGNATURES = {
     "sf_threshold": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp]),
     "sf_detect": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "sf_detect_host": (_i32, [_vp, _vp, _vp, _vp]),
+    "sf_detect_slab": (_i32, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "sf_synchronize": (_i32, [_vp, _vp]),
     "sf_create_sectioned": (_i32, [ctypes.POINTER(Config), _i64, ctypes.POINTER(_vp)]),
     "sf_create_batch": (_i32, [ctypes.POINTER(Config), _i32, ctypes.POINTER(_i64),
@@ -71,6 +72,7 @@ SIGNATURES = {
     "sf_tune_report": (_i32, [_vp, ctypes.c_char_p, _i32]),
     "sf_server_create": (_i32, [ctypes.POINTER(Config), _i64, _i32, ctypes.POINTER(_vp)]),
     "sf_server_submit": (_i32, [_vp, _vp, _i64, _i64, _i64, _vp, ctypes.POINTER(_i64)]),
+    "sf_server_cancel": (_i32, [_vp, _i64]),
     "sf_server_poll": (_i32, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_i64),
                               _i32, _i32, ctypes.POINTER(_i32)]),
     "sf_server_stats": (_i32, [_vp, ctypes.POINTER(_i64), _i32]),
@@ -84,6 +86,8 @@ SIGNATURES = {
     "sf_weighted_detect": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
     "sf_profile_enable": (_i32, [_vp, _i32]),
     "sf_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _i32]),
+    "sf_set_wait_limit": (_i32, [_vp, _i64]),
+    "sf_test_stall_batch": (_i32, [_vp, _i32]),
     "sf_fp32_peak": (_i32, [_i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "sf_fp32_peak_error": (ctypes.c_char_p, []),
 }
@@ -254,6 +258,28 @@ class SourceFinder:
                                _stream(self.device)), self._h)
         return (mask, mean, std) if stats else mask
 
+    def detect_slab(self, ext, halo: int, mask=None, stats: bool = False):
+        """sf_detect_slab: `ext` is this context's cube, an x slab with `halo`
+        neighbour planes on each side; returns the slab's mask words
+        [nx - 2 halo][ny][ceil(nz/32)] (and with stats=True its windows'
+        mean, std [n_filters][ceil(S/wx)][nwy][nwz])."""
+        import torch
+        self._check_cube(ext)
+        halo = int(halo)
+        S = self.shape[0] - 2 * halo
+        if S < 1:
+            raise ValueError("the slab needs at least one plane between its halos")
+        if mask is None:
+            mask = torch.empty((S,) + self.mask_shape[1:], dtype=torch.int32, device=self.device)
+        mean = std = None
+        if stats:
+            shp = (len(self.bank), -(-S // self.window[0])) + self.grid[1:]
+            mean = torch.empty(shp, dtype=torch.float32, device=self.device)
+            std = torch.empty(shp, dtype=torch.float32, device=self.device)
+        _check(lib().sf_detect_slab(self._h, _ptr(ext), halo, _ptr(mask), _ptr(mean), _ptr(std),
+                                    _stream(self.device)), self._h)
+        return (mask, mean, std) if stats else mask
+
     def local_stats(self, filtered, half, mean=None, std=None):
         """Per-voxel mean and std of a filtered cube over the box of
         half-widths half = (sx, sy, sz) clipped to the cube (float32, the
@@ -355,6 +381,10 @@ class SourceFinder:
     def synchronize(self):
         """Wait for this context's work on the current stream; raise on kernel-side timeouts."""
         _check(lib().sf_synchronize(self._h, _stream(self.device)), self._h)
+
+    def set_wait_limit(self, ns: int):
+        """Limit of the kernels' bounded waits in ns (sf_set_wait_limit)."""
+        _check(lib().sf_set_wait_limit(self._h, int(ns)), self._h)
 
     def profile(self, enable: bool = True):
         """Record CUDA events around the stages of every sf_detect."""
@@ -536,6 +566,14 @@ class BatchSourceFinder:
     def synchronize(self):
         _check(lib().sf_synchronize(self._h, _stream(self.device)), self._h)
 
+    def set_wait_limit(self, ns: int):
+        """Limit of the kernels' bounded waits in ns (sf_set_wait_limit)."""
+        _check(lib().sf_set_wait_limit(self._h, int(ns)), self._h)
+
+    def test_stall(self, extra: int):
+        """Test hook of sf_test_stall_batch (bounded-wait path)."""
+        _check(lib().sf_test_stall_batch(self._h, int(extra)), self._h)
+
     def close(self):
         if getattr(self, "_h", None):
             lib().sf_destroy(self._h)
@@ -555,7 +593,7 @@ class BatchSourceFinder:
 
 
 SERVER_STATS = ("submitted", "admitted", "completed", "rejected", "bytes_in_use", "peak_bytes",
-                "idle_bytes", "evictions", "contexts_created", "busy", "queued", "budget")
+                "idle_bytes", "evictions", "contexts_created", "busy", "queued", "budget", "cancelled")
 
 
 class Server:
@@ -588,6 +626,16 @@ class Server:
             raise SfError(st, "sf_server_submit")
         self._keep[rid.value] = (cube_host, mask_host)
         return rid.value
+
+    def cancel(self, rid: int) -> bool:
+        """Cancel a request still waiting for admission (it completes with
+        SF_ECANCELED); False if it was already admitted or done."""
+        st = lib().sf_server_cancel(self._h, int(rid))
+        if st == SF_ESTATE:
+            return False
+        if st != SF_OK:
+            raise SfError(st, "sf_server_cancel")
+        return True
 
     def poll(self, cap: int = 256, timeout_ms: int = 0):
         """[(id, status, latency_seconds)] of requests completed since the last poll."""

@@ -54,7 +54,7 @@ def test_status_strings(libsf):
     from paper_1507_04941_gb300 import sf
     lib = sf.lib()
     for code, name in enumerate(["SF_OK", "SF_EINVAL", "SF_ENOMEM", "SF_EBUDGET", "SF_ECUDA",
-                                 "SF_ETIMEOUT", "SF_ESTATE", "SF_EJIT"]):
+                                 "SF_ETIMEOUT", "SF_ESTATE", "SF_EJIT", "SF_ECANCELED"]):
         assert lib.sf_status_str(code).decode() == name
 
 

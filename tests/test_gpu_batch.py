@@ -114,3 +114,50 @@ def test_tune_keeps_results(dev):
         bf.synchronize()
         for x, y in zip(before, after):
             assert torch.equal(x, y)
+
+
+def test_bounded_wait_expires_and_context_recovers(dev):
+    """The watchdog path: with the test hook, every window item of the
+    persistent kernel waits for one x item more than its cube has, so each
+    wait runs into its limit (1 ms here) and the CTA leaves; sf_synchronize
+    reports SF_ETIMEOUT once.  The same context, with the hook off, then
+    gives masks bit-identical to the per-cube path, and a fresh context works.
+    Nothing faults: the waits are bounded spins on a counter."""
+    import time
+
+    import torch
+    from paper_1507_04941_gb300 import BatchSourceFinder, SfError
+    from paper_1507_04941_gb300.sf import SF_ETIMEOUT
+    shapes = SHAPES[:3]
+    cubes = _cubes(dev)[:3]
+    with BatchSourceFinder(shapes, BANK6, 3.0, (32, 32, 64), device=dev) as bf:
+        bf.set_wait_limit(1_000_000)
+        bf.test_stall(1)
+        t0 = time.perf_counter()
+        bf.detect(cubes)
+        with pytest.raises(SfError) as exc:
+            bf.synchronize()
+        assert exc.value.status == SF_ETIMEOUT
+        assert time.perf_counter() - t0 < 10.0
+        bf.synchronize()   # the flag was cleared
+        bf.test_stall(0)
+        bf.set_wait_limit(2_000_000_000)
+        masks = bf.detect(cubes)
+        bf.synchronize()
+        for i, cube in enumerate(cubes):
+            assert torch.equal(masks[i].cpu(), _single(dev, cube)[0]), f"cube {i} after recovery"
+    with BatchSourceFinder(shapes, BANK6, 3.0, (32, 32, 64), device=dev) as bf2:
+        masks = bf2.detect(cubes)
+        bf2.synchronize()
+        assert torch.equal(masks[0].cpu(), _single(dev, cubes[0])[0])
+
+
+def test_wait_limit_and_stall_hook_arguments(dev):
+    from paper_1507_04941_gb300 import BatchSourceFinder, SfError, SourceFinder
+    with SourceFinder((32, 32, 64), BANK6, 3.0, (32, 32, 64), device=dev) as sf:
+        with pytest.raises(SfError):
+            sf.set_wait_limit(10)
+        sf.set_wait_limit(5_000_000)
+    with BatchSourceFinder(SHAPES[:2], BANK6, 3.0, (32, 32, 64), device=dev) as bf:
+        with pytest.raises(SfError):
+            bf.test_stall(-1)

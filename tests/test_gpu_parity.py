@@ -49,8 +49,14 @@ def _assert_stats(gm, gs, rm, rs, rel=1e-5, what=""):
 
 
 def _assert_mask(got_bits, want_bits, sure_bits, what=""):
+    """Bit-exact where the oracle's decision is certain; the differing bits
+    inside the guard band are counted, printed and returned."""
     diff = (got_bits != want_bits) & sure_bits
     assert not diff.any(), f"{what}: {int(diff.sum())} certain mask bits differ"
+    band = int((~sure_bits).sum())
+    inside = int(((got_bits != want_bits) & ~sure_bits).sum())
+    print(f"\n[{what}] guard band: {band} voxels, {inside} differing bits inside it")
+    return inside
 
 
 # --------------------------------------------------------------- taps ------

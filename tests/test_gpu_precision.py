@@ -112,3 +112,119 @@ def test_detect_precision(dev, oracle, storage):
           f"precision band, {n_dis} disagreements; vs FP32 storage on the same cube: "
           f"{int((got != m32).sum())} differing bits; stats worst {worst_stat:.3f} x bound")
     assert n_fire > 0
+
+
+# ---- the precision workload at its own size: 1024 x 1024 x 2048, noise sigma
+# rising 0.8 -> 1.5 along z, 1000 sources, the six-filter bank ----
+
+def _windows(grid, n, seed):
+    """Seeded window indices: the eight corners of the window grid, then n
+    more drawn uniformly."""
+    rng = np.random.default_rng(seed)
+    out = [(a, b, e) for a in (0, grid[0] - 1) for b in (0, grid[1] - 1) for e in (0, grid[2] - 1)]
+    while len(out) < 8 + n:
+        w = tuple(int(rng.integers(0, g)) for g in grid)
+        if w not in out:
+            out.append(w)
+    return out
+
+
+@pytest.fixture(scope="module")
+def precision_cube(dev):
+    from paper_1507_04941_gb300 import synth
+    return synth.make(synth.PRECISION, device=dev)
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16", "f32"])
+def test_precision_workload(dev, oracle, precision_cube, storage):
+    """The full-size precision workload through sf_filter and sf_detect (the
+    bench's launch shape), compared on 32 seeded windows (corners included)
+    with the FP64 oracle.  Gate: the oracle on the storage-rounded cube, with
+    the bound of the module docstring (sigma_noise = 0.8, its smallest value;
+    FP32 storage: 1e-5 A for filtered values, 1e-5 max(std, |mean|) for the
+    statistics).  Reported per output (printed): the largest error against
+    the oracle on the FP32 cube, in units of the local noise sigma, and the
+    mask disagreements where the oracle's decision is certain."""
+    import torch
+    from paper_1507_04941_gb300 import SourceFinder, synth, words_to_bits
+    w = synth.PRECISION
+    shape, window = w.shape, w.window
+    tdt = {"f16": torch.float16, "bf16": torch.bfloat16, "f32": torch.float32}[storage]
+    cq = precision_cube.to(tdt).contiguous()
+    d_q = cq.float().cpu().numpy()
+    d32 = precision_cube.cpu().numpy()
+    eps = 2.0 ** -(MANT[storage] + 1) if storage in MANT else 0.0
+    floor = 1e-3 * 0.8 if storage in MANT else 0.0
+    nz = shape[2]
+    sig_z = 0.8 + 0.7 * np.arange(nz) / (nz - 1)
+    wins = None
+    report = {"filtered": 0.0, "mean": 0.0, "std": 0.0}
+    n_dis = n_unsure = n_fire = n_dis32 = 0
+    with SourceFinder(shape, w.bank, w.truncation, window, w.k, storage=storage, device=dev) as sf:
+        grid = sf.grid
+        wins = _windows(grid, 24, 2026)
+        mask, mean, std = sf.detect(cq, stats=True)
+        torch.cuda.synchronize(dev)
+        mask = mask.cpu().numpy()
+        gm, gs = mean.cpu().numpy(), std.cpu().numpy()
+        refs = [oracle.detect_window(d_q, w.bank, w.truncation, window, w.k, wi) for wi in wins]
+        refs32 = [oracle.detect_window(d32, w.bank, w.truncation, window, w.k, wi) for wi in wins]
+        # filtered values of the sampled windows, one filter at a time (8 GiB each)
+        for f, (sxy, sz) in enumerate(w.bank):
+            c = sf.filter(cq, f)
+            torch.cuda.synchronize(dev)
+            for wi, r, r32 in zip(wins, refs, refs32):
+                x0, y0, z0 = r["origin"]
+                ex, ey, ez = r["fire"].shape
+                g = c[x0:x0 + ex, y0:y0 + ey, z0:z0 + ez].cpu().numpy().astype(np.float64)
+                box = ((x0, x0 + ex), (y0, y0 + ey), (z0, z0 + ez))
+                A = oracle.filter_box(d_q, sxy, sz, w.truncation, box=box, take_abs=True)
+                bound = floor + (eps + 1e-5) * A
+                err = np.abs(g - r["c"][f])
+                assert (err <= bound).all(), f"{storage} filter {f} window {wi}: {(err / bound).max():.3g} x bound"
+                sig = sig_z[z0:z0 + ez][None, None, :]
+                report["filtered"] = max(report["filtered"], float((np.abs(g - r32["c"][f]) / sig).max()))
+            del c
+    for wi, r, r32 in zip(wins, refs, refs32):
+        a, b, e = wi
+        x0, y0, z0 = r["origin"]
+        ex, ey, ez = r["fire"].shape
+        box = ((x0, x0 + ex), (y0, y0 + ey), (z0, z0 + ez))
+        sig = float(sig_z[z0:z0 + ez].mean())
+        unsure = np.zeros(r["fire"].shape, dtype=bool)
+        sure_fire = np.zeros(r["fire"].shape, dtype=bool)
+        for f, (sxy, sz) in enumerate(w.bank):
+            A = oracle.filter_box(d_q, sxy, sz, w.truncation, box=box, take_abs=True)
+            band = floor + (eps + 1e-5) * A + 1e-4 * r["std"][f]
+            dlt = r["c"][f] - r["thr"][f]
+            unsure |= np.abs(dlt) < band
+            sure_fire |= dlt >= band
+            if storage in MANT:
+                sbound = floor + (eps + 1e-5) * A.max()
+            else:
+                sbound = 1e-5 * max(r["std"][f], abs(r["mean"][f]))
+            dm = abs(gm[f, a, b, e] - r["mean"][f])
+            ds = abs(gs[f, a, b, e] - r["std"][f])
+            assert dm <= sbound and ds <= sbound, f"{storage} stats window {wi} f{f}: {dm:.3g} {ds:.3g}"
+            report["mean"] = max(report["mean"], abs(gm[f, a, b, e] - r32["mean"][f]) / sig)
+            report["std"] = max(report["std"], abs(gs[f, a, b, e] - r32["std"][f]) / sig)
+        certain = sure_fire | ~unsure
+        gbits = words_to_bits(mask[x0:x0 + ex, y0:y0 + ey], shape[2])[:, :, z0:z0 + ez]
+        want = r["fire"].astype(bool)
+        assert not ((gbits != want) & certain).any(), f"{storage} window {wi}"
+        n_dis += int((gbits != want).sum())
+        n_unsure += int((~certain).sum())
+        n_fire += int(want.sum())
+        sure32 = r32["sure"].astype(bool)
+        n_dis32 += int(((gbits != r32["fire"].astype(bool)) & sure32).sum())
+    assert n_fire > 0
+    if storage == "f16":
+        # FP16 storage meets 1e-3 sigma_noise on the filtered values against
+        # the oracle on the FP32 cube itself; BF16 (8-bit mantissa, half an
+        # ulp at 1.0 is 2^-8) cannot, and its error is reported only
+        assert report["filtered"] <= 1e-3, report
+    print(f"\n[{storage}] precision workload, {len(wins)} windows: vs FP64 oracle on the FP32 cube "
+          f"(units of the local noise sigma): filtered {report['filtered']:.3e}, mean "
+          f"{report['mean']:.3e}, std {report['std']:.3e}; mask disagreements where that oracle is "
+          f"certain: {n_dis32}; vs the oracle on the {storage}-rounded cube: {n_fire} detections, "
+          f"{n_unsure} voxels in the precision band, {n_dis} disagreements")
