@@ -798,6 +798,34 @@ __device__ __forceinline__ bool sfw_wait(u32 bar, u32 parity, unsigned long long
     return true;
 }
 
+/* plane maxima: a three-input max and one warp-wide reduction instruction
+ * (sm_100a and later), or the two-input max and a shuffle tree */
+#ifndef SFD_FASTMAX
+#define SFD_FASTMAX 1
+#endif
+__device__ __forceinline__ float sfw_max3(float a, float b, float c)
+{
+#if SFD_FASTMAX
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+#else
+    return fmaxf(a, fmaxf(b, c));
+#endif
+}
+__device__ __forceinline__ float sfw_warp_max(float v)
+{
+#if SFD_FASTMAX
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+#else
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+    return v;
+#endif
+}
+
 struct sfw_state {
     sfd_t *slab0;
     float *U;
@@ -982,7 +1010,7 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
                         const f2 d = f2_add(f2_pack(c[f][i], c[f][i + 1]), NK);
                         s1p[f] = f2_add(s1p[f], d);
                         s2p[f] = f2_fma(d, d, s2p[f]);
-                        mx = fmaxf(mx, fmaxf(c[f][i], c[f][i + 1]));
+                        mx = sfw_max3(mx, c[f][i], c[f][i + 1]);
                     }
                 } else {
 #pragma unroll
@@ -994,8 +1022,7 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
                             mx = fmaxf(mx, c[f][i]);
                         }
                 }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+                mx = sfw_warp_max(mx);
                 if (lane == 0) S.pmax[(p * SFD_NWARP + warp) * SFD_NZF + f] = mx;
             }
             cnt += __popc(S.vmask);

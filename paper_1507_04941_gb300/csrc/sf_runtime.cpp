@@ -747,6 +747,8 @@ bool make_window_plan(const sf_ctx *c, int P, int minb, int CH, bool tma_shape, 
     p += "#define SFD_OFF_THR " + std::to_string(wp.off_th) + "\n";
     p += "#define SFD_OFF_FLAGS " + std::to_string(wp.off_fl) + "\n";
     p += "#define SFD_OFF_MBAR " + std::to_string(wp.off_mb) + "\n";
+    /* three-input max and warp-reduced plane maxima (SF_NO_FASTMAX=1: shuffles) */
+    if (env_int("SF_NO_FASTMAX", 0)) p += "#define SFD_FASTMAX 0\n";
     if (weighted >= 0) p += "#define SFD_WEIGHTED 1\n";
     if (c->cfg.stats_fp64) p += "#define SFD_STATS64 1\n";
     if (c->cfg.std_ddof) p += "#define SFD_DDOF 1\n";
