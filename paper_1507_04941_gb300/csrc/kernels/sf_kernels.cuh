@@ -425,7 +425,7 @@ sf_xpass_batch(const __grid_constant__ sf_xbargs a, const __grid_constant__ sfx_
 #endif /* SF_KERNEL_XBATCH */
 
 /* ======================================================================= */
-#if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_FILTER) || defined(SF_KERNEL_PERSIST)
+#if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_FILTER) || defined(SF_KERNEL_PERSIST) || defined(SF_KERNEL_TC)
 #ifndef SFD_X2
 #define SFD_X2 0
 #endif
@@ -704,7 +704,7 @@ __device__ __forceinline__ void sfd_zfilter(const sfd_t *slab, const float *U, i
 #endif
 
 /* ======================================================================= */
-#if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_PERSIST)
+#if defined(SF_KERNEL_DETECT) || defined(SF_KERNEL_PERSIST) || defined(SF_KERNEL_TC)
 /*
  * sf_window_detect: one CTA per statistics window (grid = number of windows).
  * For every input cube of the plan (the cube itself, then each x-filtered
@@ -1371,6 +1371,618 @@ sf_persist(const __grid_constant__ sf_pargs pa, const __grid_constant__ sfd_taps
     }
 }
 #endif /* SF_KERNEL_PERSIST */
+
+/* ======================================================================= */
+#ifdef SF_KERNEL_TC
+/*
+ * sf_window_tc: the window kernel for 16-bit storage with both spectral (z)
+ * and spatial (y) filters on the tensor cores (tcgen05, kind::f16, FP32
+ * accumulation in tensor memory).  16-bit values are exact tensor-core
+ * operands; every tap is split into two 16-bit parts (hi + lo; the z taps
+ * scaled by 2^SFT_SCALE so their low parts stay normal), which carries the
+ * taps to about 2^-22.
+ *
+ * y filter (inputs with sigma_xy > 0), one x-plane at a time: the plane's
+ * slab (rows y0-R .. y0+31+R padded to KY, 128 staged columns) arrives by TMA
+ * in the 128-byte swizzled layout with z contiguous, which the MMA reads as
+ * an MN-major A operand: U^T[z][y] = sum_k slab[k][z] Ty[y][k], M = 128 (z),
+ * N = 32 (y), K = KY, into a TMEM accumulator.  Each thread then reads its z
+ * column and writes the 32 values, rounded to the storage type, into the z
+ * filter's A tile (the y-filtered rows of the plane).
+ *
+ * z filter, per group of four planes (M = 128 = 4 planes x 32 rows): the
+ * z filter of a row is banded: outputs 16j..16j+15 of the window read the
+ * staged columns 16j + HZ - R .. 16j + 15 + HZ + R, i.e. the 16-column slices
+ * j + s_lo .. j + s_hi, so every output tile multiplies the same 16 x 64
+ * Toeplitz tile T[n][k] = g[k - n - HZ] by up to four K-slices of the A tile:
+ * one M=128 N=16 K=16 MMA per slice and tap part.  Inputs with sigma_xy = 0
+ * load the A tile (four planes) by TMA directly.
+ *
+ * The z accumulators feed the same per-window work as the CUDA-core kernel:
+ * shifted moments and plane maxima (pass 1), the window statistics and
+ * thresholds, then the selection bits of the flagged planes (pass 2).
+ * Thread (warp w, lane l) owns TMEM lane quarter w % 4 (plane w % 4 of the
+ * group, row l) and filter w / 4: 64 outputs per group.  One thread issues
+ * the MMAs and commits them to mbarriers; every wait is bounded.
+ */
+#ifndef SFT_SCALE
+#define SFT_SCALE 10
+#endif
+constexpr int SFT_M = 128;
+constexpr int SFT_PLANES = SFT_M / SFD_WY;          /* planes per group (4) */
+constexpr int SFT_ATOM = SFT_M * 128;                /* bytes of one 64-column atom of the A tile */
+constexpr int SFT_TM_COLS = 256;                     /* z accumulators at 0 and 128; y at 128, 160 */
+constexpr int SFT_KYM = (SFD_WY + 2 * SFD_RYM + 15) / 16 * 16;   /* padded slab rows */
+constexpr int SFT_SLAB_BYTES = 2 * SFT_KYM * 128;    /* one slab buffer: two 64-column atoms */
+static_assert(SFD_WY == 32 && SFD_WZ == 64 && SFD_THREADS == 256, "window 32 x 64, 256 threads");
+static_assert(SFD_NZF <= 2, "at most two spectral filters per input");
+static_assert(SFD_HZ + SFD_RZM <= 48, "band within the 64-column Toeplitz tile");
+static_assert(SFT_KYM <= 64, "y filter rows within one 128-byte row of the y tile");
+
+struct sft_tiles {
+    unsigned char z[SFT_NZT][2][2048];                  /* z Toeplitz tiles: 16 x 64, hi and lo */
+    unsigned char y[SFT_NYT > 0 ? SFT_NYT : 1][2][4096]; /* y Toeplitz tiles: 32 x 64, hi and lo */
+    int zt[SFD_NSRC][SFD_NZF];                          /* z tile of each (input, filter) */
+    int yt[SFD_NSRC];                                   /* y tile of each input (-1: none) */
+};
+struct sft_maps { sf_tmap m[SFD_NSRC]; };
+constexpr int SFT_TILE_BYTES = (int)(sizeof(((sft_tiles *)0)->z) + sizeof(((sft_tiles *)0)->y));
+
+__device__ __forceinline__ u32 sft_sw128(u32 row, u32 kbyte)
+{
+    return (row >> 3) * 1024u + (row & 7u) * 128u + ((((kbyte >> 4) ^ (row & 7u)) & 7u) << 4) + (kbyte & 15u);
+}
+/* shared-memory matrix descriptor, 128-byte swizzle, version 1: lbo = stride
+ * between 64-element atoms along M/N (MN-major operands), sbo = stride
+ * between 8-row groups */
+__device__ __forceinline__ unsigned long long sft_desc(u32 addr, u32 lbo, u32 sbo)
+{
+    return (unsigned long long)((addr >> 4) & 0x3fffu) | ((unsigned long long)((lbo >> 4) & 0x3fffu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46) | (2ull << 61);
+}
+/* kind::f16 instruction descriptors: D FP32, A/B FP16 (0) or BF16 (1);
+ * z: both K-major, N = 16, M = 128; y: A MN-major, N = 32, M = 128 */
+constexpr u32 SFT_AB = SFT_BF16 ? 1u : 0u;
+constexpr u32 SFT_IDESC_Z = (1u << 4) | (SFT_AB << 7) | (SFT_AB << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr u32 SFT_IDESC_Y =
+    (1u << 4) | (SFT_AB << 7) | (SFT_AB << 10) | (1u << 15) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__host__ __device__ constexpr int sft_slo(int r) { return (SFD_HZ - r) / 16; }
+__host__ __device__ constexpr int sft_shi(int r) { return (15 + SFD_HZ + r) / 16; }
+__host__ __device__ constexpr int sft_ky(int ry) { return (SFD_WY + 2 * ry + 15) / 16 * 16; }
+
+struct sft_state {
+    unsigned char *A;      /* z-filter A tile: 1024-aligned, two 16 KB atoms */
+    unsigned char *T;      /* tap tiles (z then y) */
+    unsigned char *slab;   /* y-filter slabs: two buffers of SFT_SLAB_BYTES */
+    float *pmax;           /* [WX][NZF] */
+    u32 *mask;             /* [WX][WY][2] */
+    sfd_st *red;           /* [8 warps][3] */
+    float *thr;            /* [NZF] */
+    u32 *flags;            /* [2] */
+    u32 bar_s;             /* slab copies (2), 8 bytes apart */
+    u32 bar_a;             /* A-tile copy */
+    u32 bar_z;             /* z-MMA commits (2) */
+    u32 bar_y;             /* y-MMA commits (2) */
+    u32 ph_s, ph_a, ph_z, ph_y;   /* parity of the next completion, bit per barrier */
+    u32 tmem;              /* accumulator base */
+    u32 pend;              /* completions awaited: bits 0-1 slabs, 2 A tile, 3-4 z, 5-6 y */
+    i64 x0, y0, z0;
+    int npl, wid;
+    int it;                /* slab planes consumed (buffer = it & 1) */
+    int ity;               /* y-MMAs issued (accumulator = ity & 1) */
+    unsigned long long limit;
+    int *err;
+    bool dead;
+};
+
+/* a bounded wait; on expiry the waiting site is recorded in *err (bit 1:
+ * A-tile copy, 2: slab copy, 3: z MMA, 4: y MMA) beside bit 0 */
+__device__ __forceinline__ bool sft_wait(sft_state &S, u32 bar, u32 &ph, int b, int site)
+{
+    const bool ok = sfw_wait(bar + 8u * (u32)b, (ph >> b) & 1u, S.limit);
+    ph ^= 1u << b;
+    if (!ok) atomicOr(S.err, 1 | (1 << site));
+    return ok;
+}
+
+/* the slab of plane x0+p of a y-filtered input into buffer b: two boxes
+ * {64 columns, KY rows, 1 plane}, 128-byte swizzle */
+template <int IDX, int RY>
+__device__ __forceinline__ void sft_load_slab(const sft_maps &mp, sft_state &S, int p, int b)
+{
+    if (threadIdx.x != 0) return;
+    constexpr int KY = sft_ky(RY);
+    unsigned char *dst = S.slab + b * SFT_SLAB_BYTES;
+    const u32 bar = S.bar_s + 8u * (u32)b;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((u32)(2 * KY * 128))
+                 : "memory");
+    const int cy = (int)(S.y0 - RY), cx = (int)(S.x0 + p);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int cz = (int)(S.z0 - SFD_HZ) + 64 * a;
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sf_smem_addr(dst + a * KY * 128)),
+                     "l"(reinterpret_cast<unsigned long long>(&mp.m[IDX])), "r"(cz), "r"(cy), "r"(cx), "r"(bar)
+                     : "memory");
+    }
+}
+
+/* A tile of group g of a sigma_xy = 0 input: two swizzled boxes {64, 32, 4} */
+template <int IDX>
+__device__ __forceinline__ void sft_load_a(const sft_maps &mp, sft_state &S, int g)
+{
+    if (threadIdx.x != 0) return;
+    const u32 bar = S.bar_a;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((u32)(2 * SFT_ATOM))
+                 : "memory");
+    const int cy = (int)S.y0, cx = (int)(S.x0 + SFT_PLANES * g);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int cz = (int)(S.z0 - SFD_HZ) + 64 * a;
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sf_smem_addr(S.A + a * SFT_ATOM)),
+                     "l"(reinterpret_cast<unsigned long long>(&mp.m[IDX])), "r"(cz), "r"(cy), "r"(cx), "r"(bar)
+                     : "memory");
+    }
+}
+
+/* the y-filter MMAs of the plane in slab buffer b into y accumulator yb */
+template <int RY>
+__device__ __forceinline__ void sft_mma_y(const sft_state &S, const sft_tiles &bt, int SI, int b, int yb)
+{
+    constexpr int KY = sft_ky(RY);
+    const u32 a0 = sf_smem_addr(S.slab + b * SFT_SLAB_BYTES);
+    const u32 t0 = sf_smem_addr(S.T + sizeof(bt.z) + bt.yt[SI] * 2 * 4096);
+    const u32 d = S.tmem + 128u + (u32)(yb * 32);
+    u32 acc = 0u;
+#pragma unroll
+    for (int s = 0; s < KY / 16; ++s)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const unsigned long long ad = sft_desc(a0 + (u32)(s * 2048), (u32)(KY * 128), 1024u);
+            const unsigned long long bd = sft_desc(t0 + (u32)(h * 4096 + s * 32), 16u, 1024u);
+            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                         "l"(ad), "l"(bd), "r"(SFT_IDESC_Y), "r"(acc));
+            acc = 1u;
+        }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(S.bar_y + 8u * (u32)yb)
+                 : "memory");
+}
+
+/* the z-filter MMAs of one group into z accumulator buf: for every filter and
+ * 16-output tile j, the K-slices j + s_lo .. j + s_hi against the filter's
+ * Toeplitz tile, hi and lo parts */
+template <int SI, int NZ, int RZ0, int RZ1>
+__device__ __forceinline__ void sft_mma_z(const sft_state &S, const sft_tiles &bt, int buf)
+{
+    const u32 a0 = sf_smem_addr(S.A);
+#pragma unroll
+    for (int f = 0; f < NZ; ++f) {
+        const int r = f == 0 ? RZ0 : RZ1;
+        const int slo = sft_slo(r), shi = sft_shi(r);
+        const u32 t0 = sf_smem_addr(S.T + bt.zt[SI][f] * 2 * 2048);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const u32 d = S.tmem + (u32)(buf * 128 + f * 64 + j * 16);
+            u32 acc = 0u;
+            for (int s = slo; s <= shi; ++s) {
+                const int ts = j + s;
+                const unsigned long long ad = sft_desc(a0 + (u32)((ts >> 2) * SFT_ATOM + (ts & 3) * 32), 16u, 1024u);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const unsigned long long bd = sft_desc(t0 + (u32)(h * 2048 + s * 32), 16u, 1024u);
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                                 "l"(ad), "l"(bd), "r"(SFT_IDESC_Z), "r"(acc));
+                    acc = 1u;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(S.bar_z + 8u * (u32)buf)
+                 : "memory");
+}
+
+/* 16 accumulator columns of this thread's lane */
+__device__ __forceinline__ void sft_ld16(u32 addr, float (&v)[16])
+{
+    u32 r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+/* the y-filtered plane in y accumulator yb into rows [32 slot, 32 slot + 32)
+ * of the A tile, rounded to the storage type: thread (w, l) takes column
+ * z = 32 (w % 4) + l, rows 16 (w / 4) .. +15 */
+__device__ __forceinline__ bool sft_convert(sft_state &S, int slot, int yb)
+{
+    const bool ok = sft_wait(S, S.bar_y, S.ph_y, yb, 4);
+    S.pend &= ~(32u << yb);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int z = 32 * (warp & 3) + lane, half = warp >> 2;
+    float v[16];
+    sft_ld16(S.tmem + ((u32)((warp & 3) * 32) << 16) + 128u + (u32)(yb * 32 + half * 16), v);
+    unsigned char *col = S.A + (z >> 6) * SFT_ATOM;
+    const u32 kb = (u32)((z & 63) * 2);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const u32 m = (u32)(slot * SFD_WY + half * 16 + q);
+        *reinterpret_cast<u16 *>(col + sft_sw128(m, kb)) = (u16)sf_enc16<sfd_t>(v[q]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    return ok;
+}
+
+/* first plane (y-filtered input) or A tile (sigma_xy = 0) of group g */
+template <int IDX, int RY>
+__device__ __forceinline__ void sft_start(const sft_maps &mp, sft_state &S, int g)
+{
+    if (g < 0) return;
+    if constexpr (RY > 0) {
+        const int b = S.it & 1;
+        sft_load_slab<IDX, RY>(mp, S, g * SFT_PLANES, b);
+        S.pend |= 1u << b;
+    } else {
+        sft_load_a<IDX>(mp, S, g);
+        S.pend |= 4u;
+    }
+}
+
+template <int IDX, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
+__device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, const sft_maps &mp,
+                                          const sft_tiles &bt, sft_state &S)
+{
+    static_assert(NZ <= 2, "two spectral filters per input");
+    (void)t;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int slot = warp & 3, f = warp >> 2;
+    const bool mine = f < NZ;
+    const i64 y = S.y0 + lane;
+    const bool rowv = y < a.ny;
+    const bool zfull = S.z0 + SFD_WZ <= a.nz;
+    const int ngr = (S.npl + SFT_PLANES - 1) / SFT_PLANES;
+    const float inv = 1.f / (float)(1 << SFT_SCALE);
+    float K = 0.f, s1 = 0.f, s2 = 0.f;
+    f2 s1p = 0ull, s2p = 0ull;
+    int cnt = 0;
+    bool haveK = false;
+    float T = 0.f;
+    u32 fl0 = 0u, fl1 = 0u;
+    int pass = 0;
+
+    auto next_group = [&](int after) -> int {
+        for (int g = after + 1; g < ngr; ++g) {
+            if (pass == 0) return g;
+            const int p = g * SFT_PLANES;
+            const u32 m = (p < 32 ? (fl0 >> p) : (fl1 >> (p - 32))) & 0xfu;
+            if (m) return g;
+        }
+        return -1;
+    };
+    /* read the z accumulator of group g (buffer b) once its MMAs completed */
+    auto epilogue = [&](int g, int b) {
+        const bool ok = sft_wait(S, S.bar_z, S.ph_z, b, 3);
+        S.pend &= ~(8u << b);
+        if (!ok) S.dead = true;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int p = g * SFT_PLANES + slot;
+        const bool pv = p < S.npl && rowv && mine;
+        float mx = -3.402823466e38f;
+        u32 w0 = 0u, w1 = 0u;
+        if (mine) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float v[16];
+                sft_ld16(S.tmem + ((u32)(slot * 32) << 16) + (u32)(b * 128 + f * 64 + j * 16), v);
+                if (!pv) continue;
+                if (pass == 0) {
+                    if (!haveK) { K = v[0]; haveK = true; }
+                    if (zfull) {
+                        const f2 NK = f2_pack(-K, -K);
+#pragma unroll
+                        for (int q = 0; q < 16; q += 2) {
+                            const f2 d = f2_add(f2_pack(v[q], v[q + 1]), NK);
+                            s1p = f2_add(s1p, d);
+                            s2p = f2_fma(d, d, s2p);
+                            mx = sfw_max3(mx, v[q], v[q + 1]);
+                        }
+                        cnt += 16;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q)
+                            if (S.z0 + 16 * j + q < a.nz) {
+                                const float d = v[q] - K;
+                                s1 += d;
+                                s2 = fmaf(d, d, s2);
+                                ++cnt;
+                                mx = fmaxf(mx, v[q]);
+                            }
+                    }
+                } else {
+                    u32 bits = 0u;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) bits |= (v[q] > T ? 1u : 0u) << q;
+                    if (!zfull) {
+                        const i64 left = a.nz - (S.z0 + 16 * j);
+                        bits &= left >= 16 ? 0xffffu : (left <= 0 ? 0u : ((1u << left) - 1u));
+                    }
+                    if (j < 2) w0 |= bits << (16 * j);
+                    else w1 |= bits << (16 * (j - 2));
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (pass == 0) {
+            if (mine) {
+                mx = sfw_warp_max(mx);
+                if (lane == 0 && p < S.npl) S.pmax[p * SFD_NZF + f] = mx;
+            }
+        } else if (pv && (w0 | w1)) {
+            atomicOr(&S.mask[(p * SFD_WY + lane) * 2 + 0], w0);
+            atomicOr(&S.mask[(p * SFD_WY + lane) * 2 + 1], w1);
+        }
+    };
+    /* the z MMAs of group g once its A tile is complete */
+    auto issue_z = [&](int g, int buf) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            sft_mma_z<IDX, NZ, RZ0, RZ1>(S, bt, buf);
+        }
+        S.pend |= 8u << buf;
+        (void)g;
+    };
+
+    sft_start<IDX, RY>(mp, S, next_group(-1));
+    for (;;) {
+        int pend_g = -1, pend_b = 0;
+        int gi = next_group(-1);
+        if constexpr (RY == 0) {
+            int nbuf = 0;
+            while (gi >= 0) {
+                const int gn = next_group(gi);
+                const bool ok = sft_wait(S, S.bar_a, S.ph_a, 0, 1);
+                S.pend &= ~4u;
+                if (__syncthreads_or(!ok)) { S.dead = true; return; }
+                const int cur = nbuf;
+                nbuf ^= 1;
+                issue_z(gi, cur);
+                if (pend_g >= 0) epilogue(pend_g, pend_b);
+                pend_g = gi;
+                pend_b = cur;
+                if (gn >= 0) {
+                    /* the next A tile may only land once these MMAs read this one
+                     * (a peek: the epilogue waits on the same completion) */
+                    const bool ok2 = sfw_wait(S.bar_z + 8u * (u32)cur, (S.ph_z >> cur) & 1u, S.limit);
+                    if (!ok2) atomicOr(S.err, 1 | (1 << 3));
+                    if (__syncthreads_or(!ok2)) { S.dead = true; return; }
+                    sft_load_a<IDX>(mp, S, gn);
+                    S.pend |= 4u;
+                }
+                gi = gn;
+            }
+        } else {
+            while (gi >= 0) {
+                const int gn = next_group(gi);
+                const int p0 = gi * SFT_PLANES;
+                const int np = min(SFT_PLANES, S.npl - p0);
+                int yprev = -1;
+                for (int i = 0; i < np; ++i) {
+                    const int b = S.it & 1;
+                    const bool ok = sft_wait(S, S.bar_s, S.ph_s, b, 2);
+                    S.pend &= ~(1u << b);
+                    if (__syncthreads_or(!ok)) { S.dead = true; return; }
+                    const int yb = S.ity & 1;
+                    if (threadIdx.x == 0) {
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        sft_mma_y<RY>(S, bt, IDX, b, yb);
+                    }
+                    S.pend |= 32u << yb;
+                    ++S.ity;
+                    ++S.it;
+                    /* the previous group's z accumulator, then the previous
+                     * plane into the A tile (its z MMAs are complete by then) */
+                    if (i == 0 && pend_g >= 0) {
+                        epilogue(pend_g, pend_b);
+                        pend_g = -1;
+                    }
+                    if (yprev >= 0 && !sft_convert(S, i - 1, yprev)) S.dead = true;
+                    yprev = yb;
+                    /* the other slab buffer is free once the plane before was filtered */
+                    const int pn = i + 1 < np ? p0 + i + 1 : (gn >= 0 ? gn * SFT_PLANES : -1);
+                    if (pn >= 0) {
+                        sft_load_slab<IDX, RY>(mp, S, pn, b ^ 1);
+                        S.pend |= 1u << (b ^ 1);
+                    }
+                }
+                if (!sft_convert(S, np - 1, yprev)) S.dead = true;
+                /* planes past the window's end: zero rows (excluded from every sum) */
+                for (int e = threadIdx.x + np * SFD_WY * 16; e < SFT_PLANES * SFD_WY * 16; e += SFD_THREADS) {
+                    const u32 m = (u32)(e / 16);
+                    const int k = 8 * (e % 16);
+                    *reinterpret_cast<uint4 *>(S.A + (k >> 6) * SFT_ATOM + sft_sw128(m, (u32)((k & 63) * 2))) =
+                        make_uint4(0u, 0u, 0u, 0u);
+                }
+                if (__syncthreads_or(S.dead)) { S.dead = true; return; }
+                issue_z(gi, 0);
+                pend_g = gi;
+                pend_b = 0;
+                gi = gn;
+            }
+        }
+        if (pend_g >= 0) epilogue(pend_g, pend_b);
+        if (__syncthreads_or(S.dead)) { S.dead = true; return; }
+        if (pass == 1) break;
+
+        /* end of pass 1: statistics, thresholds, flagged planes */
+        s1 += f2_lo(s1p) + f2_hi(s1p);
+        s2 += f2_lo(s2p) + f2_hi(s2p);
+        sfd_mom m{0, 0, 0};
+        if (cnt > 0) {
+            const sfd_st n = (sfd_st)cnt, mu = (sfd_st)s1 / n;
+            m = sfd_mom{n, (sfd_st)K + mu, fmax((sfd_st)s2 - (sfd_st)s1 * mu, (sfd_st)0)};
+        }
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            sfd_mom o;
+            o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
+            o.mean = __shfl_xor_sync(0xffffffffu, m.mean, off);
+            o.m2 = __shfl_xor_sync(0xffffffffu, m.m2, off);
+            m = (lane & off) ? sfd_merge(o, m) : sfd_merge(m, o);
+        }
+        if (lane == 0) {
+            sfd_st *w = S.red + warp * 3;
+            w[0] = m.n; w[1] = m.mean; w[2] = m.m2;
+        }
+        __syncthreads();
+        if (threadIdx.x < NZ) {
+            const int ff = threadIdx.x;
+            sfd_mom mm{0, 0, 0};
+            for (int w = 0; w < 4; ++w) {
+                const sfd_st *q = S.red + (ff * 4 + w) * 3;
+                mm = sfd_merge(mm, sfd_mom{q[0], q[1], q[2]});
+            }
+            const sfd_st sd = mm.n > SFD_DDOF ? sqrt(mm.m2 / (mm.n - SFD_DDOF)) : (sfd_st)0;
+            S.thr[ff] = (float)fma((sfd_st)a.k, sd, mm.mean);
+            if (a.mean != nullptr) {
+                const i64 o = (i64)a.fidx[IDX][ff] * a.nwin + S.wid;
+                a.mean[o] = (float)mm.mean * inv;
+                a.stdv[o] = (float)sd * inv;
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int base = 0; base < SFD_WX; base += 32) {
+                const int q = base + lane;
+                bool hot = false;
+                if (q < S.npl)
+#pragma unroll
+                    for (int ff = 0; ff < NZ; ++ff) hot |= S.pmax[q * SFD_NZF + ff] > S.thr[ff];
+                const u32 bits = __ballot_sync(0xffffffffu, hot);
+                if (lane == 0) S.flags[base >> 5] = bits;
+            }
+        }
+        __syncthreads();
+        fl0 = S.flags[0];
+        fl1 = SFD_WX > 32 ? S.flags[1] : 0u;
+        if (mine) T = S.thr[f];
+        pass = 1;
+        sft_start<IDX, RY>(mp, S, next_group(-1));
+    }
+}
+
+__device__ __forceinline__ bool sft_window(const sf_dargs &a, const sfd_taps &t, const sft_maps &mp,
+                                           const sft_tiles &bt, sft_state &S, int wid)
+{
+    S.wid = wid;
+    S.limit = (unsigned long long)a.wait_ns;
+    const int wz = wid % a.nwz, wy = (wid / a.nwz) % a.nwy, wx = wid / (a.nwz * a.nwy);
+    S.x0 = a.xorg + (i64)wx * SFD_WX;
+    S.y0 = (i64)wy * SFD_WY;
+    S.z0 = (i64)wz * SFD_WZ;
+    const i64 left = a.nx - S.x0;
+    S.npl = left < SFD_WX ? (int)left : SFD_WX;
+    for (int i = threadIdx.x; i < SFD_WX * SFD_WY * 2; i += SFD_THREADS) S.mask[i] = 0u;
+    __syncthreads();
+#define SFT_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3) \
+    if (!S.dead) sft_input<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(a, t, mp, bt, S);
+    SFD_SOURCES(SFT_RUN)
+#undef SFT_RUN
+    if (S.dead) return false;
+    __syncthreads();
+    /* mask words: thread (row, word) of every plane */
+    const int row = threadIdx.x >> 1, wd = threadIdx.x & 1;
+    if (row < SFD_WY && S.y0 + row < a.ny) {
+        const i64 gw = (S.z0 >> 5) + wd;
+        if (gw < a.nw32)
+            for (int p = 0; p < S.npl; ++p)
+                a.mask[((S.x0 - a.xorg + p) * a.ny + S.y0 + row) * a.nw32 + gw] = S.mask[(p * SFD_WY + row) * 2 + wd];
+    }
+    return true;
+}
+
+extern "C" __global__ void __launch_bounds__(SFD_THREADS, 2)
+sf_window_tc(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_taps t,
+             const __grid_constant__ sft_maps mp, const __grid_constant__ sft_tiles bt)
+{
+    extern __shared__ __align__(1024) unsigned char sft_raw[];
+    __shared__ u32 s_tmem;
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<unsigned long long>(sft_raw) + 1023ull) & ~1023ull);
+    sft_state S;
+    S.A = sm + SFT_OFF_A;
+    S.T = sm + SFT_OFF_T;
+    S.slab = sm + SFT_OFF_SLAB;
+    S.pmax = reinterpret_cast<float *>(sm + SFT_OFF_PMAX);
+    S.mask = reinterpret_cast<u32 *>(sm + SFT_OFF_MASK);
+    S.red = reinterpret_cast<sfd_st *>(sm + SFT_OFF_RED);
+    S.thr = reinterpret_cast<float *>(sm + SFT_OFF_THR);
+    S.flags = reinterpret_cast<u32 *>(sm + SFT_OFF_FLAGS);
+    S.bar_s = sf_smem_addr(sm + SFT_OFF_MBAR);
+    S.bar_a = S.bar_s + 16u;
+    S.bar_z = S.bar_s + 24u;
+    S.bar_y = S.bar_s + 40u;
+    S.ph_s = S.ph_a = S.ph_z = S.ph_y = 0u;
+    S.pend = 0u;
+    S.it = S.ity = 0;
+    S.dead = false;
+    S.limit = (unsigned long long)a.wait_ns;
+    S.err = a.err;
+    /* the tap tiles, already in the swizzled layout */
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(&bt);
+        uint4 *dst = reinterpret_cast<uint4 *>(S.T);
+        for (int i = threadIdx.x; i < SFT_TILE_BYTES / 16; i += SFD_THREADS) dst[i] = src[i];
+    }
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 7; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar_s + 8u * (u32)b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sf_smem_addr(&s_tmem)),
+                     "r"((u32)SFT_TM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    S.tmem = s_tmem;
+    const bool ok = sft_window(a, t, mp, bt, S, a.wid0 + (int)blockIdx.x);
+    if (!ok && threadIdx.x == 0) {
+        /* a bounded wait expired: report it, then give the copies and MMAs in
+         * flight a bounded time to land before the buffers go away */
+        atomicOr(a.err, 1);
+        for (int b = 0; b < 2; ++b) {
+            if ((S.pend >> b) & 1u) sfw_wait(S.bar_s + 8u * (u32)b, (S.ph_s >> b) & 1u, S.limit);
+            if ((S.pend >> (3 + b)) & 1u) sfw_wait(S.bar_z + 8u * (u32)b, (S.ph_z >> b) & 1u, S.limit);
+            if ((S.pend >> (5 + b)) & 1u) sfw_wait(S.bar_y + 8u * (u32)b, (S.ph_y >> b) & 1u, S.limit);
+        }
+        if ((S.pend >> 2) & 1u) sfw_wait(S.bar_a, S.ph_a & 1u, S.limit);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(S.tmem), "r"((u32)SFT_TM_COLS)
+                     : "memory");
+}
+#endif /* SF_KERNEL_TC */
+
 /* ======================================================================= */
 #ifdef SF_KERNEL_FILTER
 /* one CTA per (x, y tile, z tile): y and z passes of a single filter */

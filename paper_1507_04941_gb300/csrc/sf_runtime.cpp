@@ -23,6 +23,8 @@
 
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <nvrtc.h>
 
 #include <algorithm>
@@ -260,6 +262,11 @@ struct sf_ctx {
     Launch dlaunch;
     std::vector<float> dtaps;
     std::vector<CUtensorMap> dmaps;   /* per input; the cube's is re-encoded per call */
+    /* 16-bit storage: the window kernel with the spectral filters on the tensor cores */
+    bool use_tc = false;
+    Launch tclaunch;
+    std::vector<unsigned char> tcb;   /* swizzled Toeplitz tap tiles (parameter block) */
+    std::vector<CUtensorMap> tcmaps;  /* per input: swizzled A boxes (sigma_xy = 0) or slabs */
     int *err_flag = nullptr;          /* device flag set by kernels whose bounded wait expired */
     long long wait_ns = 2000000000LL; /* limit of the kernels' bounded waits */
     int stall_extra = 0;              /* test hook: x items each window waits for beyond its unit's */
@@ -787,6 +794,178 @@ bool tma_usable(const sf_ctx *c, const WindowPlan &wp, long long nz)
            tensor_map_encoder() != nullptr && env_int("SF_NO_TMA", 0) == 0;
 }
 
+/* A tiled 3D map of a 16-bit cube with the 128-byte swizzle and box {64,
+ * rows, planes}: four planes of a window's rows straight into the K-major
+ * layout the tensor-core MMAs read (rows = WY, planes = 4), or one plane's
+ * slab of KY rows, read as an MN-major operand (rows = KY, planes = 1). */
+bool encode_map_tc(const sf_ctx *c, const void *base, int rows, int planes, CUtensorMap *out)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const CUtensorMapDataType dt = c->cfg.storage == SF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)c->cfg.nz, (cuuint64_t)c->cfg.ny, (cuuint64_t)c->cfg.nx};
+    const cuuint64_t strides[2] = {(cuuint64_t)(c->cfg.nz * (long long)c->ebytes),
+                                   (cuuint64_t)(c->cfg.ny * c->cfg.nz * (long long)c->ebytes)};
+    const cuuint32_t box[3] = {64u, (cuuint32_t)rows, (cuuint32_t)planes};
+    const cuuint32_t es[3] = {1u, 1u, 1u};
+    return enc(out, dt, 3, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+/* byte offset of element (row, k) of a K-major tile with 128-byte rows and the
+ * 128-byte swizzle (16-byte chunk index XOR row % 8, 8-row atoms of 1 KB) */
+size_t sw128_offset(int row, int kbyte)
+{
+    return (size_t)(row / 8) * 1024 + (size_t)(row % 8) * 128 + (size_t)(((kbyte / 16) ^ (row % 8)) & 7) * 16 +
+           (size_t)(kbyte % 16);
+}
+
+/* v as two 16-bit parts of the storage type, v ~ hi + lo */
+void split16(const sf_ctx *c, float v, uint16_t *hi, uint16_t *lo)
+{
+    if (c->cfg.storage == SF_BF16) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+        std::memcpy(hi, &h, 2);
+        std::memcpy(lo, &l, 2);
+    } else {
+        const __half h = __float2half_rn(v);
+        const __half l = __float2half_rn(v - __half2float(h));
+        std::memcpy(hi, &h, 2);
+        std::memcpy(lo, &l, 2);
+    }
+}
+
+/* The window kernel with the y and z filters on the tensor cores, for 16-bit
+ * storage: window 32 x 32 x 64, at most two spectral filters per input, the
+ * z radius with its halo within the 64-column Toeplitz tile, y radius <= 16,
+ * rows TMA-able.  Leaves c->use_tc false when the shape does not qualify. */
+sf_status plan_detect_tc(sf_ctx *c)
+{
+    const sf_config &g = c->cfg;
+    c->use_tc = false;
+    if (c->ebytes != 2 || g.wy != 32 || g.wz != 64 || g.wx > 64 || g.nz % 8 != 0 ||
+        tensor_map_encoder() == nullptr)
+        return SF_OK;
+    WindowPlan wp;
+    if (!make_window_plan(c, 8, 2, copy_chunk(c->ebytes, g.nz), true, wp)) return SF_OK;
+    if (wp.nzf > 2 || wp.sh.HZ + wp.rzm > 48 || wp.rym > 16 || !tma_usable(c, wp, g.nz)) return SF_OK;
+    const int nsrc = (int)wp.srcs.size();
+    const int HZ = wp.sh.HZ;
+    auto ky_of = [&](int ry) { return (g.wy + 2 * ry + 15) / 16 * 16; };
+    const int kym = ky_of(wp.rym);
+    /* tap tiles: the z tiles of the distinct spectral filters, a y tile per
+     * y-filtered input; zt / yt index them */
+    std::vector<std::vector<float>> zkeys;
+    std::vector<int> zt((size_t)nsrc * wp.nzf, 0), yt(nsrc, -1);
+    int nyt = 0;
+    for (int i = 0; i < nsrc; ++i) {
+        for (size_t q = 0; q < wp.srcs[i].filters.size(); ++q) {
+            const Filt &f = c->filt[wp.srcs[i].filters[q]];
+            std::vector<float> key(f.gz.begin(), f.gz.end());
+            int id = -1;
+            for (size_t u = 0; u < zkeys.size(); ++u)
+                if (zkeys[u] == key) id = (int)u;
+            if (id < 0) {
+                id = (int)zkeys.size();
+                zkeys.push_back(key);
+            }
+            zt[(size_t)i * wp.nzf + q] = id;
+        }
+        if (wp.srcs[i].ry > 0) yt[i] = nyt++;
+    }
+    const int nzt = (int)zkeys.size();
+    const size_t zbytes = (size_t)nzt * 2 * 2048, ybytes = (size_t)std::max(1, nyt) * 2 * 4096;
+    const size_t tile_bytes = zbytes + ybytes;
+    /* the parameter block: tiles, then zt[nsrc][nzf] and yt[nsrc] as int32 */
+    c->tcb.assign(tile_bytes + sizeof(int32_t) * ((size_t)nsrc * wp.nzf + nsrc), 0);
+    const float scale = 1024.f;   /* 2^10: the z taps' low parts stay normal */
+    for (int u = 0; u < nzt; ++u) {
+        const std::vector<float> &gz = zkeys[u];
+        const int rz = ((int)gz.size() - 1) / 2;
+        for (int n = 0; n < 16; ++n)
+            for (int k = 0; k < 64; ++k) {
+                const int o = k - n - HZ;
+                const float v = (o >= -rz && o <= rz) ? gz[rz + o] * scale : 0.f;
+                uint16_t hi, lo;
+                split16(c, v, &hi, &lo);
+                std::memcpy(&c->tcb[((size_t)u * 2 + 0) * 2048 + sw128_offset(n, 2 * k)], &hi, 2);
+                std::memcpy(&c->tcb[((size_t)u * 2 + 1) * 2048 + sw128_offset(n, 2 * k)], &lo, 2);
+            }
+    }
+    for (int i = 0; i < nsrc; ++i) {
+        if (yt[i] < 0) continue;
+        const Filt &f = c->filt[wp.srcs[i].filters[0]];
+        const int ry = wp.srcs[i].ry;
+        for (int n = 0; n < 32; ++n)
+            for (int k = 0; k < 64; ++k) {
+                const int o = k - n - ry;
+                const float v = (o >= -ry && o <= ry) ? f.gxy[f.rxy + o] : 0.f;
+                uint16_t hi, lo;
+                split16(c, v, &hi, &lo);
+                std::memcpy(&c->tcb[zbytes + ((size_t)yt[i] * 2 + 0) * 4096 + sw128_offset(n, 2 * k)], &hi, 2);
+                std::memcpy(&c->tcb[zbytes + ((size_t)yt[i] * 2 + 1) * 4096 + sw128_offset(n, 2 * k)], &lo, 2);
+            }
+    }
+    {
+        int32_t *ix = reinterpret_cast<int32_t *>(&c->tcb[tile_bytes]);
+        for (size_t j = 0; j < zt.size(); ++j) ix[j] = zt[j];
+        for (int i = 0; i < nsrc; ++i) ix[zt.size() + i] = yt[i];
+    }
+    /* shared memory (from a 1024-aligned base) */
+    size_t off = 0;
+    const size_t offA = off;
+    off += 2 * 128 * 128;
+    const size_t offT = off;
+    off += align_up(tile_bytes, 1024);
+    const size_t offS = off;
+    off += (size_t)2 * 2 * kym * 128;
+    const size_t offP = off;
+    off += align_up((size_t)g.wx * wp.nzf * 4, 16);
+    const size_t offM = off;
+    off += align_up((size_t)g.wx * g.wy * 2 * 4, 16);
+    const size_t offR = off;
+    off += align_up((size_t)8 * 3 * (g.stats_fp64 ? 8 : 4), 16);
+    const size_t offTh = off;
+    off += 16;
+    const size_t offF = off;
+    off += 16;
+    const size_t offMB = off;
+    off += 64;
+    const size_t smem = off + 1024;
+    if (smem > kSmemLimit) return SF_OK;
+    std::string p = "#define SF_KERNEL_TC 1\n" + wp.prelude + "#define SFD_TMA 1\n";
+    p += "#define SFT_OFF_A " + std::to_string(offA) + "\n";
+    p += "#define SFT_OFF_T " + std::to_string(offT) + "\n";
+    p += "#define SFT_OFF_SLAB " + std::to_string(offS) + "\n";
+    p += "#define SFT_OFF_PMAX " + std::to_string(offP) + "\n";
+    p += "#define SFT_OFF_MASK " + std::to_string(offM) + "\n";
+    p += "#define SFT_OFF_RED " + std::to_string(offR) + "\n";
+    p += "#define SFT_OFF_THR " + std::to_string(offTh) + "\n";
+    p += "#define SFT_OFF_FLAGS " + std::to_string(offF) + "\n";
+    p += "#define SFT_OFF_MBAR " + std::to_string(offMB) + "\n";
+    p += "#define SFT_NZT " + std::to_string(nzt) + "\n";
+    p += "#define SFT_NYT " + std::to_string(nyt) + "\n";
+    p += std::string("#define SFT_BF16 ") + (g.storage == SF_BF16 ? "1" : "0") + "\n";
+    std::string err;
+    sf_status s = jit_kernel(p, "sf_window_tc", c->device, &c->tclaunch.kernel, err);
+    if (s != SF_OK) return fail(c, s, "tensor-core window kernel: %s", err.c_str());
+    c->tclaunch.smem = smem;
+    if ((s = set_smem(c, c->tclaunch.kernel, smem)) != SF_OK) return s;
+    c->tclaunch.block = dim3(256);
+    c->tclaunch.grid = dim3((unsigned)c->nwin);
+    c->tcmaps.assign(nsrc, CUtensorMap{});
+    for (int i = 0; i < nsrc; ++i)
+        if (wp.srcs[i].slot >= 0 &&
+            !encode_map_tc(c, (const char *)c->scratch + (size_t)wp.srcs[i].slot * c->cube_bytes,
+                           ky_of(wp.srcs[i].ry), 1, &c->tcmaps[i]))
+            return fail(c, SF_ECUDA, "tensor map encoding failed");
+    c->use_tc = true;
+    return SF_OK;
+}
+
 /* The fused window kernel: one CTA per statistics window (see sf_kernels.cuh). */
 sf_status plan_detect(sf_ctx *c)
 {
@@ -828,6 +1007,7 @@ sf_status plan_detect(sf_ctx *c)
                             wp.srcs[i].ry, &c->dmaps[i]))
                 return fail(c, SF_ECUDA, "tensor map encoding failed");
     c->fused = true;
+    if (env_int("SF_NO_TC", 0) == 0 && (s = plan_detect_tc(c)) != SF_OK) return s;
     return SF_OK;
 }
 
@@ -1178,6 +1358,16 @@ sf_status launch_windows(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float 
     da.wait_ns = c->wait_ns;
     da.xorg = xorg;
     da.wid0 = w0;
+    if (c->use_tc) {
+        /* the cube's own A boxes, swizzled, per call */
+        for (size_t i = 0; i < c->dsrc.size(); ++i)
+            if (c->dsrc[i].slot < 0 && !encode_map_tc(c, d_cube, c->cfg.wy, 4, &c->tcmaps[i]))
+                return fail(c, SF_ECUDA, "tensor map encoding of the cube failed");
+        Launch L = c->tclaunch;
+        L.grid = dim3((unsigned)(w1 - w0));
+        void *args[] = {&da, c->dtaps.data(), c->tcmaps.data(), c->tcb.data()};
+        return launch(c, L, args, st, "tensor-core window kernel launch");
+    }
     Launch L = c->dlaunch;
     L.grid = dim3((unsigned)(w1 - w0));
     void *args[] = {&da, c->dtaps.data(), c->dmaps.data()};
@@ -2446,7 +2636,7 @@ sf_status sf_synchronize(sf_ctx *c, void *stream)
     if (flag) {
         cudaMemset(c->err_flag, 0, sizeof(int));
         return fail(c, SF_ETIMEOUT, "a kernel's bounded wait (shared-memory loads, or another CTA's "
-                                    "x pass) expired");
+                                    "x pass) expired (flag 0x%x)", (unsigned)flag);
     }
     return SF_OK;
 }
