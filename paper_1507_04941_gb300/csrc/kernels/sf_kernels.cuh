@@ -1916,7 +1916,7 @@ __device__ __forceinline__ bool sft_window(const sf_dargs &a, const sfd_taps &t,
 
 extern "C" __global__ void __launch_bounds__(SFD_THREADS, 2)
 sf_window_tc(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_taps t,
-             const __grid_constant__ sft_maps mp, const __grid_constant__ sft_tiles bt)
+             const __grid_constant__ sft_maps mp, const __grid_constant__ sft_tiles bt, const uint4 *__restrict__ tct)
 {
     extern __shared__ __align__(1024) unsigned char sft_raw[];
     __shared__ u32 s_tmem;
@@ -1943,9 +1943,9 @@ sf_window_tc(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_tap
     S.err = a.err;
     /* the tap tiles, already in the swizzled layout */
     {
-        const uint4 *src = reinterpret_cast<const uint4 *>(&bt);
+        /* from the device copy: the same bytes as bt's tiles */
         uint4 *dst = reinterpret_cast<uint4 *>(S.T);
-        for (int i = threadIdx.x; i < SFT_TILE_BYTES / 16; i += SFD_THREADS) dst[i] = src[i];
+        for (int i = threadIdx.x; i < SFT_TILE_BYTES / 16; i += SFD_THREADS) dst[i] = __ldg(tct + i);
     }
     if (threadIdx.x == 0) {
         for (int b = 0; b < 7; ++b)

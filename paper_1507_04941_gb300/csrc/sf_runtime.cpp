@@ -266,6 +266,7 @@ struct sf_ctx {
     bool use_tc = false;
     Launch tclaunch;
     std::vector<unsigned char> tcb;   /* swizzled Toeplitz tap tiles (parameter block) */
+    void *d_tct = nullptr;            /* the same tiles in device memory: the kernel's copy source */
     std::vector<CUtensorMap> tcmaps;  /* per input: swizzled A boxes (sigma_xy = 0) or slabs */
     int *err_flag = nullptr;          /* device flag set by kernels whose bounded wait expired */
     long long wait_ns = 2000000000LL; /* limit of the kernels' bounded waits */
@@ -914,6 +915,14 @@ sf_status plan_detect_tc(sf_ctx *c)
         for (size_t j = 0; j < zt.size(); ++j) ix[j] = zt[j];
         for (int i = 0; i < nsrc; ++i) ix[zt.size() + i] = yt[i];
     }
+    /* every CTA stages the tiles from device memory (coalesced, through L2):
+     * read from the parameter block their per-thread addresses would
+     * serialise in the constant cache */
+    cudaFree(c->d_tct);
+    c->d_tct = nullptr;
+    if (cudaMalloc(&c->d_tct, tile_bytes) != cudaSuccess ||
+        cudaMemcpy(c->d_tct, c->tcb.data(), tile_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(c, SF_ECUDA, "tap tile upload failed");
     /* shared memory (from a 1024-aligned base) */
     size_t off = 0;
     const size_t offA = off;
@@ -1365,7 +1374,7 @@ sf_status launch_windows(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float 
                 return fail(c, SF_ECUDA, "tensor map encoding of the cube failed");
         Launch L = c->tclaunch;
         L.grid = dim3((unsigned)(w1 - w0));
-        void *args[] = {&da, c->dtaps.data(), c->tcmaps.data(), c->tcb.data()};
+        void *args[] = {&da, c->dtaps.data(), c->tcmaps.data(), c->tcb.data(), &c->d_tct};
         return launch(c, L, args, st, "tensor-core window kernel launch");
     }
     Launch L = c->dlaunch;
@@ -1740,6 +1749,7 @@ sf_status sf_destroy(sf_ctx *c)
     cudaFree(c->host_cube);
     cudaFree(c->host_mask);
     cudaFree(c->err_flag);
+    cudaFree(c->d_tct);
     for (cudaStream_t x : c->hcomp)
         if (x) cudaStreamDestroy(x);
     cudaFree(c->lscratch);
