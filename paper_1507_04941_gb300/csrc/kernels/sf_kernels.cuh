@@ -1461,7 +1461,7 @@ struct sft_state {
     float *thr;            /* [NZF] */
     u32 *flags;            /* [2] */
     u32 bar_s;             /* slab copies (2), 8 bytes apart */
-    u32 bar_a;             /* A-tile copy */
+    u32 bar_a;             /* A-tile copies (two buffers: the A tile, and the slab region) */
     u32 bar_z;             /* z-MMA commits (2) */
     u32 bar_y;             /* y-MMA commits (2) */
     u32 ph_s, ph_a, ph_z, ph_y;   /* parity of the next completion, bit per barrier */
@@ -1509,12 +1509,17 @@ __device__ __forceinline__ void sft_load_slab(const sft_maps &mp, sft_state &S, 
     }
 }
 
-/* A tile of group g of a sigma_xy = 0 input: two swizzled boxes {64, 32, 4} */
+/* the two atoms of A buffer ab: the A tile (0), or the slab region, idle
+ * while a sigma_xy = 0 input runs (1) */
+__device__ __forceinline__ unsigned char *sft_abuf(const sft_state &S, int ab) { return ab ? S.slab : S.A; }
+
+/* A tile of group g of a sigma_xy = 0 input into A buffer ab: two swizzled
+ * boxes {64, 32, 4} */
 template <int IDX>
-__device__ __forceinline__ void sft_load_a(const sft_maps &mp, sft_state &S, int g)
+__device__ __forceinline__ void sft_load_a(const sft_maps &mp, sft_state &S, int g, int ab)
 {
     if (threadIdx.x != 0) return;
-    const u32 bar = S.bar_a;
+    const u32 bar = S.bar_a + 8u * (u32)ab;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((u32)(2 * SFT_ATOM))
                  : "memory");
@@ -1523,7 +1528,7 @@ __device__ __forceinline__ void sft_load_a(const sft_maps &mp, sft_state &S, int
     for (int a = 0; a < 2; ++a) {
         const int cz = (int)(S.z0 - SFD_HZ) + 64 * a;
         asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                     " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sf_smem_addr(S.A + a * SFT_ATOM)),
+                     " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(sf_smem_addr(sft_abuf(S, ab) + a * SFT_ATOM)),
                      "l"(reinterpret_cast<unsigned long long>(&mp.m[IDX])), "r"(cz), "r"(cy), "r"(cx), "r"(bar)
                      : "memory");
     }
@@ -1557,9 +1562,9 @@ __device__ __forceinline__ void sft_mma_y(const sft_state &S, const sft_tiles &b
  * 16-output tile j, the K-slices j + s_lo .. j + s_hi against the filter's
  * Toeplitz tile, hi and lo parts */
 template <int SI, int NZ, int RZ0, int RZ1>
-__device__ __forceinline__ void sft_mma_z(const sft_state &S, const sft_tiles &bt, int buf)
+__device__ __forceinline__ void sft_mma_z(const sft_state &S, const sft_tiles &bt, int buf, const unsigned char *A)
 {
-    const u32 a0 = sf_smem_addr(S.A);
+    const u32 a0 = sf_smem_addr(A);
 #pragma unroll
     for (int f = 0; f < NZ; ++f) {
         const int r = f == 0 ? RZ0 : RZ1;
@@ -1607,7 +1612,7 @@ __device__ __forceinline__ void sft_ld16(u32 addr, float (&v)[16])
 __device__ __forceinline__ bool sft_convert(sft_state &S, int slot, int yb)
 {
     const bool ok = sft_wait(S, S.bar_y, S.ph_y, yb, 4);
-    S.pend &= ~(32u << yb);
+    S.pend &= ~(64u << yb);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int z = 32 * (warp & 3) + lane, half = warp >> 2;
@@ -1634,7 +1639,7 @@ __device__ __forceinline__ void sft_start(const sft_maps &mp, sft_state &S, int 
         sft_load_slab<IDX, RY>(mp, S, g * SFT_PLANES, b);
         S.pend |= 1u << b;
     } else {
-        sft_load_a<IDX>(mp, S, g);
+        sft_load_a<IDX>(mp, S, g, 0);
         S.pend |= 4u;
     }
 }
@@ -1673,7 +1678,7 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
     /* read the z accumulator of group g (buffer b) once its MMAs completed */
     auto epilogue = [&](int g, int b) {
         const bool ok = sft_wait(S, S.bar_z, S.ph_z, b, 3);
-        S.pend &= ~(8u << b);
+        S.pend &= ~(16u << b);
         if (!ok) S.dead = true;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int p = g * SFT_PLANES + slot;
@@ -1734,15 +1739,15 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
         }
     };
     /* the z MMAs of group g once its A tile is complete */
-    auto issue_z = [&](int g, int buf) {
+    auto issue_z = [&](int g, int buf, int ab) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            sft_mma_z<IDX, NZ, RZ0, RZ1>(S, bt, buf);
+            sft_mma_z<IDX, NZ, RZ0, RZ1>(S, bt, buf, sft_abuf(S, ab));
         }
-        S.pend |= 8u << buf;
+        S.pend |= 16u << buf;
         (void)g;
     };
 
@@ -1751,27 +1756,35 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
         int pend_g = -1, pend_b = 0;
         int gi = next_group(-1);
         if constexpr (RY == 0) {
-            int nbuf = 0;
+            /* A tiles double-buffered: the copy of group gn lands while the
+             * z MMAs of group gi run and the previous group is read out */
+            int nbuf = 0, ab = 0;
             while (gi >= 0) {
                 const int gn = next_group(gi);
-                const bool ok = sft_wait(S, S.bar_a, S.ph_a, 0, 1);
-                S.pend &= ~4u;
-                if (__syncthreads_or(!ok)) { S.dead = true; return; }
+                const bool ok = sft_wait(S, S.bar_a, S.ph_a, ab, 1);
+                S.pend &= ~(4u << ab);
+                if (__syncthreads_or(!ok || S.dead)) { S.dead = true; return; }
                 const int cur = nbuf;
                 nbuf ^= 1;
-                issue_z(gi, cur);
+                issue_z(gi, cur, ab);
+                if (gn >= 0 && threadIdx.x == 0) {
+                    /* the other A buffer was read by the previous group's z MMAs:
+                     * refill it once they completed (a peek: the epilogue waits
+                     * on the same completion) */
+                    bool ok2 = true;
+                    if (pend_g >= 0) ok2 = sfw_wait(S.bar_z + 8u * (u32)pend_b, (S.ph_z >> pend_b) & 1u, S.limit);
+                    if (!ok2) {
+                        atomicOr(S.err, 1 | (1 << 3));
+                        S.dead = true;
+                    } else {
+                        sft_load_a<IDX>(mp, S, gn, ab ^ 1);
+                        S.pend |= 4u << (ab ^ 1);
+                    }
+                }
                 if (pend_g >= 0) epilogue(pend_g, pend_b);
                 pend_g = gi;
                 pend_b = cur;
-                if (gn >= 0) {
-                    /* the next A tile may only land once these MMAs read this one
-                     * (a peek: the epilogue waits on the same completion) */
-                    const bool ok2 = sfw_wait(S.bar_z + 8u * (u32)cur, (S.ph_z >> cur) & 1u, S.limit);
-                    if (!ok2) atomicOr(S.err, 1 | (1 << 3));
-                    if (__syncthreads_or(!ok2)) { S.dead = true; return; }
-                    sft_load_a<IDX>(mp, S, gn);
-                    S.pend |= 4u;
-                }
+                ab ^= 1;
                 gi = gn;
             }
         } else {
@@ -1790,7 +1803,7 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         sft_mma_y<RY>(S, bt, IDX, b, yb);
                     }
-                    S.pend |= 32u << yb;
+                    S.pend |= 64u << yb;
                     ++S.ity;
                     ++S.it;
                     /* the previous group's z accumulator, then the previous
@@ -1817,7 +1830,7 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                         make_uint4(0u, 0u, 0u, 0u);
                 }
                 if (__syncthreads_or(S.dead)) { S.dead = true; return; }
-                issue_z(gi, 0);
+                issue_z(gi, 0, 0);
                 pend_g = gi;
                 pend_b = 0;
                 gi = gn;
@@ -1933,8 +1946,8 @@ sf_window_tc(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_tap
     S.flags = reinterpret_cast<u32 *>(sm + SFT_OFF_FLAGS);
     S.bar_s = sf_smem_addr(sm + SFT_OFF_MBAR);
     S.bar_a = S.bar_s + 16u;
-    S.bar_z = S.bar_s + 24u;
-    S.bar_y = S.bar_s + 40u;
+    S.bar_z = S.bar_s + 32u;
+    S.bar_y = S.bar_s + 48u;
     S.ph_s = S.ph_a = S.ph_z = S.ph_y = 0u;
     S.pend = 0u;
     S.it = S.ity = 0;
@@ -1948,7 +1961,7 @@ sf_window_tc(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_tap
         for (int i = threadIdx.x; i < SFT_TILE_BYTES / 16; i += SFD_THREADS) dst[i] = __ldg(tct + i);
     }
     if (threadIdx.x == 0) {
-        for (int b = 0; b < 7; ++b)
+        for (int b = 0; b < 8; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar_s + 8u * (u32)b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1970,10 +1983,10 @@ sf_window_tc(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_tap
         atomicOr(a.err, 1);
         for (int b = 0; b < 2; ++b) {
             if ((S.pend >> b) & 1u) sfw_wait(S.bar_s + 8u * (u32)b, (S.ph_s >> b) & 1u, S.limit);
-            if ((S.pend >> (3 + b)) & 1u) sfw_wait(S.bar_z + 8u * (u32)b, (S.ph_z >> b) & 1u, S.limit);
-            if ((S.pend >> (5 + b)) & 1u) sfw_wait(S.bar_y + 8u * (u32)b, (S.ph_y >> b) & 1u, S.limit);
+            if ((S.pend >> (2 + b)) & 1u) sfw_wait(S.bar_a + 8u * (u32)b, (S.ph_a >> b) & 1u, S.limit);
+            if ((S.pend >> (4 + b)) & 1u) sfw_wait(S.bar_z + 8u * (u32)b, (S.ph_z >> b) & 1u, S.limit);
+            if ((S.pend >> (6 + b)) & 1u) sfw_wait(S.bar_y + 8u * (u32)b, (S.ph_y >> b) & 1u, S.limit);
         }
-        if ((S.pend >> 2) & 1u) sfw_wait(S.bar_a, S.ph_a & 1u, S.limit);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -930,7 +930,11 @@ sf_status plan_detect_tc(sf_ctx *c)
     const size_t offT = off;
     off += align_up(tile_bytes, 1024);
     const size_t offS = off;
-    off += (size_t)2 * 2 * kym * 128;
+    /* two slab buffers; inputs with sigma_xy = 0 use the region as a second
+     * A tile (two 16 KB atoms) */
+    bool any_ry0 = false;
+    for (int i = 0; i < nsrc; ++i) any_ry0 |= wp.srcs[i].ry == 0;
+    off += std::max<size_t>((size_t)2 * 2 * kym * 128, any_ry0 ? 2 * 16384 : 0);
     const size_t offP = off;
     off += align_up((size_t)g.wx * wp.nzf * 4, 16);
     const size_t offM = off;
