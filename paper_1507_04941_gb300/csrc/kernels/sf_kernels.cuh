@@ -1414,6 +1414,7 @@ constexpr int SFT_ATOM = SFT_M * 128;                /* bytes of one 64-column a
 constexpr int SFT_TM_COLS = 256;                     /* z accumulators at 0 and 128; y at 128, 160 */
 constexpr int SFT_KYM = (SFD_WY + 2 * SFD_RYM + 15) / 16 * 16;   /* padded slab rows */
 constexpr int SFT_SLAB_BYTES = 2 * SFT_KYM * 128;    /* one slab buffer: two 64-column atoms */
+constexpr int SFT_NS = 3;                            /* slab buffers: copies two planes ahead */
 static_assert(SFD_WY == 32 && SFD_WZ == 64 && SFD_THREADS == 256, "window 32 x 64, 256 threads");
 static_assert(SFD_NZF <= 2, "at most two spectral filters per input");
 static_assert(SFD_HZ + SFD_RZM <= 48, "band within the 64-column Toeplitz tile");
@@ -1426,7 +1427,8 @@ struct sft_tiles {
     int yt[SFD_NSRC];                                   /* y tile of each input (-1: none) */
 };
 struct sft_maps { sf_tmap m[SFD_NSRC]; };
-constexpr int SFT_TILE_BYTES = (int)(sizeof(((sft_tiles *)0)->z) + sizeof(((sft_tiles *)0)->y));
+constexpr int SFT_ZT_BYTES = (int)sizeof(((sft_tiles *)0)->z);   /* z tiles: resident */
+constexpr int SFT_YT_BYTES = 2 * 4096;                              /* one y tile: staged per input */
 
 __device__ __forceinline__ u32 sft_sw128(u32 row, u32 kbyte)
 {
@@ -1454,22 +1456,23 @@ __host__ __device__ constexpr int sft_ky(int ry) { return (SFD_WY + 2 * ry + 15)
 struct sft_state {
     unsigned char *A;      /* z-filter A tile: 1024-aligned, two 16 KB atoms */
     unsigned char *T;      /* tap tiles (z then y) */
-    unsigned char *slab;   /* y-filter slabs: two buffers of SFT_SLAB_BYTES */
+    unsigned char *slab;   /* y-filter slabs: SFT_NS buffers of SFT_SLAB_BYTES */
     float *pmax;           /* [WX][NZF] */
     u32 *mask;             /* [WX][WY][2] */
     sfd_st *red;           /* [8 warps][3] */
     float *thr;            /* [NZF] */
     u32 *flags;            /* [2] */
-    u32 bar_s;             /* slab copies (2), 8 bytes apart */
+    u32 bar_s;             /* slab copies (SFT_NS), 8 bytes apart */
     u32 bar_a;             /* A-tile copies (two buffers: the A tile, and the slab region) */
     u32 bar_z;             /* z-MMA commits (2) */
     u32 bar_y;             /* y-MMA commits (2) */
     u32 ph_s, ph_a, ph_z, ph_y;   /* parity of the next completion, bit per barrier */
     u32 tmem;              /* accumulator base */
-    u32 pend;              /* completions awaited: bits 0-1 slabs, 2 A tile, 3-4 z, 5-6 y */
+    u32 pend;              /* completions awaited: bits 0-2 slabs, 3-4 A tiles, 5-6 z, 7-8 y */
     i64 x0, y0, z0;
     int npl, wid;
-    int it;                /* slab planes consumed (buffer = it & 1) */
+    int it;                /* slab copies issued (buffer = it % SFT_NS) */
+    int ic;                /* slab planes consumed (buffer = ic % SFT_NS) */
     int ity;               /* y-MMAs issued (accumulator = ity & 1) */
     unsigned long long limit;
     int *err;
@@ -1540,7 +1543,9 @@ __device__ __forceinline__ void sft_mma_y(const sft_state &S, const sft_tiles &b
 {
     constexpr int KY = sft_ky(RY);
     const u32 a0 = sf_smem_addr(S.slab + b * SFT_SLAB_BYTES);
-    const u32 t0 = sf_smem_addr(S.T + sizeof(bt.z) + bt.yt[SI] * 2 * 4096);
+    const u32 t0 = sf_smem_addr(S.T + SFT_ZT_BYTES);   /* this input's y tile, staged at its start */
+    (void)bt;
+    (void)SI;
     const u32 d = S.tmem + 128u + (u32)(yb * 32);
     u32 acc = 0u;
 #pragma unroll
@@ -1612,7 +1617,7 @@ __device__ __forceinline__ void sft_ld16(u32 addr, float (&v)[16])
 __device__ __forceinline__ bool sft_convert(sft_state &S, int slot, int yb)
 {
     const bool ok = sft_wait(S, S.bar_y, S.ph_y, yb, 4);
-    S.pend &= ~(64u << yb);
+    S.pend &= ~(128u << yb);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int z = 32 * (warp & 3) + lane, half = warp >> 2;
@@ -1633,20 +1638,15 @@ __device__ __forceinline__ bool sft_convert(sft_state &S, int slot, int yb)
 template <int IDX, int RY>
 __device__ __forceinline__ void sft_start(const sft_maps &mp, sft_state &S, int g)
 {
-    if (g < 0) return;
-    if constexpr (RY > 0) {
-        const int b = S.it & 1;
-        sft_load_slab<IDX, RY>(mp, S, g * SFT_PLANES, b);
-        S.pend |= 1u << b;
-    } else {
-        sft_load_a<IDX>(mp, S, g, 0);
-        S.pend |= 4u;
-    }
+    /* the slab copies of a y-filtered input start inside its plane loop */
+    if (g < 0 || RY > 0) return;
+    sft_load_a<IDX>(mp, S, g, 0);
+    S.pend |= 8u;
 }
 
 template <int IDX, int RY, int NZ, int RZ0, int RZ1, int RZ2, int RZ3>
 __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, const sft_maps &mp,
-                                          const sft_tiles &bt, sft_state &S)
+                                          const sft_tiles &bt, const uint4 *__restrict__ tct, sft_state &S)
 {
     static_assert(NZ <= 2, "two spectral filters per input");
     (void)t;
@@ -1665,6 +1665,15 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
     float T = 0.f;
     u32 fl0 = 0u, fl1 = 0u;
     int pass = 0;
+    if constexpr (RY > 0) {
+        /* this input's y tile (hi and lo parts) into the y-tile slot: every
+         * y MMA of the previous input has completed (its planes were read out) */
+        const uint4 *src = tct + (SFT_ZT_BYTES + bt.yt[IDX] * SFT_YT_BYTES) / 16;
+        uint4 *dst = reinterpret_cast<uint4 *>(S.T + SFT_ZT_BYTES);
+        for (int i = threadIdx.x; i < SFT_YT_BYTES / 16; i += SFD_THREADS) dst[i] = __ldg(src + i);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
 
     auto next_group = [&](int after) -> int {
         for (int g = after + 1; g < ngr; ++g) {
@@ -1678,7 +1687,7 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
     /* read the z accumulator of group g (buffer b) once its MMAs completed */
     auto epilogue = [&](int g, int b) {
         const bool ok = sft_wait(S, S.bar_z, S.ph_z, b, 3);
-        S.pend &= ~(16u << b);
+        S.pend &= ~(32u << b);
         if (!ok) S.dead = true;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int p = g * SFT_PLANES + slot;
@@ -1747,7 +1756,7 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             sft_mma_z<IDX, NZ, RZ0, RZ1>(S, bt, buf, sft_abuf(S, ab));
         }
-        S.pend |= 16u << buf;
+        S.pend |= 32u << buf;
         (void)g;
     };
 
@@ -1762,7 +1771,7 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
             while (gi >= 0) {
                 const int gn = next_group(gi);
                 const bool ok = sft_wait(S, S.bar_a, S.ph_a, ab, 1);
-                S.pend &= ~(4u << ab);
+                S.pend &= ~(8u << ab);
                 if (__syncthreads_or(!ok || S.dead)) { S.dead = true; return; }
                 const int cur = nbuf;
                 nbuf ^= 1;
@@ -1778,7 +1787,7 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                         S.dead = true;
                     } else {
                         sft_load_a<IDX>(mp, S, gn, ab ^ 1);
-                        S.pend |= 4u << (ab ^ 1);
+                        S.pend |= 8u << (ab ^ 1);
                     }
                 }
                 if (pend_g >= 0) epilogue(pend_g, pend_b);
@@ -1788,13 +1797,31 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                 gi = gn;
             }
         } else {
+            /* slab copies run two planes ahead through SFT_NS buffers: lp is
+             * the next plane of this pass to copy */
+            int lp = gi >= 0 ? gi * SFT_PLANES : -1;
+            auto load_next = [&]() {
+                if (lp < 0) return;
+                const int b = S.it % SFT_NS;
+                sft_load_slab<IDX, RY>(mp, S, lp, b);
+                S.pend |= 1u << b;
+                ++S.it;
+                if ((lp + 1) % SFT_PLANES != 0 && lp + 1 < S.npl) {
+                    ++lp;
+                } else {
+                    const int g2 = next_group(lp / SFT_PLANES);
+                    lp = g2 >= 0 ? g2 * SFT_PLANES : -1;
+                }
+            };
+            load_next();
+            load_next();
             while (gi >= 0) {
                 const int gn = next_group(gi);
                 const int p0 = gi * SFT_PLANES;
                 const int np = min(SFT_PLANES, S.npl - p0);
                 int yprev = -1;
                 for (int i = 0; i < np; ++i) {
-                    const int b = S.it & 1;
+                    const int b = S.ic % SFT_NS;
                     const bool ok = sft_wait(S, S.bar_s, S.ph_s, b, 2);
                     S.pend &= ~(1u << b);
                     if (__syncthreads_or(!ok)) { S.dead = true; return; }
@@ -1803,9 +1830,9 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         sft_mma_y<RY>(S, bt, IDX, b, yb);
                     }
-                    S.pend |= 64u << yb;
+                    S.pend |= 128u << yb;
                     ++S.ity;
-                    ++S.it;
+                    ++S.ic;
                     /* the previous group's z accumulator, then the previous
                      * plane into the A tile (its z MMAs are complete by then) */
                     if (i == 0 && pend_g >= 0) {
@@ -1814,12 +1841,9 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                     }
                     if (yprev >= 0 && !sft_convert(S, i - 1, yprev)) S.dead = true;
                     yprev = yb;
-                    /* the other slab buffer is free once the plane before was filtered */
-                    const int pn = i + 1 < np ? p0 + i + 1 : (gn >= 0 ? gn * SFT_PLANES : -1);
-                    if (pn >= 0) {
-                        sft_load_slab<IDX, RY>(mp, S, pn, b ^ 1);
-                        S.pend |= 1u << (b ^ 1);
-                    }
+                    /* the buffer of the plane before is free: its y MMAs completed
+                     * (converted above, or at the end of the previous group) */
+                    load_next();
                 }
                 if (!sft_convert(S, np - 1, yprev)) S.dead = true;
                 /* planes past the window's end: zero rows (excluded from every sum) */
@@ -1898,6 +1922,7 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
 }
 
 __device__ __forceinline__ bool sft_window(const sf_dargs &a, const sfd_taps &t, const sft_maps &mp,
+                                           const uint4 *__restrict__ tct,
                                            const sft_tiles &bt, sft_state &S, int wid)
 {
     S.wid = wid;
@@ -1911,7 +1936,7 @@ __device__ __forceinline__ bool sft_window(const sf_dargs &a, const sfd_taps &t,
     for (int i = threadIdx.x; i < SFD_WX * SFD_WY * 2; i += SFD_THREADS) S.mask[i] = 0u;
     __syncthreads();
 #define SFT_RUN(IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3) \
-    if (!S.dead) sft_input<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(a, t, mp, bt, S);
+    if (!S.dead) sft_input<IDX, RY, NZ, RZ0, RZ1, RZ2, RZ3>(a, t, mp, bt, tct, S);
     SFD_SOURCES(SFT_RUN)
 #undef SFT_RUN
     if (S.dead) return false;
@@ -1945,12 +1970,12 @@ sf_window_tc(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_tap
     S.thr = reinterpret_cast<float *>(sm + SFT_OFF_THR);
     S.flags = reinterpret_cast<u32 *>(sm + SFT_OFF_FLAGS);
     S.bar_s = sf_smem_addr(sm + SFT_OFF_MBAR);
-    S.bar_a = S.bar_s + 16u;
-    S.bar_z = S.bar_s + 32u;
-    S.bar_y = S.bar_s + 48u;
+    S.bar_a = S.bar_s + 8u * SFT_NS;
+    S.bar_z = S.bar_a + 16u;
+    S.bar_y = S.bar_z + 16u;
     S.ph_s = S.ph_a = S.ph_z = S.ph_y = 0u;
     S.pend = 0u;
-    S.it = S.ity = 0;
+    S.it = S.ic = S.ity = 0;
     S.dead = false;
     S.limit = (unsigned long long)a.wait_ns;
     S.err = a.err;
@@ -1958,10 +1983,10 @@ sf_window_tc(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_tap
     {
         /* from the device copy: the same bytes as bt's tiles */
         uint4 *dst = reinterpret_cast<uint4 *>(S.T);
-        for (int i = threadIdx.x; i < SFT_TILE_BYTES / 16; i += SFD_THREADS) dst[i] = __ldg(tct + i);
+        for (int i = threadIdx.x; i < SFT_ZT_BYTES / 16; i += SFD_THREADS) dst[i] = __ldg(tct + i);
     }
     if (threadIdx.x == 0) {
-        for (int b = 0; b < 8; ++b)
+        for (int b = 0; b < SFT_NS + 6; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(S.bar_s + 8u * (u32)b) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1976,16 +2001,17 @@ sf_window_tc(const __grid_constant__ sf_dargs a, const __grid_constant__ sfd_tap
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     S.tmem = s_tmem;
-    const bool ok = sft_window(a, t, mp, bt, S, a.wid0 + (int)blockIdx.x);
+    const bool ok = sft_window(a, t, mp, tct, bt, S, a.wid0 + (int)blockIdx.x);
     if (!ok && threadIdx.x == 0) {
         /* a bounded wait expired: report it, then give the copies and MMAs in
          * flight a bounded time to land before the buffers go away */
         atomicOr(a.err, 1);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < SFT_NS; ++b)
             if ((S.pend >> b) & 1u) sfw_wait(S.bar_s + 8u * (u32)b, (S.ph_s >> b) & 1u, S.limit);
-            if ((S.pend >> (2 + b)) & 1u) sfw_wait(S.bar_a + 8u * (u32)b, (S.ph_a >> b) & 1u, S.limit);
-            if ((S.pend >> (4 + b)) & 1u) sfw_wait(S.bar_z + 8u * (u32)b, (S.ph_z >> b) & 1u, S.limit);
-            if ((S.pend >> (6 + b)) & 1u) sfw_wait(S.bar_y + 8u * (u32)b, (S.ph_y >> b) & 1u, S.limit);
+        for (int b = 0; b < 2; ++b) {
+            if ((S.pend >> (3 + b)) & 1u) sfw_wait(S.bar_a + 8u * (u32)b, (S.ph_a >> b) & 1u, S.limit);
+            if ((S.pend >> (5 + b)) & 1u) sfw_wait(S.bar_z + 8u * (u32)b, (S.ph_z >> b) & 1u, S.limit);
+            if ((S.pend >> (7 + b)) & 1u) sfw_wait(S.bar_y + 8u * (u32)b, (S.ph_y >> b) & 1u, S.limit);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -928,13 +928,14 @@ sf_status plan_detect_tc(sf_ctx *c)
     const size_t offA = off;
     off += 2 * 128 * 128;
     const size_t offT = off;
-    off += align_up(tile_bytes, 1024);
+    /* the z tiles, and one y-tile slot the kernel fills per input */
+    off += align_up(zbytes + (nyt > 0 ? (size_t)2 * 4096 : 0), 1024);
     const size_t offS = off;
-    /* two slab buffers; inputs with sigma_xy = 0 use the region as a second
-     * A tile (two 16 KB atoms) */
+    /* three slab buffers; inputs with sigma_xy = 0 use the region as a
+     * second A tile (two 16 KB atoms) */
     bool any_ry0 = false;
     for (int i = 0; i < nsrc; ++i) any_ry0 |= wp.srcs[i].ry == 0;
-    off += std::max<size_t>((size_t)2 * 2 * kym * 128, any_ry0 ? 2 * 16384 : 0);
+    off += std::max<size_t>((size_t)3 * 2 * kym * 128, any_ry0 ? 2 * 16384 : 0);
     const size_t offP = off;
     off += align_up((size_t)g.wx * wp.nzf * 4, 16);
     const size_t offM = off;
@@ -946,7 +947,7 @@ sf_status plan_detect_tc(sf_ctx *c)
     const size_t offF = off;
     off += 16;
     const size_t offMB = off;
-    off += 64;
+    off += 128;   /* 3 slab, 2 A-tile, 2 z and 2 y barriers */
     const size_t smem = off + 1024;
     if (smem > kSmemLimit) return SF_OK;
     std::string p = "#define SF_KERNEL_TC 1\n" + wp.prelude + "#define SFD_TMA 1\n";
