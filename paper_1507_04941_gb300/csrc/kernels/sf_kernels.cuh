@@ -195,10 +195,12 @@ __host__ __device__ constexpr int sfx_r(int k)
 
 /* x pass of one lane (V consecutive z of one (y, z) position) over output
  * planes [xb, xe): a register ring of the last 2R+1+PF input planes, every
- * input element read once, pair sums shared by the NOUT outputs. */
+ * input element read once, pair sums shared by the NOUT outputs.  Input
+ * planes are `plane` elements apart; output k is written at
+ * dst[k] + x * oplane + lane_off (a null dst[k] is skipped). */
 template <int V>
 __device__ __forceinline__ void sfx_lane(const sfx_t *__restrict__ p, void *const *dst, i64 lane_off,
-                                         i64 nx, i64 plane, i64 xb, i64 xe, const sfx_taps &t)
+                                         i64 nx, i64 plane, i64 oplane, i64 xb, i64 xe, const sfx_taps &t)
 {
     constexpr int RM = SFX_RM, K = 2 * RM + 1 + SFX_PF;
     const i64 xlim = min(nx, xe + RM);            /* inputs used: [xb-RM, xe+RM) */
@@ -235,7 +237,8 @@ __device__ __forceinline__ void sfx_lane(const sfx_t *__restrict__ p, void *cons
                     for (int j = 1; j <= sfx_r(k); ++j)
 #pragma unroll
                         for (int v = 0; v < V; ++v) acc[v] = fmaf(t.g[k][j], ps[j][v], acc[v]);
-                    sf_st<sfx_t, V>(reinterpret_cast<sfx_t *>(dst[k]) + x * plane + lane_off, acc);
+                    if (dst[k] != nullptr)
+                        sf_st<sfx_t, V>(reinterpret_cast<sfx_t *>(dst[k]) + x * oplane + lane_off, acc);
                 }
                 /* slot u is free: refill it with plane x - RM + K */
                 const i64 xi = x - RM + K;
@@ -270,7 +273,7 @@ __device__ __forceinline__ void sfx_stage(u32 dst, const void *src, bool in)
 
 template <int V, int THREADS, int D>
 __device__ __forceinline__ void sfx_lane_staged(const sfx_t *__restrict__ p, void *const *dst,
-                                                i64 lane_off, i64 nx, i64 plane, i64 xb, i64 xe,
+                                                i64 lane_off, i64 nx, i64 plane, i64 oplane, i64 xb, i64 xe,
                                                 const sfx_taps &t, u32 sb, const unsigned char *sp)
 {
     static_assert(D >= 3, "staging depth");
@@ -347,7 +350,8 @@ __device__ __forceinline__ void sfx_lane_staged(const sfx_t *__restrict__ p, voi
                     }
 #pragma unroll
                     for (int k = 0; k < SFX_NOUT; ++k)
-                        sf_st<sfx_t, V>(reinterpret_cast<sfx_t *>(dst[k]) + x * plane + lane_off, o[k]);
+                        if (dst[k] != nullptr)
+                            sf_st<sfx_t, V>(reinterpret_cast<sfx_t *>(dst[k]) + x * oplane + lane_off, o[k]);
                 }
             }
         }
@@ -372,10 +376,10 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
 #if SFX_D > 0
     constexpr u32 VB = SFX_V * (u32)sizeof(sfx_t);
     sfx_lane_staged<SFX_V, SFX_THREADS, SFX_D>(
-        p, a.dst, lane * SFX_V, a.nx, a.plane, xb, xe, t,
+        p, a.dst, lane * SFX_V, a.nx, a.plane, a.plane, xb, xe, t,
         (u32)__cvta_generic_to_shared(sfx_smem) + threadIdx.x * VB, sfx_smem + threadIdx.x * VB);
 #else
-    sfx_lane<SFX_V>(p, a.dst, lane * SFX_V, a.nx, a.plane, xb, xe, t);
+    sfx_lane<SFX_V>(p, a.dst, lane * SFX_V, a.nx, a.plane, a.plane, xb, xe, t);
 #endif
 }
 #endif /* SF_KERNEL_XPASS */
@@ -388,11 +392,11 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
 extern __shared__ __align__(16) unsigned char sfx_smem[];
 
 template <int V>
-__device__ __forceinline__ void sfx_batch_lane(const sf_xcube &q, i64 lane, const sfx_taps &t)
+__device__ __forceinline__ void sfx_batch_lane(const sf_xcube &q, i64 lane, i64 olane, i64 oplane, const sfx_taps &t)
 {
     constexpr u32 VB = V * (u32)sizeof(sfx_t);
     const sfx_t *p = reinterpret_cast<const sfx_t *>(q.src) + lane * V;
-    sfx_lane_staged<V, SFX_THREADS, SFX_D>(p, q.dst, lane * V, q.nx, q.plane, q.x0, q.x1, t,
+    sfx_lane_staged<V, SFX_THREADS, SFX_D>(p, q.dst, olane, q.nx, q.plane, oplane, q.x0, q.x1, t,
                                            (u32)__cvta_generic_to_shared(sfx_smem) + threadIdx.x * VB,
                                            sfx_smem + threadIdx.x * VB);
 }
@@ -410,15 +414,23 @@ sf_xpass_batch(const __grid_constant__ sf_xbargs a, const __grid_constant__ sfx_
     const sf_xcube &q = a.cubes[lo];
     const i64 lane = (i64)(blk - q.block0) * SFX_THREADS + threadIdx.x;
     if (lane >= q.lanes) return;
+    /* outputs with a padded z stride (ozs > nz, one element per lane): the
+     * lane's (y, z) moves to y * ozs + z; the padding is never written */
+    i64 olane = lane * q.v, oplane = q.plane;
+    if (q.ozs != q.nz) {
+        const i64 y = lane / q.nz;
+        olane = y * q.ozs + (lane - y * q.nz);
+        oplane = (q.plane / q.nz) * q.ozs;
+    }
     if constexpr (sizeof(sfx_t) == 4) {
-        if (q.v == 2) sfx_batch_lane<2>(q, lane, t);
-        else sfx_batch_lane<1>(q, lane, t);
+        if (q.v == 2) sfx_batch_lane<2>(q, lane, olane, oplane, t);
+        else sfx_batch_lane<1>(q, lane, olane, oplane, t);
     } else {
-        if (q.v == 2) sfx_batch_lane<2>(q, lane, t);
+        if (q.v == 2) sfx_batch_lane<2>(q, lane, olane, oplane, t);
         else {
             /* two-byte lanes are below the cp.async size: register ring */
             const sfx_t *p = reinterpret_cast<const sfx_t *>(q.src) + lane;
-            sfx_lane<1>(p, q.dst, lane, q.nx, q.plane, q.x0, q.x1, t);
+            sfx_lane<1>(p, q.dst, olane, q.nx, q.plane, oplane, q.x0, q.x1, t);
         }
     }
 }
@@ -1337,10 +1349,10 @@ sf_persist(const __grid_constant__ sf_pargs pa, const __grid_constant__ sfd_taps
             const i64 nx = u.args.nx, plane = u.plane, x0 = u.x0, x1 = u.x1;
             if (u.xv == 2) {
                 for (i64 l = l0 + threadIdx.x; l < l1; l += SFD_THREADS)
-                    sfx_lane<2>(src + 2 * l, dst, 2 * l, nx, plane, x0, x1, xt);
+                    sfx_lane<2>(src + 2 * l, dst, 2 * l, nx, plane, plane, x0, x1, xt);
             } else {
                 for (i64 l = l0 + threadIdx.x; l < l1; l += SFD_THREADS)
-                    sfx_lane<1>(src + l, dst, l, nx, plane, x0, x1, xt);
+                    sfx_lane<1>(src + l, dst, l, nx, plane, plane, x0, x1, xt);
             }
             __threadfence();
             __syncthreads();

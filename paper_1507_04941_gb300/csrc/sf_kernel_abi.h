@@ -35,7 +35,9 @@ struct sf_xcube {
     long long x0, x1;  /* output planes [x0, x1) (the whole cube: 0, nx) */
     long long plane;   /* ny * nz */
     long long lanes;   /* plane / v */
-    int v;             /* elements per lane: 2, or 1 for an odd y-z plane */
+    long long nz;      /* input row length */
+    long long ozs;     /* output row stride: nz, or nz padded to a 16-byte multiple (then v = 1) */
+    int v;             /* elements per lane: 2, or 1 for an odd y-z plane or padded rows */
     int block0;        /* first block of this cube */
 };
 

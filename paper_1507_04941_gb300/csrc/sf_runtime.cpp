@@ -309,9 +309,11 @@ struct sf_ctx {
     struct Cube {
         long long nx, ny, nz, nw32;
         int nwx, nwy, nwz, nwin;
+        long long zs;                 /* z stride of the scratch cubes: nz, or nz padded to 16 bytes */
         size_t slot_bytes;            /* one x-filtered cube */
-        void *slots;                  /* n_xy scratch cubes */
+        void *slots;                  /* n_xy scratch cubes, and a copy of the cube where zs > nz */
         bool tma;
+        bool pad;                     /* this plan reads the padded scratch (and the copy) by TMA */
         int xv;
     };
     bool batch = false;               /* created by sf_create_batch */
@@ -606,16 +608,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 
 /* Tiled 3D tensor map of a cube [x][y][z] with box {srow, WY + 2 RY, 1}. */
 bool encode_map_dims(const sf_ctx *c, const void *base, long long nx, long long ny, long long nz,
-                     int srow, int ry, CUtensorMap *out)
+                     int srow, int ry, CUtensorMap *out, long long zstride = -1)
 {
+    /* rows zstride elements apart (default nz); columns past nz read as zero */
+    if (zstride < 0) zstride = nz;
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const CUtensorMapDataType dt = c->cfg.storage == SF_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                    : c->cfg.storage == SF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t dims[3] = {(cuuint64_t)nz, (cuuint64_t)ny, (cuuint64_t)nx};
-    const cuuint64_t strides[2] = {(cuuint64_t)(nz * (long long)c->ebytes),
-                                   (cuuint64_t)(ny * nz * (long long)c->ebytes)};
+    const cuuint64_t strides[2] = {(cuuint64_t)(zstride * (long long)c->ebytes),
+                                   (cuuint64_t)(ny * zstride * (long long)c->ebytes)};
     const cuuint32_t box[3] = {(cuuint32_t)srow, (cuuint32_t)(c->cfg.wy + 2 * ry), 1u};
     const cuuint32_t es[3] = {1u, 1u, 1u};
     return enc(out, dt, 3, const_cast<void *>(base), dims, strides, box, es,
@@ -1061,30 +1065,47 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
     const sf_config &g = c->cfg;
     const int nxy = (int)c->xy_sigma.size();
     if (nxy > SF_MAX_XOUT) return fail(c, SF_EINVAL, "the persistent form takes at most %d distinct sigma_xy", SF_MAX_XOUT);
-    /* copies for cubes that cannot use TMA: the largest chunk all their rows allow */
+    /* copies for cubes that cannot use TMA: the largest chunk all their rows
+     * allow.  With the batched x pass, cubes with padded scratch rows (zs > nz)
+     * read the padded scratch and a padded copy of themselves by TMA instead. */
     const int vec = (int)(16 / c->ebytes);
-    int ch = vec;
-    for (const sf_ctx::Cube &q : c->cubes)
-        if (q.nz % vec != 0) ch = std::min(ch, copy_chunk(c->ebytes, q.nz));
+    const bool xbatch = pp.xbatch && nxy > 0;
     WindowPlan wp;
-    if (!make_window_plan(c, pp.P, pp.minb, ch, true, wp))
-        return fail(c, SF_EINVAL, "window %dx%dx%d cannot be tiled by the persistent kernel (wy %% 8, "
-                    "wz %% 32, wx <= 64)", g.wx, g.wy, g.wz);
-    for (sf_ctx::Cube &q : c->cubes) {
-        q.tma = tma_usable(c, wp, q.nz);
-        q.xv = (q.ny * q.nz) % 2 == 0 && c->ebytes == 4 ? 2 : 1;
+    bool any_pad = false;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        int ch = vec;
+        for (const sf_ctx::Cube &q : c->cubes)
+            if (q.nz % vec != 0 && !(attempt == 1 && xbatch && q.zs != q.nz))
+                ch = std::min(ch, copy_chunk(c->ebytes, q.nz));
+        wp = WindowPlan{};
+        if (!make_window_plan(c, pp.P, pp.minb, ch, true, wp))
+            return fail(c, SF_EINVAL, "window %dx%dx%d cannot be tiled by the persistent kernel (wy %% 8, "
+                        "wz %% 32, wx <= 64)", g.wx, g.wy, g.wz);
+        any_pad = false;
+        for (sf_ctx::Cube &q : c->cubes) {
+            q.pad = attempt == 1 && xbatch && q.zs != q.nz;
+            any_pad |= q.pad;
+            q.tma = q.pad || tma_usable(c, wp, q.nz);
+            q.xv = (q.ny * q.nz) % 2 == 0 && c->ebytes == 4 ? 2 : 1;
+        }
+        /* padding pays only where the window code can take TMA at all */
+        if (attempt == 1 || !xbatch || !tma_usable(c, wp, vec)) break;
+        bool want = false;
+        for (const sf_ctx::Cube &q : c->cubes) want |= q.zs != q.nz;
+        if (!want) break;
     }
     int r[4] = {0, 0, 0, 0}, rm = 0;
     for (int i = 0; i < nxy; ++i) {
         r[i] = c->xy_radius[i];
         rm = std::max(rm, r[i]);
     }
-    std::string xp = "#define SFX_NOUT " + std::to_string(std::max(1, nxy)) + "\n";
+    /* padded cubes: one more x-pass output, the identity (radius 0, tap 1),
+     * which writes the padded copy of the cube exactly */
+    std::string xp = "#define SFX_NOUT " + std::to_string(std::max(1, nxy + (any_pad ? 1 : 0))) + "\n";
     for (int i = 0; i < 4; ++i) xp += "#define SFX_R" + std::to_string(i) + " " + std::to_string(r[i]) + "\n";
     xp += "#define SFX_RM " + std::to_string(rm) + "\n";
     xp += "#define SFX_PF " + std::to_string(pp.pf) + "\n";
     xp += std::string("typedef ") + storage_ctype(g.storage) + " sfx_t;\n";
-    const bool xbatch = pp.xbatch && nxy > 0;
     std::string p = "#define SF_KERNEL_PERSIST 1\n" + wp.prelude + "#define SFD_TMA 1\n" + xp;
     if (xbatch) p += "#define SFP_XITEMS 0\n";
     std::string err;
@@ -1114,6 +1135,11 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
     std::vector<int> all;
     for (int i = 0; i < nxy; ++i) all.push_back(i);
     c->pxtaps = nxy ? xpass_taps(c, all) : std::vector<float>(1, 1.f);
+    if (any_pad) {
+        std::vector<float> id((size_t)rm + 1, 0.f);
+        id[0] = 1.f;
+        c->pxtaps.insert(c->pxtaps.end(), id.begin(), id.end());
+    }
     c->psrc = wp.srcs;
     c->pnsrc = (int)wp.srcs.size();
     c->psrow = wp.sh.SROW;
@@ -1182,7 +1208,9 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
             sf_xcube &xc = c->h_xcubes[i];
             std::memset(&xc, 0, sizeof(xc));
             const long long plane = q.ny * q.nz;
-            xc.v = plane % 2 == 0 ? 2 : 1;
+            xc.v = plane % 2 == 0 && !q.pad ? 2 : 1;
+            xc.nz = q.nz;
+            xc.ozs = q.pad ? q.zs : q.nz;
             xc.nx = q.nx;
             xc.x0 = 0;
             xc.x1 = q.nx;
@@ -1197,15 +1225,17 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
     if (!items.empty() &&
         (e = cudaMemcpy(c->d_items, items.data(), sizeof(sf_item) * items.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cuda_fail(c, e, "item table");
-    /* tensor maps of the scratch inputs do not change between calls */
+    /* tensor maps of the scratch inputs (and of a padded cube's copy, the
+     * slot after them) do not change between calls */
     for (size_t i = 0; i < c->cubes.size(); ++i) {
         const sf_ctx::Cube &q = c->cubes[i];
         if (!q.tma) continue;
         for (int sidx = 0; sidx < c->pnsrc; ++sidx) {
             const DetectSource &d = c->psrc[sidx];
-            if (d.slot < 0) continue;
-            if (!encode_map_dims(c, (const char *)q.slots + (size_t)d.slot * q.slot_bytes, q.nx, q.ny, q.nz,
-                                 c->psrow, d.ry, &c->h_maps[i * c->pnsrc + sidx]))
+            if (d.slot < 0 && !q.pad) continue;
+            const int slot = d.slot < 0 ? nxy : d.slot;
+            if (!encode_map_dims(c, (const char *)q.slots + (size_t)slot * q.slot_bytes, q.nx, q.ny, q.nz,
+                                 c->psrow, d.ry, &c->h_maps[i * c->pnsrc + sidx], q.pad ? q.zs : q.nz))
                 return fail(c, SF_ECUDA, "tensor map encoding failed");
         }
     }
@@ -1283,7 +1313,9 @@ sf_status run_persist(sf_ctx *c, const void *const *cubes, uint32_t *const *mask
         sf_dargs &a = h.args;
         for (int sidx = 0; sidx < c->pnsrc; ++sidx) {
             const DetectSource &d = c->psrc[sidx];
-            a.src[sidx] = d.slot < 0 ? cubes[i] : (const void *)((const char *)q.slots + (size_t)d.slot * q.slot_bytes);
+            /* a padded cube's own input is its copy, the slot after the scratch cubes */
+            const int slot = d.slot < 0 && q.pad ? (int)c->xy_sigma.size() : d.slot;
+            a.src[sidx] = slot < 0 ? cubes[i] : (const void *)((const char *)q.slots + (size_t)slot * q.slot_bytes);
             for (size_t f = 0; f < d.filters.size(); ++f) a.fidx[sidx][f] = d.filters[f];
         }
         a.mask = masks[i];
@@ -1311,14 +1343,14 @@ sf_status run_persist(sf_ctx *c, const void *const *cubes, uint32_t *const *mask
             const sf_ctx::Cube &q = c->cubes[i];
             sf_xcube &xc = c->h_xcubes[i];
             xc.src = cubes[i];
+            const int nout = (int)c->xy_sigma.size() + (q.pad ? 1 : 0);   /* the copy: the identity output */
             for (int k = 0; k < SF_MAX_XOUT; ++k)
-                xc.dst[k] = k < (int)c->xy_sigma.size() ? (void *)((char *)q.slots + (size_t)k * q.slot_bytes)
-                                                        : nullptr;
+                xc.dst[k] = k < nout ? (void *)((char *)q.slots + (size_t)k * q.slot_bytes) : nullptr;
         }
     }
     for (size_t i = 0; i < c->cubes.size(); ++i) {
         const sf_ctx::Cube &q = c->cubes[i];
-        if (!q.tma) continue;
+        if (!q.tma || q.pad) continue;
         for (int sidx = 0; sidx < c->pnsrc; ++sidx)
             if (c->psrc[sidx].slot < 0 &&
                 !encode_map_dims(c, cubes[i], q.nx, q.ny, q.nz, c->psrow, c->psrc[sidx].ry,
@@ -1597,8 +1629,14 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
             q.nwy = (int)((q.ny + g.wy - 1) / g.wy);
             q.nwz = (int)((q.nz + g.wz - 1) / g.wz);
             q.nwin = q.nwx * q.nwy * q.nwz;
-            q.slot_bytes = align_up((size_t)(q.nx * q.ny * q.nz) * c->ebytes, 256);
-            total += q.slot_bytes * c->xy_sigma.size();
+            /* rows that are not 16-byte multiples cannot be copied by TMA:
+             * the batched x pass writes such a cube's scratch cubes, and a
+             * copy of the cube itself, with rows padded to 16 bytes */
+            const long long vec = 16 / c->ebytes;
+            const size_t nxy = c->xy_sigma.size();
+            q.zs = q.nz % vec != 0 && nxy > 0 && nxy < SF_MAX_XOUT ? (q.nz + vec - 1) / vec * vec : q.nz;
+            q.slot_bytes = align_up((size_t)(q.nx * q.ny * q.zs) * c->ebytes, 256);
+            total += q.slot_bytes * (nxy + (q.zs != q.nz ? 1 : 0));
             c->cubes.push_back(q);
         }
         if (total > 0) {
@@ -1611,7 +1649,7 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
         size_t off = 0;
         for (sf_ctx::Cube &q : c->cubes) {
             q.slots = c->bscratch ? (char *)c->bscratch + off : nullptr;
-            off += q.slot_bytes * c->xy_sigma.size();
+            off += q.slot_bytes * (c->xy_sigma.size() + (q.zs != q.nz ? 1 : 0));
         }
         if (s == SF_OK) {
             sf_ctx::PersistPlan dp;
@@ -2067,6 +2105,7 @@ sf_status sf_tune(sf_ctx *c, const void *const *d_cubes, uint32_t *const *d_mask
         q.nwy = c->nwy;
         q.nwz = c->nwz;
         q.nwin = c->nwin;
+        q.zs = q.nz;
         q.slot_bytes = c->cube_bytes;
         q.slots = c->scratch;
         c->cubes.push_back(q);

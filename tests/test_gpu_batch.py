@@ -58,6 +58,31 @@ def test_batch_equals_per_cube(dev, oracle):
     assert not ((got != want) & sure).any()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_batch_padded_rows_equal_per_cube(dev, storage, monkeypatch):
+    """Cubes whose rows are not 16-byte multiples (nz 131, 129, 130 in FP32;
+    also 200 in FP16) take padded scratch rows and a padded copy of the cube
+    written by the batched x pass, read by TMA: bit-identical to the per-cube
+    path, which reads them unpadded by cp.async (the CUDA-core window kernel
+    for FP16, as in the batch)."""
+    import torch
+    from paper_1507_04941_gb300 import BatchSourceFinder, SourceFinder
+    dt = {"f32": torch.float32, "f16": torch.float16}[storage]
+    cubes = [c.to(dt).contiguous() for c in _cubes(dev)]
+    with BatchSourceFinder(SHAPES, BANK6, 3.0, (32, 32, 64), storage=storage, device=dev) as bf:
+        masks, means, stds = bf.detect(cubes, stats=True)
+        bf.synchronize()
+    monkeypatch.setenv("SF_NO_TC", "1")
+    for i, cube in enumerate(cubes):
+        with SourceFinder(SHAPES[i], BANK6, 3.0, (32, 32, 64), storage=storage, device=dev) as sf:
+            m1, me1, sd1 = sf.detect(cube, stats=True)
+            torch.cuda.synchronize(dev)
+        assert m1.any() or not masks[i].any()
+        assert torch.equal(masks[i], m1), f"{storage} cube {i} {SHAPES[i]} mask"
+        assert torch.equal(means[i], me1), f"{storage} cube {i} mean"
+        assert torch.equal(stds[i], sd1), f"{storage} cube {i} std"
+
+
 @pytest.mark.parametrize("opts", [dict(stats_fp64=True), dict(std_ddof=1)])
 def test_batch_statistics_options(dev, opts):
     """The statistics options reach the persistent kernel: bit-identical to
