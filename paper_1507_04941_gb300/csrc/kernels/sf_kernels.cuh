@@ -373,13 +373,21 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
     const i64 xb = a.xoff + (i64)blockIdx.y * a.xseg;
     const i64 xe = min(a.nx, xb + a.xseg);
     const sfx_t *p = reinterpret_cast<const sfx_t *>(a.src) + lane * SFX_V;
+    /* outputs with a padded z stride (ozs > nz; planned with V = 1): the
+     * lane's (y, z) moves to y * ozs + z; the padding is never written */
+    i64 olane = lane * SFX_V, oplane = a.plane;
+    if (a.ozs != a.nz) {
+        const i64 y = lane / a.nz;
+        olane = y * a.ozs + (lane - y * a.nz);
+        oplane = (a.plane / a.nz) * a.ozs;
+    }
 #if SFX_D > 0
     constexpr u32 VB = SFX_V * (u32)sizeof(sfx_t);
     sfx_lane_staged<SFX_V, SFX_THREADS, SFX_D>(
-        p, a.dst, lane * SFX_V, a.nx, a.plane, a.plane, xb, xe, t,
+        p, a.dst, olane, a.nx, a.plane, oplane, xb, xe, t,
         (u32)__cvta_generic_to_shared(sfx_smem) + threadIdx.x * VB, sfx_smem + threadIdx.x * VB);
 #else
-    sfx_lane<SFX_V>(p, a.dst, lane * SFX_V, a.nx, a.plane, a.plane, xb, xe, t);
+    sfx_lane<SFX_V>(p, a.dst, olane, a.nx, a.plane, oplane, xb, xe, t);
 #endif
 }
 #endif /* SF_KERNEL_XPASS */

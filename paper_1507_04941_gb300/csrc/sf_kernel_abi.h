@@ -24,6 +24,8 @@ struct sf_xargs {
     long long lanes;   /* plane / V */
     long long xseg;    /* x positions per grid row */
     long long xoff;    /* first output plane of grid row 0 */
+    long long nz;      /* input row length */
+    long long ozs;     /* output row stride: nz, or nz padded to a 16-byte multiple (then V = 1) */
 };
 
 /* x pass of many cubes in one launch: blocks [block0, next block0) of the

@@ -111,6 +111,7 @@ struct Launch {
     cudaKernel_t kernel = nullptr;
     dim3 grid, block;
     size_t smem = 0;
+    int v = 1;   /* x passes: elements per lane */
 };
 
 /* ------------------------------------------------------------ JIT -------- */
@@ -252,6 +253,14 @@ struct sf_ctx {
     long long xseg = 0;
     std::vector<std::vector<int>> xgroups;   /* slots per x-pass launch */
     std::vector<Launch> xlaunch;
+    /* rows that are not 16-byte multiples: the scratch slots have a padded z
+     * stride zs, and the detect path's x pass (one element per lane) also
+     * writes a padded copy of the cube into slot n_xy (the identity output),
+     * so the window kernels read every input by TMA */
+    long long zs = 0;
+    bool dpad = false;                       /* the detect plan reads the padded layout */
+    std::vector<std::vector<int>> xgroups_p; /* slots per padded x-pass launch (n_xy: the copy) */
+    std::vector<Launch> xlaunch_p;
 
     /* fused detect */
     bool fused = false;
@@ -416,12 +425,21 @@ sf_status set_smem(sf_ctx *c, cudaKernel_t k, size_t smem)
 }
 
 /* ---------------------------------------------------- x pass kernels --- */
-sf_status build_xpass(sf_ctx *c, const std::vector<int> &slots, Launch *L)
+/* x radius of a scratch slot; slot n_xy is the identity (the cube's copy) */
+int slot_radius(const sf_ctx *c, int slot)
 {
+    return slot < (int)c->xy_radius.size() ? c->xy_radius[slot] : 0;
+}
+
+sf_status build_xpass(sf_ctx *c, const std::vector<int> &slots, Launch *L, int v = 0)
+{
+    if (v <= 0) v = c->xv;
+    /* cp.async copies 4, 8 or 16 bytes: narrower lanes use the register ring */
+    const int xd = v * (int)c->ebytes < 4 ? 0 : c->xd;
     const int nout = (int)slots.size();
     int r[4] = {0, 0, 0, 0}, rm = 0;
     for (int i = 0; i < nout; ++i) {
-        r[i] = c->xy_radius[slots[i]];
+        r[i] = slot_radius(c, slots[i]);
         rm = std::max(rm, r[i]);
     }
     std::string p;
@@ -430,20 +448,21 @@ sf_status build_xpass(sf_ctx *c, const std::vector<int> &slots, Launch *L)
     for (int i = 0; i < 4; ++i) p += "#define SFX_R" + std::to_string(i) + " " + std::to_string(r[i]) + "\n";
     p += "#define SFX_RM " + std::to_string(rm) + "\n";
     p += "#define SFX_PF " + std::to_string(c->xpf) + "\n";
-    p += "#define SFX_V " + std::to_string(c->xv) + "\n";
+    p += "#define SFX_V " + std::to_string(v) + "\n";
     p += "#define SFX_THREADS " + std::to_string(c->xthreads) + "\n";
-    p += "#define SFX_D " + std::to_string(c->xd) + "\n";
+    p += "#define SFX_D " + std::to_string(xd) + "\n";
     p += std::string("typedef ") + storage_ctype(c->cfg.storage) + " sfx_t;\n";
     std::string err;
     sf_status s = jit_kernel(p, "sf_xpass", c->device, &L->kernel, err);
     if (s != SF_OK) return fail(c, s, "x pass: %s", err.c_str());
     const long long plane = c->cfg.ny * c->cfg.nz;
-    const long long lanes = plane / c->xv;
+    const long long lanes = plane / v;
     const long long nseg = (c->cfg.nx + c->xseg - 1) / c->xseg;
     L->block = dim3(c->xthreads);
     L->grid = dim3((unsigned)((lanes + c->xthreads - 1) / c->xthreads), (unsigned)nseg);
+    L->v = v;
     /* staged form: xd slots of one vector per thread */
-    L->smem = c->xd > 0 ? (size_t)c->xd * c->xthreads * c->xv * c->ebytes : 0;
+    L->smem = xd > 0 ? (size_t)xd * c->xthreads * v * c->ebytes : 0;
     if (L->smem > 48 * 1024 && (s = set_smem(c, L->kernel, L->smem)) != SF_OK) return s;
     return SF_OK;
 }
@@ -451,9 +470,13 @@ sf_status build_xpass(sf_ctx *c, const std::vector<int> &slots, Launch *L)
 std::vector<float> xpass_taps(const sf_ctx *c, const std::vector<int> &slots)
 {
     int rm = 0;
-    for (int s : slots) rm = std::max(rm, c->xy_radius[s]);
+    for (int s : slots) rm = std::max(rm, slot_radius(c, s));
     std::vector<float> t(slots.size() * (rm + 1), 0.f);
     for (size_t i = 0; i < slots.size(); ++i) {
+        if (slots[i] >= (int)c->xy_radius.size()) {
+            t[i * (rm + 1)] = 1.f;   /* the identity: an exact copy */
+            continue;
+        }
         /* any filter of this slot carries its taps */
         for (const Filt &f : c->filt)
             if (f.slot == slots[i]) {
@@ -465,7 +488,7 @@ std::vector<float> xpass_taps(const sf_ctx *c, const std::vector<int> &slots)
 }
 
 sf_status run_xpass(sf_ctx *c, const Launch &L, const std::vector<int> &slots, const void *cube,
-                    cudaStream_t st, long long x0 = 0, long long x1 = -1)
+                    cudaStream_t st, long long x0 = 0, long long x1 = -1, bool padded = false)
 {
     sf_xargs xa{};
     xa.src = cube;
@@ -473,7 +496,9 @@ sf_status run_xpass(sf_ctx *c, const Launch &L, const std::vector<int> &slots, c
         xa.dst[i] = (char *)c->scratch + (size_t)slots[i] * c->cube_bytes;
     xa.nx = c->cfg.nx;
     xa.plane = c->cfg.ny * c->cfg.nz;
-    xa.lanes = xa.plane / c->xv;
+    xa.lanes = xa.plane / L.v;
+    xa.nz = c->cfg.nz;
+    xa.ozs = padded ? c->zs : c->cfg.nz;
     xa.xseg = c->xseg;
     xa.xoff = 0;
     Launch LL = L;
@@ -627,9 +652,17 @@ bool encode_map_dims(const sf_ctx *c, const void *base, long long nx, long long 
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+/* the detect path's maps: rows zs apart in the padded layout */
 bool encode_map(const sf_ctx *c, const void *base, int ry, CUtensorMap *out)
 {
-    return encode_map_dims(c, base, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->dSROW, ry, out);
+    return encode_map_dims(c, base, c->cfg.nx, c->cfg.ny, c->cfg.nz, c->dSROW, ry, out,
+                           c->dpad ? c->zs : c->cfg.nz);
+}
+
+/* the detect path's copy of the cube (padded layout), else nullptr */
+const void *padded_copy(const sf_ctx *c)
+{
+    return c->dpad ? (const char *)c->scratch + c->xy_sigma.size() * c->cube_bytes : nullptr;
 }
 
 /* Shape, shared-memory layout and parameter blocks of the window code (the
@@ -809,9 +842,10 @@ bool encode_map_tc(const sf_ctx *c, const void *base, int rows, int planes, CUte
     if (!enc) return false;
     const CUtensorMapDataType dt = c->cfg.storage == SF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const long long zs = c->dpad ? c->zs : c->cfg.nz;   /* rows zs apart in the padded layout */
     const cuuint64_t dims[3] = {(cuuint64_t)c->cfg.nz, (cuuint64_t)c->cfg.ny, (cuuint64_t)c->cfg.nx};
-    const cuuint64_t strides[2] = {(cuuint64_t)(c->cfg.nz * (long long)c->ebytes),
-                                   (cuuint64_t)(c->cfg.ny * c->cfg.nz * (long long)c->ebytes)};
+    const cuuint64_t strides[2] = {(cuuint64_t)(zs * (long long)c->ebytes),
+                                   (cuuint64_t)(c->cfg.ny * zs * (long long)c->ebytes)};
     const cuuint32_t box[3] = {64u, (cuuint32_t)rows, (cuuint32_t)planes};
     const cuuint32_t es[3] = {1u, 1u, 1u};
     return enc(out, dt, 3, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -851,12 +885,14 @@ sf_status plan_detect_tc(sf_ctx *c)
 {
     const sf_config &g = c->cfg;
     c->use_tc = false;
-    if (c->ebytes != 2 || g.wy != 32 || g.wz != 64 || g.wx > 64 || g.nz % 8 != 0 ||
+    /* TMA row strides: nz a multiple of 8, or the padded layout */
+    const long long zs = c->dpad ? c->zs : g.nz;
+    if (c->ebytes != 2 || g.wy != 32 || g.wz != 64 || g.wx > 64 || zs % 8 != 0 ||
         tensor_map_encoder() == nullptr)
         return SF_OK;
     WindowPlan wp;
-    if (!make_window_plan(c, 8, 2, copy_chunk(c->ebytes, g.nz), true, wp)) return SF_OK;
-    if (wp.nzf > 2 || wp.sh.HZ + wp.rzm > 48 || wp.rym > 16 || !tma_usable(c, wp, g.nz)) return SF_OK;
+    if (!make_window_plan(c, 8, 2, c->dpad ? 8 : copy_chunk(c->ebytes, g.nz), true, wp)) return SF_OK;
+    if (wp.nzf > 2 || wp.sh.HZ + wp.rzm > 48 || wp.rym > 16 || !tma_usable(c, wp, zs)) return SF_OK;
     const int nsrc = (int)wp.srcs.size();
     const int HZ = wp.sh.HZ;
     auto ky_of = [&](int ry) { return (g.wy + 2 * ry + 15) / 16 * 16; };
@@ -975,11 +1011,15 @@ sf_status plan_detect_tc(sf_ctx *c)
     c->tclaunch.block = dim3(256);
     c->tclaunch.grid = dim3((unsigned)c->nwin);
     c->tcmaps.assign(nsrc, CUtensorMap{});
-    for (int i = 0; i < nsrc; ++i)
+    for (int i = 0; i < nsrc; ++i) {
         if (wp.srcs[i].slot >= 0 &&
             !encode_map_tc(c, (const char *)c->scratch + (size_t)wp.srcs[i].slot * c->cube_bytes,
                            ky_of(wp.srcs[i].ry), 1, &c->tcmaps[i]))
             return fail(c, SF_ECUDA, "tensor map encoding failed");
+        /* the padded copy of the cube: A boxes of four planes, fixed */
+        if (wp.srcs[i].slot < 0 && c->dpad && !encode_map_tc(c, padded_copy(c), g.wy, 4, &c->tcmaps[i]))
+            return fail(c, SF_ECUDA, "tensor map encoding failed");
+    }
     c->use_tc = true;
     return SF_OK;
 }
@@ -994,8 +1034,20 @@ sf_status plan_detect(sf_ctx *c)
     if ((penv == 8 || penv == 16) && g.wz % (4 * penv) == 0) P = penv;
     const int minb = std::max(1, std::min(8, env_int("SF_WMINB", 3)));
     WindowPlan wp;
-    if (!make_window_plan(c, P, minb, copy_chunk(c->ebytes, g.nz), true, wp)) return SF_OK;
-    const bool tma = tma_usable(c, wp, g.nz);
+    /* rows that are not 16-byte multiples: the padded layout when the window
+     * code can take TMA slabs at all (SF_NO_PAD=1: element copies instead) */
+    bool tma = false;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        c->dpad = attempt == 0 && c->zs != g.nz && !c->xlaunch_p.empty() && env_int("SF_NO_PAD", 0) == 0;
+        wp = WindowPlan{};
+        const int ch = c->dpad ? (int)(16 / c->ebytes) : copy_chunk(c->ebytes, g.nz);
+        if (!make_window_plan(c, P, minb, ch, true, wp)) {
+            if (c->dpad) continue;
+            return SF_OK;
+        }
+        tma = tma_usable(c, wp, c->dpad ? c->zs : g.nz);
+        if (tma || !c->dpad) break;
+    }
     std::string p = "#define SF_KERNEL_DETECT 1\n" + wp.prelude;
     p += std::string("#define SFD_TMA ") + (tma ? "1" : "0") + "\n";
     std::string err;
@@ -1019,11 +1071,14 @@ sf_status plan_detect(sf_ctx *c)
     c->dtaps = wp.taps;
     c->dmaps.assign(wp.srcs.size(), CUtensorMap{});
     if (tma)
-        for (size_t i = 0; i < wp.srcs.size(); ++i)
-            if (wp.srcs[i].slot >= 0 &&
-                !encode_map(c, (const char *)c->scratch + (size_t)wp.srcs[i].slot * c->cube_bytes,
-                            wp.srcs[i].ry, &c->dmaps[i]))
+        for (size_t i = 0; i < wp.srcs.size(); ++i) {
+            /* scratch inputs, and in the padded layout the cube's copy */
+            const void *base = wp.srcs[i].slot >= 0
+                                   ? (const void *)((const char *)c->scratch + (size_t)wp.srcs[i].slot * c->cube_bytes)
+                                   : padded_copy(c);
+            if (base && !encode_map(c, base, wp.srcs[i].ry, &c->dmaps[i]))
                 return fail(c, SF_ECUDA, "tensor map encoding failed");
+        }
     c->fused = true;
     if (env_int("SF_NO_TC", 0) == 0 && (s = plan_detect_tc(c)) != SF_OK) return s;
     return SF_OK;
@@ -1383,9 +1438,12 @@ sf_status launch_windows(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float 
     sf_dargs da{};
     for (size_t i = 0; i < c->dsrc.size(); ++i) {
         const DetectSource &d = c->dsrc[i];
-        da.src[i] = d.slot < 0 ? d_cube : (const void *)((const char *)c->scratch + (size_t)d.slot * c->cube_bytes);
+        /* the cube itself: the caller's buffer, or in the padded layout its
+         * copy written by the x pass (whose map is fixed) */
+        da.src[i] = d.slot < 0 ? (c->dpad ? padded_copy(c) : d_cube)
+                               : (const void *)((const char *)c->scratch + (size_t)d.slot * c->cube_bytes);
         for (size_t q = 0; q < d.filters.size(); ++q) da.fidx[i][q] = d.filters[q];
-        if (c->dtma && d.slot < 0 && !encode_map(c, d_cube, d.ry, &c->dmaps[i]))
+        if (c->dtma && d.slot < 0 && !c->dpad && !encode_map(c, d_cube, d.ry, &c->dmaps[i]))
             return fail(c, SF_ECUDA, "tensor map encoding of the cube failed");
     }
     da.mask = d_mask;
@@ -1406,7 +1464,7 @@ sf_status launch_windows(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float 
     da.wid0 = w0;
     if (c->use_tc) {
         /* the cube's own A boxes, swizzled, per call */
-        for (size_t i = 0; i < c->dsrc.size(); ++i)
+        for (size_t i = 0; i < c->dsrc.size() && !c->dpad; ++i)
             if (c->dsrc[i].slot < 0 && !encode_map_tc(c, d_cube, c->cfg.wy, 4, &c->tcmaps[i]))
                 return fail(c, SF_ECUDA, "tensor map encoding of the cube failed");
         Launch L = c->tclaunch;
@@ -1604,7 +1662,12 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
     c->xseg = g.nx;
     const int nseg = env_int("SF_XSEG", 1);
     if (nseg > 1) c->xseg = (g.nx + nseg - 1) / nseg;
-    c->cube_bytes = align_up((size_t)c->nvox * c->ebytes, 256);
+    {
+        const long long vec = 16 / c->ebytes;
+        c->zs = g.nz % vec != 0 ? (g.nz + vec - 1) / vec * vec : g.nz;
+    }
+    /* one scratch slot: sized for the padded z stride */
+    c->cube_bytes = align_up((size_t)(g.nx * g.ny * c->zs) * c->ebytes, 256);
     sf_status s = SF_OK;
     {
         cudaError_t e = cudaMalloc(&c->err_flag, sizeof(int));
@@ -1667,13 +1730,13 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
         *out = c;
         return SF_OK;
     }
-    if (!c->xy_sigma.empty()) {
-        cudaError_t e = cudaMalloc(&c->scratch, c->cube_bytes * c->xy_sigma.size());
+    const size_t nslot = c->xy_sigma.size() + (c->zs != g.nz ? 1 : 0);
+    if (nslot > 0) {
+        cudaError_t e = cudaMalloc(&c->scratch, c->cube_bytes * nslot);
         if (e != cudaSuccess) {
             cudaGetLastError();
             delete c;
-            return fail(nullptr, SF_ENOMEM, "scratch allocation of %zu bytes failed",
-                        c->cube_bytes * (size_t)c->xy_sigma.size());
+            return fail(nullptr, SF_ENOMEM, "scratch allocation of %zu bytes failed", c->cube_bytes * nslot);
         }
         for (size_t i = 0; i < c->xy_sigma.size(); i += SF_MAX_XOUT) {
             std::vector<int> slots;
@@ -1682,6 +1745,16 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
             if ((s = build_xpass(c, slots, &L)) != SF_OK) break;
             c->xgroups.push_back(slots);
             c->xlaunch.push_back(L);
+        }
+        /* the detect path's padded x passes: every slot and the copy, one
+         * element per lane */
+        for (size_t i = 0; s == SF_OK && c->zs != g.nz && i < nslot; i += SF_MAX_XOUT) {
+            std::vector<int> slots;
+            for (size_t j = i; j < std::min(nslot, i + SF_MAX_XOUT); ++j) slots.push_back((int)j);
+            Launch L;
+            if ((s = build_xpass(c, slots, &L, 1)) != SF_OK) break;
+            c->xgroups_p.push_back(slots);
+            c->xlaunch_p.push_back(L);
         }
     }
     if (s == SF_OK) s = plan_detect(c);
@@ -1945,9 +2018,11 @@ sf_status sf_detect(sf_ctx *c, const void *d_cube, uint32_t *d_mask, float *d_me
     }
     {
         StageTimer tx(c, 0, st);
-        for (size_t i = 0; i < c->xlaunch.size(); ++i)
-            if ((s = run_xpass(c, c->xlaunch[i], c->xgroups[i], d_cube, st)) != SF_OK) return s;
-        tx.done((int)c->xlaunch.size());
+        const std::vector<Launch> &XL = c->dpad ? c->xlaunch_p : c->xlaunch;
+        const std::vector<std::vector<int>> &XG = c->dpad ? c->xgroups_p : c->xgroups;
+        for (size_t i = 0; i < XL.size(); ++i)
+            if ((s = run_xpass(c, XL[i], XG[i], d_cube, st, 0, -1, c->dpad)) != SF_OK) return s;
+        tx.done((int)XL.size());
     }
     StageTimer tf(c, 1, st);
     if (c->fused) {
@@ -2000,10 +2075,12 @@ sf_status sf_detect_slab(sf_ctx *c, const void *d_ext, int64_t halo, uint32_t *d
     {
         /* x pass of the slab's planes only; they read the halo planes */
         StageTimer tx(c, 0, st);
-        for (size_t i = 0; i < c->xlaunch.size(); ++i)
-            if ((s = run_xpass(c, c->xlaunch[i], c->xgroups[i], d_ext, st, halo, halo + S)) != SF_OK)
+        const std::vector<Launch> &XL = c->dpad ? c->xlaunch_p : c->xlaunch;
+        const std::vector<std::vector<int>> &XG = c->dpad ? c->xgroups_p : c->xgroups;
+        for (size_t i = 0; i < XL.size(); ++i)
+            if ((s = run_xpass(c, XL[i], XG[i], d_ext, st, halo, halo + S, c->dpad)) != SF_OK)
                 return s;
-        tx.done((int)c->xlaunch.size());
+        tx.done((int)XL.size());
     }
     StageTimer tf(c, 1, st);
     const int nwx = (int)((S + c->cfg.wx - 1) / c->cfg.wx);
@@ -2359,8 +2436,10 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
         const int need = (int)(std::min(nx, x1 + rxm) - 1) / (int)S;
         for (int j = waited[k & 1] + 1; j <= need; ++j) cudaStreamWaitEvent(ks, c->hev[j], 0);
         waited[k & 1] = std::max(waited[k & 1], need);
-        for (size_t i = 0; i < c->xlaunch.size(); ++i)
-            if ((s = run_xpass(c, c->xlaunch[i], c->xgroups[i], c->host_cube, ks, x0, x1)) != SF_OK) return s;
+        const std::vector<Launch> &XL = c->dpad ? c->xlaunch_p : c->xlaunch;
+        const std::vector<std::vector<int>> &XG = c->dpad ? c->xgroups_p : c->xgroups;
+        for (size_t i = 0; i < XL.size(); ++i)
+            if ((s = run_xpass(c, XL[i], XG[i], c->host_cube, ks, x0, x1, c->dpad)) != SF_OK) return s;
         const int w0 = (int)(x0 / wx) * c->nwy * c->nwz;
         const int w1 = (int)((x1 + wx - 1) / wx) * c->nwy * c->nwz;
         if ((s = launch_windows(c, c->host_cube, c->host_mask, nullptr, nullptr, ks, w0, w1)) != SF_OK) return s;
