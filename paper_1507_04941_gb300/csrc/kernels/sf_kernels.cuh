@@ -373,12 +373,13 @@ sf_xpass(const __grid_constant__ sf_xargs a, const __grid_constant__ sfx_taps t)
     const i64 xb = a.xoff + (i64)blockIdx.y * a.xseg;
     const i64 xe = min(a.nx, xb + a.xseg);
     const sfx_t *p = reinterpret_cast<const sfx_t *>(a.src) + lane * SFX_V;
-    /* outputs with a padded z stride (ozs > nz; planned with V = 1): the
-     * lane's (y, z) moves to y * ozs + z; the padding is never written */
+    /* outputs with a padded z stride (ozs > nz; planned with V dividing nz,
+     * so a lane stays within a row): the lane's first element (y, z) moves
+     * to y * ozs + z; the padding is never written */
     i64 olane = lane * SFX_V, oplane = a.plane;
     if (a.ozs != a.nz) {
-        const i64 y = lane / a.nz;
-        olane = y * a.ozs + (lane - y * a.nz);
+        const i64 e = lane * SFX_V, y = e / a.nz;
+        olane = y * a.ozs + (e - y * a.nz);
         oplane = (a.plane / a.nz) * a.ozs;
     }
 #if SFX_D > 0
@@ -422,12 +423,13 @@ sf_xpass_batch(const __grid_constant__ sf_xbargs a, const __grid_constant__ sfx_
     const sf_xcube &q = a.cubes[lo];
     const i64 lane = (i64)(blk - q.block0) * SFX_THREADS + threadIdx.x;
     if (lane >= q.lanes) return;
-    /* outputs with a padded z stride (ozs > nz, one element per lane): the
-     * lane's (y, z) moves to y * ozs + z; the padding is never written */
+    /* outputs with a padded z stride (ozs > nz; v divides nz, so a lane
+     * stays within a row): the lane's first element (y, z) moves to
+     * y * ozs + z; the padding is never written */
     i64 olane = lane * q.v, oplane = q.plane;
     if (q.ozs != q.nz) {
-        const i64 y = lane / q.nz;
-        olane = y * q.ozs + (lane - y * q.nz);
+        const i64 e = lane * q.v, y = e / q.nz;
+        olane = y * q.ozs + (e - y * q.nz);
         oplane = (q.plane / q.nz) * q.ozs;
     }
     if constexpr (sizeof(sfx_t) == 4) {

@@ -1263,7 +1263,8 @@ sf_status plan_persist(sf_ctx *c, const sf_ctx::PersistPlan &pp)
             sf_xcube &xc = c->h_xcubes[i];
             std::memset(&xc, 0, sizeof(xc));
             const long long plane = q.ny * q.nz;
-            xc.v = plane % 2 == 0 && !q.pad ? 2 : 1;
+            /* padded rows: pairs only where a pair never straddles a row */
+            xc.v = (q.pad ? q.nz % 2 == 0 : plane % 2 == 0) ? 2 : 1;
             xc.nz = q.nz;
             xc.ozs = q.pad ? q.zs : q.nz;
             xc.nx = q.nx;
@@ -1746,13 +1747,13 @@ static sf_status create_impl(const sf_config *cfg_in, int32_t n, const int64_t *
             c->xgroups.push_back(slots);
             c->xlaunch.push_back(L);
         }
-        /* the detect path's padded x passes: every slot and the copy, one
-         * element per lane */
+        /* the detect path's padded x passes: every slot and the copy; lanes
+         * of two elements where nz is even (a lane stays within a row) */
         for (size_t i = 0; s == SF_OK && c->zs != g.nz && i < nslot; i += SF_MAX_XOUT) {
             std::vector<int> slots;
             for (size_t j = i; j < std::min(nslot, i + SF_MAX_XOUT); ++j) slots.push_back((int)j);
             Launch L;
-            if ((s = build_xpass(c, slots, &L, 1)) != SF_OK) break;
+            if ((s = build_xpass(c, slots, &L, g.nz % 2 == 0 ? std::min(2, c->xv) : 1)) != SF_OK) break;
             c->xgroups_p.push_back(slots);
             c->xlaunch_p.push_back(L);
         }
