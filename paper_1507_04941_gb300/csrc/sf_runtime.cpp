@@ -2422,9 +2422,11 @@ sf_status sf_detect_host(sf_ctx *c, const void *h_cube, uint32_t *h_mask, void *
         cudaStreamWaitEvent(c->hcomp[i], c->hev[2 * K], 0);
     }
     cudaStreamWaitEvent(c->hback, c->hev[2 * K], 0);
+    /* host-to-device chunks on one copy stream (SF_HCOPY=2: alternating two) */
+    const int ncopy = env_int("SF_HCOPY", 1) == 2 ? 2 : 1;
     for (int k = 0; k < K; ++k) {
         const long long x0 = k * S, x1 = std::min(nx, x0 + S);
-        cudaStream_t cs = c->hcopy[k & 1];
+        cudaStream_t cs = c->hcopy[ncopy == 2 ? (k & 1) : 0];
         if ((e = cudaMemcpyAsync((char *)c->host_cube + (size_t)x0 * plane, (const char *)h_cube + (size_t)x0 * plane,
                                  (size_t)(x1 - x0) * plane, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
             return cuda_fail(c, e, "host-to-device copy");
