@@ -87,7 +87,13 @@ typedef struct sf_config {
 /* Create a context: copies cfg, computes the taps (Sec. 2.1: sampled Gaussian
  * exp(-o^2/2sigma^2), o in [-R, R], normalised to sum 1; radius limit 64 per
  * axis), plans the kernels, compiles them for the device at run time and
- * allocates the scratch cubes.  *out is NULL on failure. */
+ * allocates the scratch cubes: one per distinct non-zero sigma_xy, in the
+ * storage dtype.  Where nz * element size is not a multiple of 16 bytes the
+ * scratch rows are padded to 16 bytes and one more scratch cube holds a
+ * padded copy of the input, written by the detect path's x pass, so that the
+ * window kernels read every input with TMA (results are identical; the
+ * environment variable SF_NO_PAD=1 at creation keeps the unpadded layout).
+ * *out is NULL on failure. */
 sf_status sf_create(const sf_config *cfg, sf_ctx **out);
 
 /* Free the context after synchronising the device work it owns. NULL-safe. */
