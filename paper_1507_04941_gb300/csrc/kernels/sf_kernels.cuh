@@ -1564,8 +1564,9 @@ template <int RY>
 __device__ __forceinline__ void sft_mma_y(const sft_state &S, const sft_tiles &bt, int SI, int b, int yb)
 {
     constexpr int KY = sft_ky(RY);
-    const u32 a0 = sf_smem_addr(S.slab + b * SFT_SLAB_BYTES);
-    const u32 t0 = sf_smem_addr(S.T + SFT_ZT_BYTES);   /* this input's y tile, staged at its start */
+    /* base descriptors once, compile-time offsets per slice and part */
+    const unsigned long long a0 = sft_desc(sf_smem_addr(S.slab + b * SFT_SLAB_BYTES), (u32)(KY * 128), 1024u);
+    const unsigned long long t0 = sft_desc(sf_smem_addr(S.T + SFT_ZT_BYTES), 16u, 1024u);   /* this input's y tile */
     (void)bt;
     (void)SI;
     const u32 d = S.tmem + 128u + (u32)(yb * 32);
@@ -1574,8 +1575,8 @@ __device__ __forceinline__ void sft_mma_y(const sft_state &S, const sft_tiles &b
     for (int s = 0; s < KY / 16; ++s)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const unsigned long long ad = sft_desc(a0 + (u32)(s * 2048), (u32)(KY * 128), 1024u);
-            const unsigned long long bd = sft_desc(t0 + (u32)(h * 4096 + s * 32), 16u, 1024u);
+            const unsigned long long ad = a0 + (unsigned long long)((s * 2048) >> 4);
+            const unsigned long long bd = t0 + (unsigned long long)((h * 4096 + s * 32) >> 4);
             asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
                          "l"(ad), "l"(bd), "r"(SFT_IDESC_Y), "r"(acc));
@@ -1591,22 +1592,28 @@ __device__ __forceinline__ void sft_mma_y(const sft_state &S, const sft_tiles &b
 template <int SI, int NZ, int RZ0, int RZ1>
 __device__ __forceinline__ void sft_mma_z(const sft_state &S, const sft_tiles &bt, int buf, const unsigned char *A)
 {
-    const u32 a0 = sf_smem_addr(A);
+    /* base descriptors once; every slice's start is a compile-time offset
+     * added to the 14-bit address field (shared addresses stay below 2^18) */
+    const unsigned long long a0 = sft_desc(sf_smem_addr(A), 16u, 1024u);
 #pragma unroll
     for (int f = 0; f < NZ; ++f) {
         const int r = f == 0 ? RZ0 : RZ1;
-        const int slo = sft_slo(r), shi = sft_shi(r);
-        const u32 t0 = sf_smem_addr(S.T + bt.zt[SI][f] * 2 * 2048);
+        constexpr int SLO0 = sft_slo(RZ0), SHI0 = sft_shi(RZ0), SLO1 = sft_slo(RZ1), SHI1 = sft_shi(RZ1);
+        const int slo = f == 0 ? SLO0 : SLO1, shi = f == 0 ? SHI0 : SHI1;
+        (void)r;
+        const unsigned long long t0 = sft_desc(sf_smem_addr(S.T + bt.zt[SI][f] * 2 * 2048), 16u, 1024u);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const u32 d = S.tmem + (u32)(buf * 128 + f * 64 + j * 16);
             u32 acc = 0u;
-            for (int s = slo; s <= shi; ++s) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                if (s < slo || s > shi) continue;
                 const int ts = j + s;
-                const unsigned long long ad = sft_desc(a0 + (u32)((ts >> 2) * SFT_ATOM + (ts & 3) * 32), 16u, 1024u);
+                const unsigned long long ad = a0 + (unsigned long long)(((ts >> 2) * SFT_ATOM + (ts & 3) * 32) >> 4);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const unsigned long long bd = sft_desc(t0 + (u32)(h * 2048 + s * 32), 16u, 1024u);
+                    const unsigned long long bd = t0 + (unsigned long long)((h * 2048 + s * 32) >> 4);
                     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
                                  "l"(ad), "l"(bd), "r"(SFT_IDESC_Z), "r"(acc));
