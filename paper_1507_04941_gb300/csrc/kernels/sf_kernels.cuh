@@ -747,6 +747,7 @@ __device__ __forceinline__ void sfd_zfilter(const sfd_t *slab, const float *U, i
  * arguments); on expiry the CTA records the failure in *err and leaves.
  */
 struct __align__(64) sf_tmap { unsigned long long opaque[16]; };
+
 struct sfw_maps { sf_tmap m[SFD_NSRC]; };
 
 constexpr int SFW_RG = SFD_WY / 8;                 /* row groups of 8 */
@@ -1714,13 +1715,19 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
         return -1;
     };
     /* read the z accumulator of group g (buffer b) once its MMAs completed */
+    /* plane p takes part in this pass (every plane in pass 1) */
+    auto flagged = [&](int p) -> bool {
+        return pass == 0 || (((p < 32 ? (fl0 >> p) : (fl1 >> (p - 32))) & 1u) != 0u);
+    };
     auto epilogue = [&](int g, int b) {
         const bool ok = sft_wait(S, S.bar_z, S.ph_z, b, 3);
         S.pend &= ~(32u << b);
         if (!ok) S.dead = true;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int p = g * SFT_PLANES + slot;
-        const bool pv = p < S.npl && rowv && mine;
+        /* pass 2 reads flagged planes only: the rows of the others are not
+         * filtered in that pass (and could not select anything) */
+        const bool pv = p < S.npl && rowv && mine && (pass == 0 || flagged(p));
         float mx = -3.402823466e38f;
         u32 w0 = 0u, w1 = 0u;
         if (mine) {
@@ -1828,19 +1835,29 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
         } else {
             /* slab copies run two planes ahead through SFT_NS buffers: lp is
              * the next plane of this pass to copy */
-            int lp = gi >= 0 ? gi * SFT_PLANES : -1;
+            /* the next plane of this pass after p (-1: the first): pass 2
+             * filters only the flagged planes of its groups */
+            auto next_plane = [&](int p) -> int {
+                int g = p < 0 ? -1 : p / SFT_PLANES, q = p + 1;
+                for (;;) {
+                    if (g >= 0 && q < (g + 1) * SFT_PLANES && q < S.npl) {
+                        if (flagged(q)) return q;
+                        ++q;
+                        continue;
+                    }
+                    g = next_group(g);
+                    if (g < 0) return -1;
+                    q = g * SFT_PLANES;
+                }
+            };
+            int lp = next_plane(-1);
             auto load_next = [&]() {
                 if (lp < 0) return;
                 const int b = S.it % SFT_NS;
                 sft_load_slab<IDX, RY>(mp, S, lp, b);
                 S.pend |= 1u << b;
                 ++S.it;
-                if ((lp + 1) % SFT_PLANES != 0 && lp + 1 < S.npl) {
-                    ++lp;
-                } else {
-                    const int g2 = next_group(lp / SFT_PLANES);
-                    lp = g2 >= 0 ? g2 * SFT_PLANES : -1;
-                }
+                lp = next_plane(lp);
             };
             load_next();
             load_next();
@@ -1848,8 +1865,9 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                 const int gn = next_group(gi);
                 const int p0 = gi * SFT_PLANES;
                 const int np = min(SFT_PLANES, S.npl - p0);
-                int yprev = -1;
+                int yprev = -1, iprev = -1;
                 for (int i = 0; i < np; ++i) {
+                    if (!flagged(p0 + i)) continue;
                     const int b = S.ic % SFT_NS;
                     const bool ok = sft_wait(S, S.bar_s, S.ph_s, b, 2);
                     S.pend &= ~(1u << b);
@@ -1864,17 +1882,18 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                     ++S.ic;
                     /* the previous group's z accumulator, then the previous
                      * plane into the A tile (its z MMAs are complete by then) */
-                    if (i == 0 && pend_g >= 0) {
+                    if (pend_g >= 0) {
                         epilogue(pend_g, pend_b);
                         pend_g = -1;
                     }
-                    if (yprev >= 0 && !sft_convert(S, i - 1, yprev)) S.dead = true;
+                    if (yprev >= 0 && !sft_convert(S, iprev, yprev)) S.dead = true;
                     yprev = yb;
+                    iprev = i;
                     /* the buffer of the plane before is free: its y MMAs completed
                      * (converted above, or at the end of the previous group) */
                     load_next();
                 }
-                if (!sft_convert(S, np - 1, yprev)) S.dead = true;
+                if (!sft_convert(S, iprev, yprev)) S.dead = true;
                 /* planes past the window's end: zero rows (excluded from every sum) */
                 for (int e = threadIdx.x + np * SFD_WY * 16; e < SFT_PLANES * SFD_WY * 16; e += SFD_THREADS) {
                     const u32 m = (u32)(e / 16);
