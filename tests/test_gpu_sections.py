@@ -26,6 +26,7 @@ def dev():
     ((96, 24, 70), 32, ((0.0, 2.0),)),  # no x filter: no halo; nz ragged
     ((60, 32, 64), 64, BANK),           # one section holds the cube
     ((130, 36, 64), 16, BANK),          # halo wider than the section
+    ((150, 40, 101), 64, BANK),         # rows not 16-byte multiples: the padded layout
 ])
 def test_sections_match_whole_cube(dev, shape, section, bank):
     import torch

@@ -83,7 +83,8 @@ def _rank_gpu(rank, world, port, out_dir, shape, bank, window):
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("shape,window", [((200, 64, 256), (32, 32, 64)),    # slabs of 128 + 72
-                                          ((70, 40, 100), (16, 16, 32))])    # ragged nz, tail window
+                                          ((70, 40, 100), (16, 16, 32)),     # ragged nz, tail window
+                                          ((70, 40, 101), (16, 16, 32))])    # padded rows
 def test_two_rank_slabs_through_the_library(tmp_path, shape, window):
     import socket
 
