@@ -5,7 +5,9 @@
  * memory at any time.  A request is admitted as soon as a worker slot is free
  * and its device footprint fits the HBM budget: the footprint is that of the
  * context sf_detect_host runs it on (the cube, the mask and one x-filtered
- * scratch cube per distinct non-zero sigma_xy).  Admitted requests run
+ * scratch cube per distinct non-zero sigma_xy; where rows are not 16-byte
+ * multiples, the scratch rows padded and one more scratch cube, the cube's
+ * padded copy).  Admitted requests run
  * concurrently, one CUDA stream per worker, so their copies and kernels
  * overlap on the device; a request that arrives while others are on the GPU
  * is admitted as soon as a slot and memory free up (no batch boundary).
@@ -96,7 +98,12 @@ int64_t footprint(const sf_server *s, int64_t nx, int64_t ny, int64_t nz)
     auto up = [](int64_t v) { return (v + 255) / 256 * 256; };
     const int64_t cube = up(nx * ny * nz * (int64_t)s->ebytes);
     const int64_t mask = up(nx * ny * ((nz + 31) / 32) * 4);
-    return cube * (1 + s->n_xy) + mask + 4096;
+    /* the context's scratch: rows padded to 16 bytes, and a padded copy of
+     * the cube, where nz * element size is not a multiple of 16 (sf_create) */
+    const int64_t vec = 16 / (int64_t)s->ebytes;
+    const int64_t zs = nz % vec != 0 ? (nz + vec - 1) / vec * vec : nz;
+    const int64_t slot = up(nx * ny * zs * (int64_t)s->ebytes);
+    return cube + slot * (s->n_xy + (zs != nz ? 1 : 0)) + mask + 4096;
 }
 
 /* make room for `need` bytes by destroying idle contexts (LRU); caller holds mu */
