@@ -1444,7 +1444,7 @@ static_assert(SFD_HZ + SFD_RZM <= 48, "band within the 64-column Toeplitz tile")
 static_assert(SFT_KYM <= 64, "y filter rows within one 128-byte row of the y tile");
 
 struct sft_tiles {
-    unsigned char z[SFT_NZT][2][2048];                  /* z Toeplitz tiles: 16 x 64, hi and lo */
+    unsigned char z[SFT_NZT][2][SFT_ZROWS * 32];       /* z Toeplitz tall tiles: ZROWS x 16, hi and lo */
     unsigned char y[SFT_NYT > 0 ? SFT_NYT : 1][2][4096]; /* y Toeplitz tiles: 32 x 64, hi and lo */
     int zt[SFD_NSRC][SFD_NZF];                          /* z tile of each (input, filter) */
     int yt[SFD_NSRC];                                   /* y tile of each input (-1: none) */
@@ -1457,6 +1457,13 @@ __device__ __forceinline__ u32 sft_sw128(u32 row, u32 kbyte)
 {
     return (row >> 3) * 1024u + (row & 7u) * 128u + ((((kbyte >> 4) ^ (row & 7u)) & 7u) << 4) + (kbyte & 15u);
 }
+/* shared-memory matrix descriptor without swizzle (K-major: lbo = stride
+ * between the two core matrices along K, sbo = stride between 8-row groups) */
+__device__ __forceinline__ unsigned long long sft_desc_plain(u32 addr, u32 lbo, u32 sbo)
+{
+    return (unsigned long long)((addr >> 4) & 0x3fffu) | ((unsigned long long)((lbo >> 4) & 0x3fffu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
 /* shared-memory matrix descriptor, 128-byte swizzle, version 1: lbo = stride
  * between 64-element atoms along M/N (MN-major operands), sbo = stride
  * between 8-row groups */
@@ -1466,14 +1473,27 @@ __device__ __forceinline__ unsigned long long sft_desc(u32 addr, u32 lbo, u32 sb
            ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46) | (2ull << 61);
 }
 /* kind::f16 instruction descriptors: D FP32, A/B FP16 (0) or BF16 (1);
- * z: both K-major, N = 16, M = 128; y: A MN-major, N = 32, M = 128 */
+ * z: both K-major, N = 32 (two output tiles), M = 128; y: A MN-major, N = 32, M = 128 */
 constexpr u32 SFT_AB = SFT_BF16 ? 1u : 0u;
-constexpr u32 SFT_IDESC_Z = (1u << 4) | (SFT_AB << 7) | (SFT_AB << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr u32 SFT_IDESC_Z = (1u << 4) | (SFT_AB << 7) | (SFT_AB << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 constexpr u32 SFT_IDESC_Y =
     (1u << 4) | (SFT_AB << 7) | (SFT_AB << 10) | (1u << 15) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 
-__host__ __device__ constexpr int sft_slo(int r) { return (SFD_HZ - r) / 16; }
-__host__ __device__ constexpr int sft_shi(int r) { return (15 + SFD_HZ + r) / 16; }
+/* z MMAs: 32 outputs (two 16-output tiles, pair p) per MMA.  Outputs
+ * 32p .. 32p+31 read the K-slices sft_zlo(r, p) .. sft_zhi(r, p).  The B
+ * operand of (p, slice S) is rows t0 .. t0+31 of the filter's tall tile
+ * Tt[t][kk] = g[kk - t + C] (no swizzle, K-major: 8-row groups of two
+ * 8 x 16-byte core matrices, 256 bytes apart), t0 = 32p + HZ + C - 16S,
+ * C the smallest multiple of 8 that keeps every t0 >= 0. */
+__host__ __device__ constexpr int sft_zlo(int r, int p) { return (32 * p + SFD_HZ - r) / 16; }
+__host__ __device__ constexpr int sft_zhi(int r, int p) { return (32 * p + 31 + SFD_HZ + r) / 16; }
+__host__ __device__ constexpr int sft_zc(int r)
+{
+    const int m0 = 16 * sft_zhi(r, 0) - SFD_HZ, m1 = 16 * sft_zhi(r, 1) - 32 - SFD_HZ;
+    const int m = m0 > m1 ? m0 : m1;
+    return m <= 0 ? 0 : (m + 7) / 8 * 8;
+}
+__host__ __device__ constexpr int sft_zt0(int r, int p, int S) { return 32 * p + SFD_HZ + sft_zc(r) - 16 * S; }
 __host__ __device__ constexpr int sft_ky(int ry) { return (SFD_WY + 2 * ry + 15) / 16 * 16; }
 
 struct sft_state {
@@ -1598,23 +1618,22 @@ __device__ __forceinline__ void sft_mma_z(const sft_state &S, const sft_tiles &b
     const unsigned long long a0 = sft_desc(sf_smem_addr(A), 16u, 1024u);
 #pragma unroll
     for (int f = 0; f < NZ; ++f) {
-        const int r = f == 0 ? RZ0 : RZ1;
-        constexpr int SLO0 = sft_slo(RZ0), SHI0 = sft_shi(RZ0), SLO1 = sft_slo(RZ1), SHI1 = sft_shi(RZ1);
-        const int slo = f == 0 ? SLO0 : SLO1, shi = f == 0 ? SHI0 : SHI1;
-        (void)r;
-        const unsigned long long t0 = sft_desc(sf_smem_addr(S.T + bt.zt[SI][f] * 2 * 2048), 16u, 1024u);
+        constexpr int RA = RZ0, RB = RZ1;
+        const unsigned long long t0 =
+            sft_desc_plain(sf_smem_addr(S.T + bt.zt[SI][f] * 2 * SFT_ZROWS * 32), 128u, 256u);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const u32 d = S.tmem + (u32)(buf * 128 + f * 64 + j * 16);
+        for (int p = 0; p < 2; ++p) {
+            const u32 d = S.tmem + (u32)(buf * 128 + f * 64 + p * 32);
+            const int lo = f == 0 ? sft_zlo(RA, p) : sft_zlo(RB, p), hi = f == 0 ? sft_zhi(RA, p) : sft_zhi(RB, p);
             u32 acc = 0u;
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                if (s < slo || s > shi) continue;
-                const int ts = j + s;
+            for (int ts = 0; ts < 7; ++ts) {
+                if (ts < lo || ts > hi) continue;
+                const int t0r = f == 0 ? sft_zt0(RA, p, ts) : sft_zt0(RB, p, ts);
                 const unsigned long long ad = a0 + (unsigned long long)(((ts >> 2) * SFT_ATOM + (ts & 3) * 32) >> 4);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const unsigned long long bd = t0 + (unsigned long long)((h * 2048 + s * 32) >> 4);
+                    const unsigned long long bd = t0 + (unsigned long long)((h * SFT_ZROWS * 32 + (t0r / 8) * 256) >> 4);
                     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
                                  "l"(ad), "l"(bd), "r"(SFT_IDESC_Z), "r"(acc));

@@ -918,22 +918,43 @@ sf_status plan_detect_tc(sf_ctx *c)
         if (wp.srcs[i].ry > 0) yt[i] = nyt++;
     }
     const int nzt = (int)zkeys.size();
-    const size_t zbytes = (size_t)nzt * 2 * 2048, ybytes = (size_t)std::max(1, nyt) * 2 * 4096;
+    /* z tiles: the kernel's z MMAs take 32 outputs (pair p of 16-output
+     * tiles) per MMA against rows t0 .. t0+31 of a tall Toeplitz tile
+     * Tt[t][kk] = g[kk - t + C] (16 columns, no swizzle), t0 = 32p + HZ + C -
+     * 16S for the K-slices S of the pair; C and the rows follow the kernel's
+     * sft_zc / sft_zt0 */
+    auto zlo = [&](int r, int pp) { return (32 * pp + HZ - r) / 16; };
+    auto zhi = [&](int r, int pp) { return (32 * pp + 31 + HZ + r) / 16; };
+    auto zc = [&](int r) {
+        const int m = std::max(16 * zhi(r, 0) - HZ, 16 * zhi(r, 1) - 32 - HZ);
+        return m <= 0 ? 0 : (m + 7) / 8 * 8;
+    };
+    int zrows = 0;
+    for (int u = 0; u < nzt; ++u) {
+        const int rz = ((int)zkeys[u].size() - 1) / 2;
+        for (int pp = 0; pp < 2; ++pp)
+            zrows = std::max(zrows, 32 * pp + HZ + zc(rz) - 16 * zlo(rz, pp) + 32);
+    }
+    zrows = (zrows + 15) / 16 * 16;   /* the y tile after the z tiles stays 1024-aligned */
+    const size_t zpart = (size_t)zrows * 32;
+    const size_t zbytes = (size_t)nzt * 2 * zpart, ybytes = (size_t)std::max(1, nyt) * 2 * 4096;
     const size_t tile_bytes = zbytes + ybytes;
     /* the parameter block: tiles, then zt[nsrc][nzf] and yt[nsrc] as int32 */
     c->tcb.assign(tile_bytes + sizeof(int32_t) * ((size_t)nsrc * wp.nzf + nsrc), 0);
     const float scale = 1024.f;   /* 2^10: the z taps' low parts stay normal */
     for (int u = 0; u < nzt; ++u) {
         const std::vector<float> &gz = zkeys[u];
-        const int rz = ((int)gz.size() - 1) / 2;
-        for (int n = 0; n < 16; ++n)
-            for (int k = 0; k < 64; ++k) {
-                const int o = k - n - HZ;
+        const int rz = ((int)gz.size() - 1) / 2, C = zc(rz);
+        for (int t = 0; t < zrows; ++t)
+            for (int kk = 0; kk < 16; ++kk) {
+                const int o = kk - t + C;
                 const float v = (o >= -rz && o <= rz) ? gz[rz + o] * scale : 0.f;
                 uint16_t hi, lo;
                 split16(c, v, &hi, &lo);
-                std::memcpy(&c->tcb[((size_t)u * 2 + 0) * 2048 + sw128_offset(n, 2 * k)], &hi, 2);
-                std::memcpy(&c->tcb[((size_t)u * 2 + 1) * 2048 + sw128_offset(n, 2 * k)], &lo, 2);
+                /* 8-row groups of two 8 x 16-byte core matrices (k 0-7, 8-15) */
+                const size_t off = (size_t)(t / 8) * 256 + (size_t)(kk / 8) * 128 + (size_t)(t % 8) * 16 + (size_t)(kk % 8) * 2;
+                std::memcpy(&c->tcb[((size_t)u * 2 + 0) * zpart + off], &hi, 2);
+                std::memcpy(&c->tcb[((size_t)u * 2 + 1) * zpart + off], &lo, 2);
             }
     }
     for (int i = 0; i < nsrc; ++i) {
@@ -1001,6 +1022,7 @@ sf_status plan_detect_tc(sf_ctx *c)
     p += "#define SFT_OFF_FLAGS " + std::to_string(offF) + "\n";
     p += "#define SFT_OFF_MBAR " + std::to_string(offMB) + "\n";
     p += "#define SFT_NZT " + std::to_string(nzt) + "\n";
+    p += "#define SFT_ZROWS " + std::to_string(zrows) + "\n";
     p += "#define SFT_NYT " + std::to_string(nyt) + "\n";
     p += std::string("#define SFT_BF16 ") + (g.storage == SF_BF16 ? "1" : "0") + "\n";
     std::string err;
