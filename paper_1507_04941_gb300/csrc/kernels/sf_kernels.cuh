@@ -1434,7 +1434,7 @@ sf_persist(const __grid_constant__ sf_pargs pa, const __grid_constant__ sfd_taps
 constexpr int SFT_M = 128;
 constexpr int SFT_PLANES = SFT_M / SFD_WY;          /* planes per group (4) */
 constexpr int SFT_ATOM = SFT_M * 128;                /* bytes of one 64-column atom of the A tile */
-constexpr int SFT_TM_COLS = 256;                     /* z accumulators at 0 and 128; y at 128, 160 */
+constexpr int SFT_TM_COLS = 256;                     /* z accumulators at 0 and 128; y at 128, 192 */
 constexpr int SFT_KYM = (SFD_WY + 2 * SFD_RYM + 15) / 16 * 16;   /* padded slab rows */
 constexpr int SFT_SLAB_BYTES = 2 * SFT_KYM * 128;    /* one slab buffer: two 64-column atoms */
 constexpr int SFT_NS = 3;                            /* slab buffers: copies two planes ahead */
@@ -1473,11 +1473,12 @@ __device__ __forceinline__ unsigned long long sft_desc(u32 addr, u32 lbo, u32 sb
            ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46) | (2ull << 61);
 }
 /* kind::f16 instruction descriptors: D FP32, A/B FP16 (0) or BF16 (1);
- * z: both K-major, N = 32 (two output tiles), M = 128; y: A MN-major, N = 32, M = 128 */
+ * z: both K-major, N = 32 (two output tiles), M = 128; y: A MN-major, N = 64
+ * (the 32 outputs against the hi part, then against the lo part), M = 128 */
 constexpr u32 SFT_AB = SFT_BF16 ? 1u : 0u;
 constexpr u32 SFT_IDESC_Z = (1u << 4) | (SFT_AB << 7) | (SFT_AB << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 constexpr u32 SFT_IDESC_Y =
-    (1u << 4) | (SFT_AB << 7) | (SFT_AB << 10) | (1u << 15) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    (1u << 4) | (SFT_AB << 7) | (SFT_AB << 10) | (1u << 15) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
 
 /* z MMAs: 32 outputs (two 16-output tiles, pair p) per MMA.  Outputs
  * 32p .. 32p+31 read the K-slices sft_zlo(r, p) .. sft_zhi(r, p).  The B
@@ -1590,19 +1591,20 @@ __device__ __forceinline__ void sft_mma_y(const sft_state &S, const sft_tiles &b
     const unsigned long long t0 = sft_desc(sf_smem_addr(S.T + SFT_ZT_BYTES), 16u, 1024u);   /* this input's y tile */
     (void)bt;
     (void)SI;
-    const u32 d = S.tmem + 128u + (u32)(yb * 32);
+    /* the tile's hi and lo parts are 32 rows each, contiguous in the same
+     * swizzled layout: one N = 64 MMA per K-slice takes both, into columns
+     * 0-31 (hi) and 32-63 (lo) of the accumulator, which the read-out adds */
+    const u32 d = S.tmem + 128u + (u32)(yb * 64);
     u32 acc = 0u;
 #pragma unroll
-    for (int s = 0; s < KY / 16; ++s)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const unsigned long long ad = a0 + (unsigned long long)((s * 2048) >> 4);
-            const unsigned long long bd = t0 + (unsigned long long)((h * 4096 + s * 32) >> 4);
-            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                         "l"(ad), "l"(bd), "r"(SFT_IDESC_Y), "r"(acc));
-            acc = 1u;
-        }
+    for (int s = 0; s < KY / 16; ++s) {
+        const unsigned long long ad = a0 + (unsigned long long)((s * 2048) >> 4);
+        const unsigned long long bd = t0 + (unsigned long long)((s * 32) >> 4);
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                     "l"(ad), "l"(bd), "r"(SFT_IDESC_Y), "r"(acc));
+        acc = 1u;
+    }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(S.bar_y + 8u * (u32)yb)
                  : "memory");
 }
@@ -1671,7 +1673,13 @@ __device__ __forceinline__ bool sft_convert(sft_state &S, int slot, int yb)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int z = 32 * (warp & 3) + lane, half = warp >> 2;
     float v[16];
-    sft_ld16(S.tmem + ((u32)((warp & 3) * 32) << 16) + 128u + (u32)(yb * 32 + half * 16), v);
+    sft_ld16(S.tmem + ((u32)((warp & 3) * 32) << 16) + 128u + (u32)(yb * 64 + half * 16), v);
+    {
+        float vl[16];   /* the lo part's products */
+        sft_ld16(S.tmem + ((u32)((warp & 3) * 32) << 16) + 128u + (u32)(yb * 64 + 32 + half * 16), vl);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] += vl[q];
+    }
     unsigned char *col = S.A + (z >> 6) * SFT_ATOM;
     const u32 kb = (u32)((z & 63) * 2);
 #pragma unroll
