@@ -1811,16 +1811,22 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
         }
     };
     /* the z MMAs of group g once its A tile is complete */
-    auto issue_z = [&](int g, int buf, int ab) {
+    /* one barrier: the A tile is complete and every thread is alive (false:
+     * a wait expired somewhere, the input stops) */
+    auto issue_z = [&](int g, int buf, int ab) -> bool {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        if (__syncthreads_or(S.dead)) {
+            S.dead = true;
+            return false;
+        }
         if (threadIdx.x == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             sft_mma_z<IDX, NZ, RZ0, RZ1>(S, bt, buf, sft_abuf(S, ab));
         }
         S.pend |= 32u << buf;
         (void)g;
+        return true;
     };
 
     sft_start<IDX, RY>(mp, S, next_group(-1));
@@ -1835,10 +1841,10 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                 const int gn = next_group(gi);
                 const bool ok = sft_wait(S, S.bar_a, S.ph_a, ab, 1);
                 S.pend &= ~(8u << ab);
-                if (__syncthreads_or(!ok || S.dead)) { S.dead = true; return; }
+                if (!ok) S.dead = true;
                 const int cur = nbuf;
                 nbuf ^= 1;
-                issue_z(gi, cur, ab);
+                if (!issue_z(gi, cur, ab)) return;
                 if (gn >= 0 && threadIdx.x == 0) {
                     /* the other A buffer was read by the previous group's z MMAs:
                      * refill it once they completed (a peek: the epilogue waits
@@ -1928,8 +1934,7 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
                     *reinterpret_cast<uint4 *>(S.A + (k >> 6) * SFT_ATOM + sft_sw128(m, (u32)((k & 63) * 2))) =
                         make_uint4(0u, 0u, 0u, 0u);
                 }
-                if (__syncthreads_or(S.dead)) { S.dead = true; return; }
-                issue_z(gi, 0, 0);
+                if (!issue_z(gi, 0, 0)) return;
                 pend_g = gi;
                 pend_b = 0;
                 gi = gn;
