@@ -510,15 +510,23 @@ def run_ours(args):
             for _ in range(2):
                 ss.detect_host(h_cube_s, h_mask_s)
             n_s = max(3, min(args.steps, 20))
+            # each call ends with its mask on the host, so a host clock around
+            # it times one step; the mean is the value, the spread shows
+            # transient slowdowns of the host link
+            per = []
             torch.cuda.synchronize(dev)
-            t0 = time.perf_counter()
             for _ in range(n_s):
+                t0 = time.perf_counter()
                 ss.detect_host(h_cube_s, h_mask_s)
+                per.append(time.perf_counter() - t0)
             torch.cuda.synchronize(dev)
-            s_sec = (time.perf_counter() - t0) / n_s
+            s_sec = sum(per) / n_s
         rxm = max(int(math.ceil(w.truncation * b[0])) for b in w.bank)
         halo = -(-rxm // w.window[0]) * w.window[0] if rxm else 0
+        per.sort()
         sectioned = {"value": units / s_sec, "unit": UNIT, "ms_per_step": s_sec * 1e3, "steps": n_s,
+                     "step_ms_min_median_max": [round(per[0] * 1e3, 3), round(per[n_s // 2] * 1e3, 3),
+                                                round(per[-1] * 1e3, 3)],
                      "section_planes": sec, "halo_planes": halo,
                      "device_bytes": int(dev_bytes),
                      "device_bytes_in_core": int(nvox * sbytes * (1 + len({b[0] for b in w.bank if b[0] > 0}))),
