@@ -10,7 +10,8 @@
  *
  * Conventions shared by every entry point:
  *   - Cube layout is cube[x][y][z], z (frequency) contiguous, x the major
- *     axis (Sec. 3.1).  nx, ny, nz >= 1.
+ *     axis (Sec. 3.1).  1 <= nx, ny, nz <= 2^31; an empty cube (a zero
+ *     extent) is refused with SF_EINVAL before any device work.
  *   - Pointers prefixed d_ are device pointers, h_ host pointers.  The caller
  *     owns every buffer it passes and must keep it alive until the work
  *     enqueued on `stream` has finished.  Device pointers must be 16-byte

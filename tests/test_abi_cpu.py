@@ -67,7 +67,8 @@ def _cfg(sf, **kw):
     return sf.Config(**vals), specs
 
 
-@pytest.mark.parametrize("bad", [dict(nx=0), dict(nz=-3), dict(n_filters=0), dict(truncation=0.0),
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(ny=0), dict(nz=-3), dict(nx=2 ** 31 + 1),
+                                 dict(n_filters=0), dict(truncation=0.0),
                                  dict(wx=0), dict(storage=7), dict(stats_fp64=2), dict(std_ddof=2),
                                  dict(bank=((-1.0, 2.0),)), dict(bank=((1.0, 40.0),)),
                                  dict(filters=None)])
@@ -80,6 +81,20 @@ def test_invalid_config_rejected_on_host(libsf, bad):
     assert st == sf.SF_EINVAL
     assert not h.value
     assert lib.sf_last_error(None).decode()
+
+
+@pytest.mark.parametrize("dims", [(0, 4, 8), (4, 0, 8), (4, 4, 0), (4, 4, -1), (2 ** 31 + 1, 1, 1)])
+def test_batch_with_an_empty_or_oversized_cube_rejected_on_host(libsf, dims):
+    """An empty cube (a zero extent) has no windows: a batch holding one is
+    refused before any device work, as is an extent above 2^31."""
+    from paper_1507_04941_gb300 import sf
+    lib = sf.lib()
+    cfg, _keep = _cfg(sf)
+    arr = (ctypes.c_int64 * 6)(16, 16, 32, *dims)
+    h = ctypes.c_void_p()
+    assert lib.sf_create_batch(ctypes.byref(cfg), 2, arr, ctypes.byref(h)) == sf.SF_EINVAL
+    assert not h.value
+    assert "dimensions" in lib.sf_last_error(None).decode()
 
 
 def test_create_without_gpu_reports_cuda_error(libsf):
