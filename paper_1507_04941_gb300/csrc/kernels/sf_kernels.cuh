@@ -1758,7 +1758,10 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
         float mx = -3.402823466e38f;
         u32 w0 = 0u, w1 = 0u;
         if (mine) {
-#pragma unroll
+            /* not unrolled: this read-out is inlined at every call site of
+             * every input, and four copies of it per site made the kernel's
+             * code outgrow the instruction caches */
+#pragma unroll 1
             for (int j = 0; j < 4; ++j) {
                 float v[16];
                 sft_ld16(S.tmem + ((u32)(slot * 32) << 16) + (u32)(b * 128 + f * 64 + j * 16), v);
