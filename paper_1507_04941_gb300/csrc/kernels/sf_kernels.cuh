@@ -1103,7 +1103,9 @@ __device__ __forceinline__ void sfw_input(const sf_dargs &a, const sfd_taps &t, 
                     const sfd_st n = (sfd_st)cnt, mu = (sfd_st)s1[f] / n;
                     m = sfd_mom{n, (sfd_st)K[f] + mu, fmax((sfd_st)s2[f] - (sfd_st)s1[f] * mu, (sfd_st)0)};
                 }
-#pragma unroll
+                /* rolled: once per input and window, and every input's copy
+                 * of the kernel carries it (smaller code, fewer fetch stalls) */
+#pragma unroll 1
                 for (int off = 1; off < 32; off <<= 1) {
                     sfd_mom o;
                     o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
@@ -1955,7 +1957,8 @@ __device__ __forceinline__ void sft_input(const sf_dargs &a, const sfd_taps &t, 
             const sfd_st n = (sfd_st)cnt, mu = (sfd_st)s1 / n;
             m = sfd_mom{n, (sfd_st)K + mu, fmax((sfd_st)s2 - (sfd_st)s1 * mu, (sfd_st)0)};
         }
-#pragma unroll
+        /* rolled: once per input and window (smaller code) */
+#pragma unroll 1
         for (int off = 1; off < 32; off <<= 1) {
             sfd_mom o;
             o.n = __shfl_xor_sync(0xffffffffu, m.n, off);
